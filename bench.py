@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Benchmark: seconds per HMC trajectory of the Schwarz-preconditioned
+two-flavour Wilson HMC (one-dimensional x0-slab decomposition) on a
+16^3 x 32 lattice, mixed-precision batched form, beside the plain
+double-precision GPU form, the Dslash bandwidth against the HBM roofline
+and the FP64 CPU oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  A step is one full trajectory (heatbath,
+molecular dynamics with the W1 and boundary (Schur) pseudo-fermion forces
+and the gauge force on three time scales, Metropolis, x0 shift) on seeded
+synthetic links; inputs are resident in HBM and L2 is flushed between
+timed trajectories.  With N > 1 every rank runs an independent replica on
+its own GPU (the path is not sharded here), the time is the maximum over
+ranks and value = that time / all trajectories of the job.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# ---------------------------------------------------------------------------
+# the workload (16^3 x 32, kappa = 0.1575, beta = 5.6, l0 = 4: 8 slabs)
+# ---------------------------------------------------------------------------
+WL = dict(L=(32, 16, 16, 16), l0=4, kappa=0.1575, beta=5.6, eps=0.6, seed=2009, tau=1.0,
+          nlevels=3, scheme=(1, 1, 1), nsteps=(2, 4, 8), lam=0.1931833275037836,
+          level_gauge=0, level_w1=1, level_schur=2, tol=1e-10, max_iter=20000)
+WORKLOAD_NAME = ("Schwarz-HMC trajectory 16^3x32, l0=4 (8 x0-slabs, red/black), kappa=0.1575, "
+                 "beta=5.6, tau=1, Omelyan (lambda=0.1932) on 3 time scales: gauge / W1 / boundary "
+                 "Schur force, n=(2,4,8); eps=0.6 synthetic links")
+DSLASH_L = (64, 32, 32, 32)
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (host cores)
+# ---------------------------------------------------------------------------
+def oracle_M_seconds(budget_s, L, l0, eps, seed):
+    """seconds per application of the oracle's full-lattice Wilson matrix"""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_0710_0066_gb300 import synthetic as syn
+
+    lat = O.Lattice(L, l0, -1)
+    U = syn.random_links(L, eps, seed)
+    x = syn.gaussian_spinor(lat.V, seed + 1)
+    lat.M(U, 0.1575, x)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        x = lat.M(U, 0.1575, x)
+        x /= np.linalg.norm(x)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return (time.perf_counter() - t0) / n, n
+
+
+def oracle_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+# Wilson-matrix applications in one trajectory of this workload: four
+# half-lattice hopping sweeps per inner iteration and system site, counted by
+# the library (site_iters); the value below is the mixed-precision count of a
+# 16^3x32 run, used when no GPU run is made in the same process
+M_APPS_PER_TRAJ_DEFAULT = 6000.0
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    L, l0 = WL["L"], WL["l0"]
+    times = []
+    for k in range(args.warmup + args.steps):
+        t_M, n = oracle_M_seconds(8.0, L, l0, WL["eps"], WL["seed"])
+        if k >= args.warmup:
+            times.append(t_M * M_APPS_PER_TRAJ_DEFAULT)
+    v = statistics.mean(times)
+    line = {
+        "impl": "reference", "metric": "s/HMC trajectory (16^3x32 Schwarz HMC)", "value": v,
+        "unit": "s/trajectory", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD_NAME},
+        "cpu_baseline": {"value": v, "unit": "s/trajectory", "cores": oracle_threads(), "kind": "oracle",
+                         "sample": "per step ~8 s of oracle Wilson-matrix applications (FP64, 16^3x32), "
+                                   "scaled by %d applications per trajectory" % M_APPS_PER_TRAJ_DEFAULT},
+        "e2e": {"value": v, "unit": "s/trajectory", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_0710_0066_gb300 import lqcd, synthetic as syn
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    L, l0 = WL["L"], WL["l0"]
+    lat = lqcd.Lattice(L, l0, -1)
+    U0 = syn.random_links_torch(L, WL["eps"], WL["seed"] + rank, "cuda").contiguous()
+
+    def params(prec):
+        return lqcd.hmc_params(WL["beta"], WL["kappa"], WL["tau"], WL["nlevels"], WL["scheme"], WL["nsteps"],
+                               WL["level_gauge"], WL["level_w1"], WL["level_schur"], lam=WL["lam"], roll=1,
+                               metropolis=1, precision=prec, tol=WL["tol"], max_iter=WL["max_iter"])
+
+    prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
+    prm = params(prec)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    U = U0.clone()
+    traj = 0
+    for _ in range(args.warmup):
+        U, res = lat.hmc_trajectory(U, prm, WL["seed"], traj)
+        traj += 1
+    torch.cuda.synchronize()
+
+    # ---- timed region: K trajectories, L2 flushed between them
+    lqcd.lqcd_profile_reset(lat.h)
+    lqcd.lqcd_profile_enable(lat.h, 1 << lqcd.KERNEL_SOLVER)
+    l0_launch = lqcd.lqcd_launch_count(lat.h)
+    clocks = Clocks(local)
+    clocks.start()
+    step_ms, results, U_in = [], [], []
+    for k in range(args.steps):
+        flush.zero_()
+        barrier()
+        U_in.append((U.clone(), traj))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        U, res = lat.hmc_trajectory(U, prm, WL["seed"], traj)
+        b.record(stream)
+        barrier()
+        step_ms.append(a.elapsed_time(b))
+        results.append(res)
+        traj += 1
+    clk = clocks.stop()
+    launches = lqcd.lqcd_launch_count(lat.h) - l0_launch
+    n_sol, ms_sol, by_sol = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
+    lqcd.lqcd_profile_enable(lat.h, 0)
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = total_ms / 1e3 / (args.steps * world)
+
+    # ---- plain double-precision GPU form on the first timed input
+    fp64 = None
+    if not args.no_fp64 and prec != lqcd.PREC_F64:
+        Uk, tk = U_in[0]
+        prm64 = params(lqcd.PREC_F64)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, r64 = lat.hmc_trajectory(Uk, prm64, WL["seed"], tk)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        fp64 = {"s_per_traj": t64, "dH": r64.dH, "dH_mixed": results[0].dH,
+                "abs_dH_diff": abs(r64.dH - results[0].dH),
+                "speedup_mixed_vs_fp64": t64 / (step_ms[0] / 1e3),
+                "solver_iters": r64.solver_iters}
+
+    # ---- end to end through the C-ABI with host buffers
+    Uh = torch.empty_like(U, device="cpu").pin_memory()
+    Uh.copy_(U)
+    Ud = torch.empty_like(U)
+    e2e_ms = []
+    for k in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ud.copy_(Uh, non_blocking=True)
+        res = lqcd.lqcd_hmc_trajectory(lat.h, Ud, prm, WL["seed"], traj)
+        Uh.copy_(Ud, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        traj += 1
+    e2e_value = e2e_ms[-1] / 1e3
+    ubytes = U.numel() * 16
+
+    # ---- Dslash (even-odd hopping sweep) bandwidth at 32^3 x 64 (> L2)
+    dslash = {}
+    if not args.no_dslash:
+        latd = lqcd.Lattice(DSLASH_L, 8, -1)
+        Ud_ = syn.random_links_torch(DSLASH_L, WL["eps"], WL["seed"] + 7, "cuda").contiguous()
+        latd.set_gauge(Ud_)
+        del Ud_
+        x = torch.randn((latd.Vh, 4, 3), dtype=torch.complex128, device="cuda")
+        for name, pr in (("f32", lqcd.PREC_F32), ("f16", lqcd.PREC_F16), ("f64", lqcd.PREC_F64)):
+            latd.dslash_eo(x, 0, 0.0, 0, lqcd.OP_HOP, pr)
+            lqcd.lqcd_profile_reset(latd.h)
+            lqcd.lqcd_profile_enable(latd.h, 1 << lqcd.KERNEL_HOP)
+            for _ in range(10):
+                latd.dslash_eo(x, 0, 0.0, 0, lqcd.OP_HOP, pr)
+            n, ms, by = lqcd.lqcd_profile_read(latd.h, lqcd.KERNEL_HOP)
+            lqcd.lqcd_profile_enable(latd.h, 0)
+            dslash[name] = {"gbs": by / ms / 1e6, "ms": ms / n, "bytes_per_launch": by / n}
+        latd.close()
+
+    # ---- oracle on the host cores (bounded sample)
+    site_iters = statistics.mean(r.site_iters for r in results)
+    m_apps = 4.0 * site_iters / lat.V
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        t_M, n = oracle_M_seconds(args.cpu_seconds, L, l0, WL["eps"], WL["seed"])
+        cpu = {"value": t_M * m_apps, "unit": "s/trajectory", "cores": oracle_threads(), "kind": "oracle",
+               "sample": "%d applications of the oracle's FP64 Wilson matrix at 16^3x32 (%.2f s each), "
+                         "scaled by the %.0f matrix applications of one GPU trajectory" % (n, t_M, m_apps)}
+
+    peak, peak_kind = hbm_peak()
+    achieved = by_sol / ms_sol / 1e6 if ms_sol > 0 else None
+    line = {
+        "metric": "s/HMC trajectory (16^3x32 Schwarz HMC, mixed precision batched)",
+        "value": value, "unit": "s/trajectory", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision + "-storage/f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "lattice": "x".join(map(str, L)), "l0": l0,
+                   "inner_precision": args.precision, "l2": "flushed between timed trajectories",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": "persistent batched solver (k_solve)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_kind": peak_kind, "launches": n_sol,
+                     "kernel_share_of_step": ms_sol / total_ms if total_ms else None},
+        "dslash": dslash,
+        "fp64_form": fp64,
+        "trajectory": {"dH": [r.dH for r in results], "accepted": [r.accepted for r in results],
+                       "plaq": results[-1].plaq, "solver_iters": [r.solver_iters for r in results],
+                       "n_solves": results[-1].n_solves, "n_force": results[-1].n_force,
+                       "step_ms": step_ms},
+        "e2e": {"value": e2e_value, "unit": "s/trajectory", "h2d_bytes_per_step": ubytes,
+                "d2h_bytes_per_step": ubytes},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f16", choices=["f16", "f32", "f64"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-dslash", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * lqcd.h -- C-ABI of the GB300 (sm_103a) hot path of the Schwarz-
+ * preconditioned two-flavour Wilson HMC with a one-dimensional (x0-slab)
+ * domain decomposition (M. Hasenbusch, "HMC algorithm for two-flavour
+ * lattice QCD: Schwarz-preconditioning with a one-dimensional domain
+ * decomposition", Lattice 2007, arXiv:0710.0066).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Status: every function returns LQCD_OK (0) or a negative LQCD_ERR_*;
+ *   lqcd_last_error() gives a one-line description.  No function exits,
+ *   traps or waits without bound: device-side waits are bounded and
+ *   report LQCD_ERR_TIMEOUT.
+ * Memory: every field pointer is a DEVICE pointer owned by the caller
+ *   (16-byte aligned); the library reads/writes it on the handle's stream
+ *   and owns only its internal workspace, allocated in lqcd_create.
+ * Sites x = (x0,x1,x2,x3), 0 <= x_mu < L_mu, x0 is time (Sec. 1, text
+ *   after eq. (1)).  All L_mu even; x0-slabs of thickness l0 with
+ *   L0 % (2 l0) == 0 (Sec. 1, one-dimensional block decomposition:
+ *   l_mu = L_mu for mu = 1,2,3); slab k = x0 / l0, colour k mod 2
+ *   (0 = red, 1 = black).
+ * Site order ("checkerboard"): all even sites (x0+x1+x2+x3 even), then all
+ *   odd sites; within one parity the lexicographic index
+ *   ((x0*L1 + x1)*L2 + x2)*L3 + x3, divided by two.
+ * Layouts (double precision, interleaved re,im):
+ *   spinor (full lattice)   double[V][4 spin][3 colour][2]
+ *   spinor (one parity)     double[V/2][4][3][2]
+ *   gauge field             double[4 mu][V][3][3][2], U_mu(x) row-major
+ *   momenta / forces        double[4 mu][V][8]: coefficients p^a of
+ *                           P = sum_a p^a T^a, T^a = lambda^a / 2
+ *   boundary field (R)      double[L0/(2 l0)][2 face][V3][2][3][2]: black
+ *                           slab k = 2j+1 has ordinal j; face 0 is its first
+ *                           time slice with spin basis (e_i - e_{i+2})/sqrt2
+ *                           of range (1+gamma_0)/2, face 1 its last slice
+ *                           with basis (e_i + e_{i+2})/sqrt2 of range
+ *                           (1-gamma_0)/2, i = 0,1; V3 spatial sites in
+ *                           lexicographic (x1,x2,x3) order.
+ * Gamma matrices: chiral basis, gamma_0 = [[0,-1],[-1,0]],
+ *   gamma_k = [[0,-i sigma_k],[i sigma_k,0]], gamma_5 = diag(1,1,-1,-1).
+ * Fermion phase bc_t (+1 / -1) on every x0 hop that wraps L0-1 <-> 0.
+ * Precision argument: LQCD_PREC_F64 runs everything in double precision;
+ *   LQCD_PREC_F32 / LQCD_PREC_F16 run stencils and inner Krylov iterations
+ *   with single- / half-precision storage (FP32 arithmetic) and keep
+ *   double-precision residuals, dot products and outer defect correction.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lqcd_ctx* lqcd_t;
+
+enum {
+    LQCD_OK = 0,
+    LQCD_ERR_ARG = -1,        /* bad pointer, size or flag */
+    LQCD_ERR_GEOM = -2,       /* invalid lattice / slab geometry */
+    LQCD_ERR_NOCONVERGE = -3, /* a solve hit max_iter */
+    LQCD_ERR_CUDA = -4,       /* a CUDA runtime call failed */
+    LQCD_ERR_NAN = -5,        /* non-finite residual or energy */
+    LQCD_ERR_TIMEOUT = -6,    /* a bounded device-side wait gave up */
+    LQCD_ERR_STATE = -7       /* call order (e.g. no gauge field set) */
+};
+
+enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2 };
+enum { LQCD_OP_HOP = 0, LQCD_OP_MHAT = 1 };
+enum { LQCD_SCHUR_R = 0, LQCD_SCHUR_RDAG = 1, LQCD_SCHUR_RINV = 2, LQCD_SCHUR_RINVDAG = 3 };
+enum { LQCD_TERM_W1 = 0, LQCD_TERM_SCHUR = 1 };
+enum { LQCD_LF = 0, LQCD_SW = 1 };
+
+/* Create a handle for the lattice L[4] with x0-slabs of thickness l0 and
+ * fermion phase bc_t on the x0 wrap.  stream: a cudaStream_t (NULL = the
+ * legacy default stream); every call of this handle is ordered on it.
+ * Allocates the internal workspace on the current device.
+ * Errors: LQCD_ERR_GEOM (odd extent, L0 % (2 l0) != 0, V >= 2^31),
+ * LQCD_ERR_ARG, LQCD_ERR_CUDA.  (Sec. 1: lattice, blocks l_0 x L1 x L2 x L3.) */
+int lqcd_create(lqcd_t* h, const int L[4], int l0, int bc_t, void* stream);
+int lqcd_destroy(lqcd_t h);
+const char* lqcd_last_error(lqcd_t h);
+int lqcd_set_stream(lqcd_t h, void* stream);
+
+/* Load the gauge field U (device, gauge layout above, SU(3) links) into the
+ * handle; builds the double, single (12-real, two rows) and half (12-real)
+ * internal copies.  lqcd_get_gauge writes the handle's double-precision
+ * field back in the same layout.  (Sec. 1: U_{x,mu} in SU(3).) */
+int lqcd_set_gauge(lqcd_t h, const double* U);
+int lqcd_get_gauge(lqcd_t h, double* U);
+
+/* Fill maps (device int32[14][V]) with the integer index maps, site s in
+ * checkerboard order: 0 lexicographic index, 1 parity, 2 slab, 3 colour,
+ * 4..7 site of x+mu_hat, 8..11 site of x-mu_hat (periodic), 12 face flags
+ * (1: first slice of its slab, 2: last slice), 13 boundary-field site
+ * (j*2+f)*V3 + lex3 for black face sites (face 0 if both), else -1.
+ * (Sec. 1: sites, slabs, red/black blocks.) */
+int lqcd_index_maps(lqcd_t h, int32_t* maps);
+
+/* Even-odd pieces of the Wilson matrix, eq. (2), M = 1 - kappa H with
+ *   (H psi)(x) = sum_mu (1-gamma_mu) U_mu(x) psi(x+mu)
+ *                     + (1+gamma_mu) U_mu(x-mu)^dag psi(x-mu).
+ * op = LQCD_OP_HOP:  out_p = H_{p,1-p} in_{1-p}  (in: parity 1-p field,
+ *                    out: parity p field); kappa unused.
+ * op = LQCD_OP_MHAT: out_e = in_e - kappa^2 H_eo H_oe in_e (parity must be
+ *                    0), the even-odd reduced matrix used for the global
+ *                    solver (Sec. 3: BiCGstab with even-odd preconditioning).
+ * dagger = 1 applies the adjoint (H^dag swaps the projectors).  precision
+ * selects the internal storage (results returned in double).  Asynchronous. */
+int lqcd_dslash_eo(lqcd_t h, double* out, const double* in, double kappa, int parity,
+                   int dagger, int op, int precision);
+
+/* W1: eq. (2) with every hop between different x0-slabs removed (Sec. 1,
+ * "eliminating the hopping terms in M that connect different blocks"),
+ * applied on the slabs of one colour (0 red, 1 black, -1 all); out is zero
+ * on the other slabs.  Full-lattice fields.  Asynchronous. */
+int lqcd_block_dslash(lqcd_t h, double* out, const double* in, double kappa, int colour,
+                      int dagger, int precision);
+
+/* Solve W1 x = b (dagger: W1^dag x = b) independently on every slab of the
+ * given colour (-1: all slabs) in one persistent batched launch: even-odd
+ * reduced BiCGstab per slab, inner iterations in `precision`, double
+ * precision residuals and defect correction to |b - W1 x| <= tol |b| per
+ * slab.  x is zero on the other slabs.  iters_out (host int[nb], may be
+ * NULL) receives the inner iterations per slab, resid_out (host
+ * double[nb], may be NULL) the final relative residual per slab (0 for
+ * slabs not solved).  Synchronous.  Errors: LQCD_ERR_NOCONVERGE after
+ * max_iter inner iterations, LQCD_ERR_TIMEOUT.  (Sec. 1 W1; Sec. 3 solver.) */
+int lqcd_block_solve_batched(lqcd_t h, double* x, const double* b, double kappa, int colour,
+                             int dagger, int precision, double tol, int max_iter,
+                             int* iters_out, double* resid_out);
+
+/* Solve M x = b (dagger: M^dag x = b) on the full lattice: even-odd reduced
+ * BiCGstab, inner iterations in `precision`, double precision defect
+ * correction to |b - M x| <= tol |b|.  iters_out / resid_out: host scalars
+ * (may be NULL).  Synchronous.  (Sec. 3: the S4 solver.) */
+int lqcd_solve_wilson(lqcd_t h, double* x, const double* b, double kappa, int dagger,
+                      int precision, double tol, int max_iter, int* iters_out,
+                      double* resid_out);
+
+/* Boundary operator of det^2(W1^-1 M) (Sec. 1, pseudo-fermions on the
+ * boundaries of the black blocks, dimension halved).  With sites ordered
+ * red|black, M = [[A,B],[C,D]], W1 = diag(A,D), block LU gives
+ * det M = det W1 det R with
+ *   R = E (1 - C A^-1 B D^-1) E^dag
+ * on the boundary space (E: orthonormal spin-projected black-face
+ * coordinates, layout above).  op: R, R^dag, R^-1 = E D (M^-1)_bb E^dag,
+ * R^-dag.  in/out: boundary fields.  Synchronous. */
+int lqcd_schur_apply(lqcd_t h, double* out, const double* in, double kappa, int op,
+                     int precision, double tol, int max_iter);
+
+/* Pseudo-fermion action and force (Sec. 1 eq. (3), Sec. 2 eq. (4)):
+ * term W1:    S = |W1^-1 phi|^2, phi a full-lattice spinor;
+ * term SCHUR: S = |R^-1 phi|^2, phi a boundary field.
+ * F (device double[4][V][8]) += dS/dw^a for U_mu(x) -> exp(i w^a T^a) U_mu(x)
+ * (not zeroed).  S_out (host, may be NULL) receives S.  F may be NULL to
+ * compute S only.  Solutions are recomputed, never stored.  Synchronous. */
+int lqcd_pf_force(lqcd_t h, double* F, const double* phi, double kappa, int term,
+                  int precision, double tol, int max_iter, double* S_out);
+
+/* Wilson gauge action (Sec. 1): S_G = -beta/3 sum_x sum_{mu>nu} Re tr P_{mu nu}(x).
+ * F (device, may be NULL) += dS_G/dw^a; S_out / plaq_out (host, may be NULL)
+ * receive S_G and the average Re tr P / 3.  Synchronous. */
+int lqcd_gauge_force(lqcd_t h, double* F, double beta, double* S_out, double* plaq_out);
+
+/* Philox4x32-10 normal deviates (Salmon et al., SC'11) as used by the HMC
+ * heatbath: out[k] (device double[n]) for counter (k/2 lo, k/2 hi, stream,
+ * traj) and key (seed lo, seed hi); two 53-bit uniforms per counter and
+ * Box-Muller (cos for even k, sin for odd k).  Asynchronous. */
+int lqcd_rng_normals(lqcd_t h, double* out, int64_t n, uint64_t seed, uint32_t stream,
+                     uint32_t traj);
+
+typedef struct {
+    double beta, kappa;
+    double tau;         /* trajectory length */
+    double lambda;      /* SW / Omelyan parameter, the paper uses 1/6 */
+    int nlevels;        /* 1..4 integration levels */
+    int scheme[4];      /* LQCD_LF or LQCD_SW per level */
+    int nsteps[4];      /* n_j: steps of level j per step of level j+1;
+                           nsteps[nlevels-1] = steps per trajectory */
+    int level_gauge;    /* level of S_G, -1 to leave the term out */
+    int level_w1;       /* level of |W1^-1 phi1|^2, or -1 */
+    int level_schur;    /* level of |R^-1 phi2|^2, or -1 */
+    int pf_init;        /* 0: heatbath phi = W eta; 1: phi = eta directly */
+    int roll;           /* 1: shift U along x0 by a random amount after */
+    int metropolis;     /* 1: accept/reject on dH; 0: always accept */
+    int precision;      /* LQCD_PREC_* for every solve */
+    double tol;         /* relative residual of every solve */
+    int max_iter;
+} lqcd_hmc_params;
+
+typedef struct {
+    double dH, H0, H1;
+    double plaq;        /* average Re tr P / 3 of the field returned */
+    double u;           /* Metropolis uniform */
+    int accepted;
+    int shift;          /* x0 roll applied */
+    int64_t solver_iters; /* inner Krylov iterations, whole trajectory */
+    int n_solves;
+    int n_force;        /* force evaluations */
+    int64_t site_iters; /* sum over solves of inner iterations x even sites
+                           of the system (each is four half-lattice hopping
+                           site updates) */
+} lqcd_hmc_result;
+
+/* One HMC trajectory (Sec. 2): heatbath (momenta p^a ~ N(0,1), eta ~
+ * exp(-|eta|^2)), phi1 = W1 eta1, phi2 = R eta2, molecular dynamics
+ * T_{X,top}(dt_top)^{n_top} with the recursive LF / SW levels of eqs.
+ * (5)-(7), Metropolis on dH, then the x0 shift of the configuration.
+ * U: device gauge field, overwritten with the field after the trajectory.
+ * P0 / eta1 / eta2: optional device inputs (momenta, full spinor,
+ * boundary field) replacing the Philox draws of (seed, traj); NULL draws
+ * them.  res: host.  Synchronous. */
+int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_t seed,
+                        uint32_t traj, const double* P0, const double* eta1,
+                        const double* eta2, lqcd_hmc_result* res);
+
+/* Molecular dynamics only: integrates (U, P) in place (device buffers, gauge
+ * and momenta layouts) for fixed phi1 (full spinor) / phi2 (boundary
+ * field); either may be NULL when its term is left out.  Synchronous. */
+int lqcd_md(lqcd_t h, double* U, double* P, const double* phi1, const double* phi2,
+            const lqcd_hmc_params* prm);
+
+/* Kernel timing with CUDA events on the handle's stream.  kernel ids:
+ * 0 hopping sweep, 1 persistent solver, 2 force, 3 gauge force / update,
+ * 4 layout / BLAS-1.  enable: 0 off, 1 all ids, otherwise a bit mask
+ * (1 << id) of the ids to time.  lqcd_profile_read returns, per id, the launches,
+ * the summed device time (ms) and the summed algorithmic DRAM bytes of
+ * the launches recorded since the last reset (synchronises the stream). */
+int lqcd_profile_enable(lqcd_t h, int enable);
+int lqcd_profile_reset(lqcd_t h);
+int lqcd_profile_read(lqcd_t h, int kernel_id, int64_t* launches, double* ms, double* bytes);
+
+/* Number of kernels this handle has launched since lqcd_create (host
+ * counter; *count is a host int64). */
+int lqcd_launch_count(lqcd_t h, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,830 @@
+// lqcd_api.cu -- handle, composite operators and the extern "C" entry
+// points declared in include/lqcd.h.
+//
+// Composite operators on internal double full-lattice fields:
+//   W1^-1 / M^-1  : even-odd reduction around the persistent batched solver
+//                   b_e' = b_e + kappa H_eo b_o,  solve (1 - k^2 H_eo H_oe) x_e = b_e',
+//                   x_o = b_o + kappa H_oe x_e;  adjoints via gamma5 (W^dag = g5 W g5)
+//   R      = E (1 - C A^-1 B D^-1) E^dag,  C, B = -kappa H_cross  (block LU of eq. (2))
+//   R^-1   = E D (M^-1)_bb E^dag,          R^-dag = E (M^-dag)_bb D^dag E^dag
+//   dS_R   = 2 Re <eta~, dD psi> - 2 Re <chi, dM psi> with psi = M^-1 E^dag phi,
+//            eta~ = E^dag E D psi_b (so S_R = |eta~|^2), chi = M^-dag D^dag eta~
+//   dS_W1  = -2 Re <xi, dW1 eta>, eta = W1^-1 phi, xi = W1^-dag eta
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lqcd_common.cuh"
+
+int reduction_blocks();
+int bnd_sub(lqcd_ctx* h, double* out, const double* in, int n);
+
+namespace {
+
+enum { F_T1 = 0, F_T2, F_A, F_B, F_C, F_D, F_E, F_G, F_PHI1, F_ETA1, NFIELD };
+
+inline double2* fld(lqcd_ctx* h, int k) { return h->f64[k]; }
+
+int nbnd_of(const Geo& g) { return (g.nb / 2) * 2 * g.V3 * 6; }
+
+bool prec_ok(int p) { return p == LQCD_PREC_F64 || p == LQCD_PREC_F32 || p == LQCD_PREC_F16; }
+
+SpinorF none()
+{
+    SpinorF f;
+    f.v = nullptr;
+    f.nrm = nullptr;
+    f.N = 0;
+    return f;
+}
+
+// full-lattice out = a x + c H_mode in on the output slabs of `colour`
+int hop_full(lqcd_ctx* h, int mode, int dag, int colour, double2* out, const double2* in, double a,
+             const double2* x, double c)
+{
+    const int Vh = h->g.Vh;
+    for (int p = 0; p < 2; ++p) {
+        SpinorF xo = x ? sp64((double2*)x, p, Vh) : none();
+        LQ_TRY(hop_sweep(h, PREC64, mode, dag, p, colour, sp64(out, p, Vh), sp64((double2*)in, 1 - p, Vh), a, xo, c));
+    }
+    if (colour >= 0) LQ_TRY(keep_colour(h, out, colour));
+    return LQCD_OK;
+}
+
+// x = W^-1 b (block: W1 on the slabs of `colour`; global: M).  x, b full
+// double fields, b is not modified, x must not alias b.
+int solve_full(lqcd_ctx* h, int mode, int colour, int dagger, int prec, double kappa, double2* x,
+               const double2* b, double tol, int max_iter, int* iters, double* resid)
+{
+    const int Vh = h->g.Vh;
+    const double2* bb = b;
+    if (dagger) {
+        LQ_TRY(gamma5_full(h, fld(h, F_T1), b));
+        bb = fld(h, F_T1);
+    }
+    const int col = mode == MODE_ALL ? -1 : colour;
+    // b_e' = b_e + kappa H_eo b_o
+    LQ_TRY(hop_sweep(h, PREC64, mode, 0, 0, col, sp64(fld(h, F_T2), 0, Vh), sp64((double2*)bb, 1, Vh), 1.0,
+                     sp64((double2*)bb, 0, Vh), kappa));
+    LQ_TRY(eo_solve(h, mode, col, prec, kappa, x, fld(h, F_T2), tol, max_iter, iters, resid));
+    // x_o = b_o + kappa H_oe x_e
+    LQ_TRY(hop_sweep(h, PREC64, mode, 0, 1, col, sp64(x, 1, Vh), sp64(x, 0, Vh), 1.0, sp64((double2*)bb, 1, Vh),
+                     kappa));
+    if (col >= 0) LQ_TRY(keep_colour(h, x, col));
+    if (dagger) LQ_TRY(gamma5_full(h, x, x));
+    return LQCD_OK;
+}
+
+struct SolveCfg {
+    int prec;
+    double tol;
+    int max_iter;
+};
+
+// R, R^dag, R^-1, R^-dag on boundary coordinates (device doubles)
+int schur_op(lqcd_ctx* h, double* out, const double* in, double kappa, int op, const SolveCfg& c)
+{
+    double2 *A = fld(h, F_A), *B = fld(h, F_B), *C = fld(h, F_C), *D = fld(h, F_D), *E = fld(h, F_E);
+    const int nb2 = 2 * nbnd_of(h->g);
+    LQ_TRY(embed_boundary(h, A, in));
+    if (op == LQCD_SCHUR_R) {
+        LQ_TRY(solve_full(h, MODE_INTRA, 1, 0, c.prec, kappa, B, A, c.tol, c.max_iter, nullptr, nullptr));
+        LQ_TRY(hop_full(h, MODE_CROSS, 0, 0, C, B, 0.0, nullptr, -kappa));
+        LQ_TRY(solve_full(h, MODE_INTRA, 0, 0, c.prec, kappa, D, C, c.tol, c.max_iter, nullptr, nullptr));
+        LQ_TRY(hop_full(h, MODE_CROSS, 0, 1, E, D, 0.0, nullptr, -kappa));
+        LQ_TRY(project_boundary(h, out, E));
+    } else if (op == LQCD_SCHUR_RDAG) {
+        LQ_TRY(hop_full(h, MODE_CROSS, 1, 0, C, A, 0.0, nullptr, -kappa));
+        LQ_TRY(solve_full(h, MODE_INTRA, 0, 1, c.prec, kappa, D, C, c.tol, c.max_iter, nullptr, nullptr));
+        LQ_TRY(hop_full(h, MODE_CROSS, 1, 1, E, D, 0.0, nullptr, -kappa));
+        LQ_TRY(solve_full(h, MODE_INTRA, 1, 1, c.prec, kappa, B, E, c.tol, c.max_iter, nullptr, nullptr));
+        LQ_TRY(project_boundary(h, out, B));
+    } else if (op == LQCD_SCHUR_RINV) {
+        LQ_TRY(solve_full(h, MODE_ALL, -1, 0, c.prec, kappa, B, A, c.tol, c.max_iter, nullptr, nullptr));
+        LQ_TRY(hop_full(h, MODE_INTRA, 0, 1, C, B, 1.0, B, -kappa));
+        LQ_TRY(project_boundary(h, out, C));
+        return LQCD_OK;
+    } else {
+        LQ_TRY(hop_full(h, MODE_INTRA, 1, 1, C, A, 1.0, A, -kappa));
+        LQ_TRY(solve_full(h, MODE_ALL, -1, 1, c.prec, kappa, B, C, c.tol, c.max_iter, nullptr, nullptr));
+        LQ_TRY(project_boundary(h, out, B));
+        return LQCD_OK;
+    }
+    // out = in - E(...)
+    return bnd_sub(h, out, in, nb2);
+}
+
+// F += coef * dS/dw for S = |W1^-1 phi|^2; *S_dev (device) receives S
+int pf_w1(lqcd_ctx* h, double* F, const double2* phi, double kappa, double coef, const SolveCfg& c,
+          double* S_dev)
+{
+    double2 *eta = fld(h, F_A), *xi = fld(h, F_B);
+    LQ_TRY(solve_full(h, MODE_INTRA, -1, 0, c.prec, kappa, eta, phi, c.tol, c.max_iter, nullptr, nullptr));
+    if (S_dev) LQ_TRY(norm2_dev(h, (const double*)eta, (int64_t)48 * h->g.Vh, S_dev));
+    if (!F) return LQCD_OK;
+    LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, xi, eta, c.tol, c.max_iter, nullptr, nullptr));
+    return force_bilinear(h, F, xi, eta, MODE_INTRA, kappa * coef, nullptr, nullptr, 0, 0.0);
+}
+
+// F += coef * dS/dw for S = |R^-1 phi|^2 (phi: device boundary coordinates)
+int pf_schur(lqcd_ctx* h, double* F, const double* phi, double kappa, double coef, const SolveCfg& c,
+             double* S_dev)
+{
+    double2 *A = fld(h, F_A), *psi = fld(h, F_B), *C = fld(h, F_C), *et = fld(h, F_D), *E = fld(h, F_E),
+            *chi = fld(h, F_G);
+    const int nbd = 2 * nbnd_of(h->g);
+    double* eta = h->bnd[1];
+    LQ_TRY(embed_boundary(h, A, phi));
+    LQ_TRY(solve_full(h, MODE_ALL, -1, 0, c.prec, kappa, psi, A, c.tol, c.max_iter, nullptr, nullptr));
+    LQ_TRY(hop_full(h, MODE_INTRA, 0, 1, C, psi, 1.0, psi, -kappa));
+    LQ_TRY(project_boundary(h, eta, C));
+    if (S_dev) LQ_TRY(norm2_dev(h, eta, nbd, S_dev));
+    if (!F) return LQCD_OK;
+    LQ_TRY(embed_boundary(h, et, eta));
+    LQ_TRY(hop_full(h, MODE_INTRA, 1, 1, E, et, 1.0, et, -kappa));
+    LQ_TRY(solve_full(h, MODE_ALL, -1, 1, c.prec, kappa, chi, E, c.tol, c.max_iter, nullptr, nullptr));
+    return force_bilinear(h, F, et, psi, MODE_INTRA, -kappa * coef, chi, psi, MODE_ALL, kappa * coef);
+}
+
+// ---------------------------------------------------------------------------
+// integrator schedule (Sec. 2, eqs. (5)-(7)); consecutive kicks of one level
+// act on the same field and are merged
+// ---------------------------------------------------------------------------
+struct Op {
+    int kind;  // 0: T_P(level), 1: T_U
+    int level;
+    double dt;
+};
+
+void push_p(std::vector<Op>& v, int level, double dt)
+{
+    if (!v.empty() && v.back().kind == 0 && v.back().level == level) {
+        v.back().dt += dt;
+        return;
+    }
+    v.push_back({0, level, dt});
+}
+
+void build_step(const lqcd_hmc_params& p, int j, double dt, std::vector<Op>& v)
+{
+    const double lam = p.lambda;
+    if (j == 0) {
+        if (p.scheme[0] == LQCD_LF) {
+            push_p(v, 0, 0.5 * dt);
+            v.push_back({1, 0, dt});
+            push_p(v, 0, 0.5 * dt);
+        } else {
+            push_p(v, 0, lam * dt);
+            v.push_back({1, 0, 0.5 * dt});
+            push_p(v, 0, (1.0 - 2.0 * lam) * dt);
+            v.push_back({1, 0, 0.5 * dt});
+            push_p(v, 0, lam * dt);
+        }
+        return;
+    }
+    const int n = p.nsteps[j - 1];
+    const double di = dt / n;
+    if (p.scheme[j] == LQCD_LF) {
+        push_p(v, j, 0.5 * dt);
+        for (int i = 0; i < n; ++i) build_step(p, j - 1, di, v);
+        push_p(v, j, 0.5 * dt);
+    } else {
+        push_p(v, j, lam * dt);
+        for (int i = 0; i < n / 2; ++i) build_step(p, j - 1, di, v);
+        push_p(v, j, (1.0 - 2.0 * lam) * dt);
+        for (int i = 0; i < n / 2; ++i) build_step(p, j - 1, di, v);
+        push_p(v, j, lam * dt);
+    }
+}
+
+int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
+{
+    if (!p || p->nlevels < 1 || p->nlevels > 4 || !(p->tau > 0) || !prec_ok(p->precision) || !(p->tol > 0)) {
+        h->err = "hmc params: bad nlevels / tau / precision / tol";
+        return LQCD_ERR_ARG;
+    }
+    for (int j = 0; j < p->nlevels; ++j) {
+        if (p->nsteps[j] < 1 || (p->scheme[j] != LQCD_LF && p->scheme[j] != LQCD_SW)) {
+            h->err = "hmc params: bad nsteps / scheme";
+            return LQCD_ERR_ARG;
+        }
+        if (j >= 1 && p->scheme[j] == LQCD_SW && (p->nsteps[j - 1] % 2)) {
+            h->err = "hmc params: an SW level needs an even number of inner steps";
+            return LQCD_ERR_ARG;
+        }
+    }
+    const int lv[3] = {p->level_gauge, p->level_w1, p->level_schur};
+    for (int k = 0; k < 3; ++k)
+        if (lv[k] < -1 || lv[k] >= p->nlevels) {
+            h->err = "hmc params: term level out of range";
+            return LQCD_ERR_ARG;
+        }
+    return LQCD_OK;
+}
+
+int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const double2* phi1, const double* phi2, int* nforce)
+{
+    std::vector<Op> ops;
+    const int top = p.nlevels - 1;
+    const double dt = p.tau / p.nsteps[top];
+    for (int i = 0; i < p.nsteps[top]; ++i) build_step(p, top, dt, ops);
+    SolveCfg c{p.precision, p.tol, p.max_iter};
+    for (const Op& o : ops) {
+        if (o.kind == 1) {
+            LQ_TRY(update_links(h, P, o.dt));
+            continue;
+        }
+        if (p.level_gauge == o.level) LQ_TRY(gauge_force_kick(h, P, -o.dt * p.beta / 6.0));
+        if (p.level_w1 == o.level) {
+            LQ_TRY(pf_w1(h, P, phi1, p.kappa, -o.dt, c, nullptr));
+            ++*nforce;
+        }
+        if (p.level_schur == o.level) {
+            LQ_TRY(pf_schur(h, P, phi2, p.kappa, -o.dt, c, nullptr));
+            ++*nforce;
+        }
+    }
+    return LQCD_OK;
+}
+
+// host Philox4x32-10 for the Metropolis uniform and the x0 shift
+void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t a = (uint64_t)0xD2511F53u * c[0], b = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t n0 = (uint32_t)(b >> 32) ^ c[1] ^ k0, n1 = (uint32_t)b;
+        const uint32_t n2 = (uint32_t)(a >> 32) ^ c[3] ^ k1, n3 = (uint32_t)a;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+}
+
+// the (up to) four energy terms: kinetic, gauge, W1, Schur -> red_out[base..base+3]
+int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const double2* phi1, const double* phi2, int base)
+{
+    SolveCfg c{p.precision, p.tol, p.max_iter};
+    LQ_TRY(kinetic_sum(h, h->P, h->red_out + base));
+    if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, h->red_out + base + 1));
+    if (p.level_w1 >= 0) LQ_TRY(pf_w1(h, nullptr, phi1, p.kappa, 0.0, c, h->red_out + base + 2));
+    if (p.level_schur >= 0) LQ_TRY(pf_schur(h, nullptr, phi2, p.kappa, 0.0, c, h->red_out + base + 3));
+    return LQCD_OK;
+}
+
+double combine(const lqcd_hmc_params& p, const double* e)
+{
+    double H = 0.5 * e[0];
+    if (p.level_gauge >= 0) H += -p.beta / 3.0 * e[1];
+    if (p.level_w1 >= 0) H += e[2];
+    if (p.level_schur >= 0) H += e[3];
+    return H;
+}
+
+}  // namespace
+
+// small elementwise helper for boundary vectors: out = in - out
+namespace {
+__global__ void k_bnd_sub(double* out, const double* in, int n)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = in[t] - out[t];
+}
+}  // namespace
+int bnd_sub(lqcd_ctx* h, double* out, const double* in, int n)
+{
+    k_bnd_sub<<<(n + 255) / 256, 256, 0, h->stream>>>(out, in, n);
+    h->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->err = std::string("bnd_sub: ") + cudaGetErrorString(e);
+        return LQCD_ERR_CUDA;
+    }
+    return LQCD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// views and profiling
+// ---------------------------------------------------------------------------
+GaugeF gauge_view(lqcd_ctx* h, int prec)
+{
+    GaugeF g;
+    g.Vh = h->g.Vh;
+    g.v = prec == PREC64 ? (const void*)h->U64 : prec == PREC32 ? (const void*)h->U32 : (const void*)h->U16;
+    return g;
+}
+
+void prof_begin(lqcd_ctx* h, int id, cudaEvent_t* a)
+{
+    *a = nullptr;
+    if (!(h->prof.on & (1u << id))) return;
+    if (h->prof.pool.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        h->prof.pool.push_back(e);
+    }
+    *a = h->prof.pool.back();
+    h->prof.pool.pop_back();
+    cudaEventRecord(*a, h->stream);
+}
+
+void prof_end(lqcd_ctx* h, int id, cudaEvent_t a, double bytes)
+{
+    if (!(h->prof.on & (1u << id)) || !a) return;
+    cudaEvent_t b;
+    if (h->prof.pool.empty()) {
+        if (cudaEventCreate(&b) != cudaSuccess) return;
+    } else {
+        b = h->prof.pool.back();
+        h->prof.pool.pop_back();
+    }
+    cudaEventRecord(b, h->stream);
+    h->prof.recs.push_back({a, b, id, bytes});
+}
+
+static void prof_flush(lqcd_ctx* h)
+{
+    if (h->prof.recs.empty()) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto& r : h->prof.recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        h->prof.launches[r.id] += 1;
+        h->prof.ms[r.id] += ms;
+        h->prof.bytes[r.id] += r.bytes;
+        h->prof.pool.push_back(r.a);
+        h->prof.pool.push_back(r.b);
+    }
+    h->prof.recs.clear();
+}
+
+// ---------------------------------------------------------------------------
+// extern "C" entry points
+// ---------------------------------------------------------------------------
+#define CHECK_H(h)                          \
+    do {                                    \
+        if (!(h)) return LQCD_ERR_ARG;      \
+    } while (0)
+#define NEED_GAUGE(h)                                         \
+    do {                                                      \
+        if (!(h)->have_gauge) {                               \
+            (h)->err = "no gauge field set (lqcd_set_gauge)"; \
+            return LQCD_ERR_STATE;                            \
+        }                                                     \
+    } while (0)
+#define NEED(cond, msg)               \
+    do {                              \
+        if (!(cond)) {                \
+            h->err = (msg);           \
+            return LQCD_ERR_ARG;      \
+        }                             \
+    } while (0)
+
+extern "C" {
+
+int lqcd_create(lqcd_t* out, const int L[4], int l0, int bc_t, void* stream)
+{
+    if (!out || !L) return LQCD_ERR_ARG;
+    *out = nullptr;
+    for (int mu = 0; mu < 4; ++mu)
+        if (L[mu] < 2 || (L[mu] & 1)) return LQCD_ERR_GEOM;
+    if (l0 < 1 || L[0] % (2 * l0)) return LQCD_ERR_GEOM;
+    if (bc_t != 1 && bc_t != -1) return LQCD_ERR_ARG;
+    const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    if (32 * V >= ((int64_t)1 << 31)) return LQCD_ERR_GEOM;
+    lqcd_ctx* h = new lqcd_ctx();
+    Geo& g = h->g;
+    for (int mu = 0; mu < 4; ++mu) g.L[mu] = L[mu];
+    g.V = (int)V;
+    g.Vh = g.V / 2;
+    g.V3 = L[1] * L[2] * L[3];
+    g.l0 = l0;
+    g.nb = L[0] / l0;
+    g.bc_t = bc_t;
+    g.Sh = l0 * g.V3 / 2;
+    h->stream = (cudaStream_t)stream;
+    *out = h;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        h->err = "no CUDA device";
+        return LQCD_ERR_CUDA;
+    }
+    const size_t Vh = g.Vh;
+    LQ_CUDA(h, cudaMalloc(&h->U64, sizeof(double2) * 72 * Vh));
+    LQ_CUDA(h, cudaMalloc(&h->U64_save, sizeof(double2) * 72 * Vh));
+    LQ_CUDA(h, cudaMalloc(&h->U32, sizeof(float4) * 24 * Vh));
+    LQ_CUDA(h, cudaMalloc(&h->U16, sizeof(uint2) * 24 * Vh));
+    h->f64.assign(NFIELD, nullptr);
+    for (int k = 0; k < NFIELD; ++k) LQ_CUDA(h, cudaMalloc(&h->f64[k], sizeof(double2) * 24 * Vh));
+    LQ_CUDA(h, cudaMalloc(&h->P, sizeof(double) * 32 * (size_t)g.V));
+    LQ_CUDA(h, cudaMalloc(&h->F, sizeof(double) * 32 * (size_t)g.V));
+    const size_t nb2 = 2 * (size_t)nbnd_of(g);
+    for (int k = 0; k < 4; ++k) LQ_CUDA(h, cudaMalloc(&h->bnd[k], sizeof(double) * std::max<size_t>(nb2, 2)));
+    h->red_blocks = reduction_blocks();
+    LQ_CUDA(h, cudaMalloc(&h->red_part, sizeof(double) * h->red_blocks));
+    LQ_CUDA(h, cudaMalloc(&h->red_out, sizeof(double) * 16));
+    LQ_CUDA(h, cudaMallocHost(&h->red_host, sizeof(double) * 16));
+    LQ_CUDA(h, cudaMemsetAsync(h->red_out, 0, sizeof(double) * 16, h->stream));
+    return solver_init(h);
+}
+
+int lqcd_destroy(lqcd_t h)
+{
+    if (!h) return LQCD_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    solver_free(h);
+    cudaFree(h->U64);
+    cudaFree(h->U64_save);
+    cudaFree(h->U32);
+    cudaFree(h->U16);
+    for (double2* f : h->f64) cudaFree(f);
+    cudaFree(h->P);
+    cudaFree(h->F);
+    for (int k = 0; k < 4; ++k) cudaFree(h->bnd[k]);
+    cudaFree(h->red_part);
+    cudaFree(h->red_out);
+    cudaFreeHost(h->red_host);
+    for (auto& r : h->prof.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->prof.pool) cudaEventDestroy(e);
+    delete h;
+    return LQCD_OK;
+}
+
+const char* lqcd_last_error(lqcd_t h) { return h ? h->err.c_str() : "null handle"; }
+
+int lqcd_set_stream(lqcd_t h, void* stream)
+{
+    CHECK_H(h);
+    h->stream = (cudaStream_t)stream;
+    return LQCD_OK;
+}
+
+int lqcd_set_gauge(lqcd_t h, const double* U)
+{
+    CHECK_H(h);
+    NEED(U, "null gauge pointer");
+    LQ_TRY(pack_gauge(h, U));
+    h->have_gauge = true;
+    return LQCD_OK;
+}
+
+int lqcd_get_gauge(lqcd_t h, double* U)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(U, "null gauge pointer");
+    return unpack_gauge(h, U);
+}
+
+int lqcd_index_maps(lqcd_t h, int32_t* maps)
+{
+    CHECK_H(h);
+    NEED(maps, "null maps pointer");
+    return index_maps(h, maps);
+}
+
+int lqcd_dslash_eo(lqcd_t h, double* out, const double* in, double kappa, int parity, int dagger, int op,
+                   int precision)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(out && in, "null field pointer");
+    NEED(parity == 0 || parity == 1, "parity must be 0 or 1");
+    NEED(op == LQCD_OP_HOP || (op == LQCD_OP_MHAT && parity == 0), "op must be HOP, or MHAT with parity 0");
+    NEED(prec_ok(precision), "bad precision");
+    const int Vh = h->g.Vh;
+    double2 *A = fld(h, F_A), *B = fld(h, F_B);
+    const int pin = op == LQCD_OP_HOP ? 1 - parity : 0;
+    LQ_TRY(pack_spinor(h, A, in, pin, 1));
+    // low-precision work fields live in F_C / F_D (same byte size as double)
+    SpinorF src = sp64(A, pin, Vh), res = sp64(B, parity, Vh);
+    if (precision != LQCD_PREC_F64) {
+        auto lowview = [&](double2* buf, int par) {
+            SpinorF f;
+            f.v = (char*)buf + (size_t)par * 12 * Vh * sizeof(double2);
+            f.N = Vh;
+            f.nrm = precision == PREC16 ? (float*)((uint4*)f.v + (size_t)3 * Vh) : nullptr;
+            return f;
+        };
+        SpinorF ls = lowview(fld(h, F_C), pin), lr = lowview(fld(h, F_D), parity);
+        LQ_TRY(convert_spinor(h, ls, precision, src, PREC64, Vh));
+        if (op == LQCD_OP_HOP) {
+            LQ_TRY(hop_sweep(h, precision, MODE_ALL, dagger, parity, -1, lr, ls, 0.0, none(), 1.0));
+        } else {
+            SpinorF lt = lowview(fld(h, F_E), 1);
+            LQ_TRY(hop_sweep(h, precision, MODE_ALL, dagger, 1, -1, lt, ls, 0.0, none(), 1.0));
+            LQ_TRY(hop_sweep(h, precision, MODE_ALL, dagger, 0, -1, lr, lt, 1.0, ls, -kappa * kappa));
+        }
+        LQ_TRY(convert_spinor(h, res, PREC64, lr, precision, Vh));
+    } else if (op == LQCD_OP_HOP) {
+        LQ_TRY(hop_sweep(h, PREC64, MODE_ALL, dagger, parity, -1, res, src, 0.0, none(), 1.0));
+    } else {
+        SpinorF tt = sp64(fld(h, F_C), 1, Vh);
+        LQ_TRY(hop_sweep(h, PREC64, MODE_ALL, dagger, 1, -1, tt, src, 0.0, none(), 1.0));
+        LQ_TRY(hop_sweep(h, PREC64, MODE_ALL, dagger, 0, -1, res, tt, 1.0, src, -kappa * kappa));
+    }
+    return unpack_spinor(h, out, B, parity, 1);
+}
+
+int lqcd_block_dslash(lqcd_t h, double* out, const double* in, double kappa, int colour, int dagger, int precision)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(out && in, "null field pointer");
+    NEED(colour >= -1 && colour <= 1, "colour must be -1, 0 or 1");
+    NEED(prec_ok(precision), "bad precision");
+    const int Vh = h->g.Vh;
+    double2 *A = fld(h, F_A), *B = fld(h, F_B);
+    LQ_TRY(pack_spinor(h, A, in, 0, 2));
+    if (precision == LQCD_PREC_F64) {
+        LQ_TRY(hop_full(h, MODE_INTRA, dagger, colour, B, A, 1.0, A, -kappa));
+    } else {
+        auto lowview = [&](double2* buf, int par) {
+            SpinorF f;
+            f.v = (char*)buf + (size_t)par * 12 * Vh * sizeof(double2);
+            f.N = Vh;
+            f.nrm = precision == PREC16 ? (float*)((uint4*)f.v + (size_t)3 * Vh) : nullptr;
+            return f;
+        };
+        for (int p = 0; p < 2; ++p) LQ_TRY(convert_spinor(h, lowview(fld(h, F_C), p), precision, sp64(A, p, Vh), PREC64, Vh));
+        for (int p = 0; p < 2; ++p)
+            LQ_TRY(hop_sweep(h, precision, MODE_INTRA, dagger, p, colour, lowview(fld(h, F_D), p),
+                             lowview(fld(h, F_C), 1 - p), 1.0, lowview(fld(h, F_C), p), -kappa));
+        LQ_CUDA(h, cudaMemsetAsync(B, 0, sizeof(double2) * 24 * (size_t)Vh, h->stream));
+        for (int p = 0; p < 2; ++p) LQ_TRY(convert_spinor(h, sp64(B, p, Vh), PREC64, lowview(fld(h, F_D), p), precision, Vh));
+        if (colour >= 0) LQ_TRY(keep_colour(h, B, colour));
+    }
+    return unpack_spinor(h, out, B, 0, 2);
+}
+
+int lqcd_block_solve_batched(lqcd_t h, double* x, const double* b, double kappa, int colour, int dagger,
+                             int precision, double tol, int max_iter, int* iters_out, double* resid_out)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(x && b, "null field pointer");
+    NEED(colour >= -1 && colour <= 1, "colour must be -1, 0 or 1");
+    NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
+    double2 *A = fld(h, F_A), *B = fld(h, F_B);
+    LQ_TRY(pack_spinor(h, A, b, 0, 2));
+    const int nsys = colour < 0 ? h->g.nb : h->g.nb / 2;
+    std::vector<int> it(nsys, 0);
+    std::vector<double> rs(nsys, 0.0);
+    const int st = solve_full(h, MODE_INTRA, colour, dagger, precision, kappa, B, A, tol, max_iter, it.data(), rs.data());
+    if (iters_out || resid_out)
+        for (int k = 0; k < h->g.nb; ++k) {
+            if (iters_out) iters_out[k] = 0;
+            if (resid_out) resid_out[k] = 0.0;
+        }
+    for (int s = 0; s < nsys; ++s) {
+        const int slab = colour < 0 ? s : colour + 2 * s;
+        if (iters_out) iters_out[slab] = it[s];
+        if (resid_out) resid_out[slab] = rs[s];
+    }
+    LQ_TRY(st);
+    LQ_TRY(unpack_spinor(h, x, B, 0, 2));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LQCD_OK;
+}
+
+int lqcd_solve_wilson(lqcd_t h, double* x, const double* b, double kappa, int dagger, int precision, double tol,
+                      int max_iter, int* iters_out, double* resid_out)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(x && b, "null field pointer");
+    NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
+    double2 *A = fld(h, F_A), *B = fld(h, F_B);
+    LQ_TRY(pack_spinor(h, A, b, 0, 2));
+    int it = 0;
+    double rs = 0.0;
+    LQ_TRY(solve_full(h, MODE_ALL, -1, dagger, precision, kappa, B, A, tol, max_iter, &it, &rs));
+    if (iters_out) *iters_out = it;
+    if (resid_out) *resid_out = rs;
+    LQ_TRY(unpack_spinor(h, x, B, 0, 2));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LQCD_OK;
+}
+
+int lqcd_schur_apply(lqcd_t h, double* out, const double* in, double kappa, int op, int precision, double tol,
+                     int max_iter)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(out && in && out != in, "null or aliased boundary pointer");
+    NEED(op >= LQCD_SCHUR_R && op <= LQCD_SCHUR_RINVDAG, "bad Schur op");
+    NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
+    SolveCfg c{precision, tol, max_iter};
+    LQ_TRY(schur_op(h, out, in, kappa, op, c));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LQCD_OK;
+}
+
+int lqcd_pf_force(lqcd_t h, double* F, const double* phi, double kappa, int term, int precision, double tol,
+                  int max_iter, double* S_out)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(phi, "null phi");
+    NEED(term == LQCD_TERM_W1 || term == LQCD_TERM_SCHUR, "bad term");
+    NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
+    SolveCfg c{precision, tol, max_iter};
+    if (term == LQCD_TERM_W1) {
+        LQ_TRY(pack_spinor(h, fld(h, F_PHI1), phi, 0, 2));
+        LQ_TRY(pf_w1(h, F, fld(h, F_PHI1), kappa, 1.0, c, h->red_out));
+    } else {
+        LQ_TRY(pf_schur(h, F, phi, kappa, 1.0, c, h->red_out));
+    }
+    double S;
+    LQ_TRY(read_scalars(h, 1, &S));
+    if (S_out) *S_out = S;
+    return LQCD_OK;
+}
+
+int lqcd_gauge_force(lqcd_t h, double* F, double beta, double* S_out, double* plaq_out)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    if (F) LQ_TRY(gauge_force_kick(h, F, beta / 6.0));
+    LQ_TRY(plaquette_sum(h, h->red_out));
+    double s;
+    LQ_TRY(read_scalars(h, 1, &s));
+    if (S_out) *S_out = -beta / 3.0 * s;
+    if (plaq_out) *plaq_out = s / (18.0 * h->g.V);
+    return LQCD_OK;
+}
+
+int lqcd_rng_normals(lqcd_t h, double* out, int64_t n, uint64_t seed, uint32_t stream, uint32_t traj)
+{
+    CHECK_H(h);
+    NEED(out || n == 0, "null output");
+    NEED(n >= 0, "negative n");
+    return rng_normals(h, out, n, seed, stream, traj, 1.0);
+}
+
+int lqcd_md(lqcd_t h, double* U, double* P, const double* phi1, const double* phi2, const lqcd_hmc_params* prm)
+{
+    CHECK_H(h);
+    NEED(U && P, "null U / P");
+    LQ_TRY(check_params(h, prm));
+    NEED(prm->level_w1 < 0 || phi1, "phi1 needed for the W1 term");
+    NEED(prm->level_schur < 0 || phi2, "phi2 needed for the Schur term");
+    LQ_TRY(pack_gauge(h, U));
+    h->have_gauge = true;
+    if (prm->level_w1 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI1), phi1, 0, 2));
+    if (prm->level_schur >= 0)
+        LQ_CUDA(h, cudaMemcpyAsync(h->bnd[0], phi2, sizeof(double) * 2 * nbnd_of(h->g), cudaMemcpyDeviceToDevice,
+                                   h->stream));
+    int nf = 0;
+    LQ_TRY(do_md(h, *prm, P, fld(h, F_PHI1), h->bnd[0], &nf));
+    LQ_TRY(unpack_gauge(h, U));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LQCD_OK;
+}
+
+int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_t seed, uint32_t traj,
+                        const double* P0, const double* eta1, const double* eta2, lqcd_hmc_result* res)
+{
+    CHECK_H(h);
+    NEED(U && res, "null U / result");
+    LQ_TRY(check_params(h, prm));
+    const lqcd_hmc_params& p = *prm;
+    const Geo& g = h->g;
+    const int nbd = 2 * nbnd_of(g);
+    h->iter_count = 0;
+    h->site_iters = 0;
+    h->solve_count = 0;
+    LQ_TRY(pack_gauge(h, U));
+    h->have_gauge = true;
+    LQ_CUDA(h, cudaMemcpyAsync(h->U64_save, h->U64, sizeof(double2) * 72 * (size_t)g.Vh, cudaMemcpyDeviceToDevice,
+                               h->stream));
+    // heatbath: momenta N(0,1), pseudo-fermion noise exp(-|eta|^2)
+    if (P0)
+        LQ_CUDA(h, cudaMemcpyAsync(h->P, P0, sizeof(double) * 32 * (size_t)g.V, cudaMemcpyDeviceToDevice, h->stream));
+    else
+        LQ_TRY(rng_normals(h, h->P, (int64_t)32 * g.V, seed, 1, traj, 1.0));
+    SolveCfg c{p.precision, p.tol, p.max_iter};
+    double* e0 = h->red_out;  // [0..3] H0 terms, [4..7] H1 terms
+    LQ_CUDA(h, cudaMemsetAsync(h->red_out, 0, sizeof(double) * 16, h->stream));
+    LQ_TRY(kinetic_sum(h, h->P, e0));
+    if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, e0 + 1));
+    if (p.level_w1 >= 0) {
+        double2* et = fld(h, F_ETA1);
+        if (eta1) LQ_TRY(pack_spinor(h, et, eta1, 0, 2));
+        else LQ_TRY(rng_spinor(h, et, seed, 2, traj));
+        if (p.pf_init == 0) {
+            LQ_TRY(hop_full(h, MODE_INTRA, 0, -1, fld(h, F_PHI1), et, 1.0, et, -p.kappa));
+            LQ_TRY(norm2_dev(h, (const double*)et, (int64_t)48 * g.Vh, e0 + 2));
+        } else {
+            LQ_CUDA(h, cudaMemcpyAsync(fld(h, F_PHI1), et, sizeof(double2) * 24 * (size_t)g.Vh,
+                                       cudaMemcpyDeviceToDevice, h->stream));
+            LQ_TRY(pf_w1(h, nullptr, fld(h, F_PHI1), p.kappa, 0.0, c, e0 + 2));
+        }
+    }
+    if (p.level_schur >= 0) {
+        double* e2 = h->bnd[2];
+        if (eta2) LQ_CUDA(h, cudaMemcpyAsync(e2, eta2, sizeof(double) * nbd, cudaMemcpyDeviceToDevice, h->stream));
+        else LQ_TRY(rng_normals(h, e2, nbd, seed, 3, traj, sqrt(0.5)));
+        if (p.pf_init == 0) {
+            LQ_TRY(schur_op(h, h->bnd[0], e2, p.kappa, LQCD_SCHUR_R, c));
+            LQ_TRY(norm2_dev(h, e2, nbd, e0 + 3));
+        } else {
+            LQ_CUDA(h, cudaMemcpyAsync(h->bnd[0], e2, sizeof(double) * nbd, cudaMemcpyDeviceToDevice, h->stream));
+            LQ_TRY(pf_schur(h, nullptr, h->bnd[0], p.kappa, 0.0, c, e0 + 3));
+        }
+    }
+    int nforce = 0;
+    LQ_TRY(do_md(h, p, h->P, fld(h, F_PHI1), h->bnd[0], &nforce));
+    LQ_TRY(energy(h, p, fld(h, F_PHI1), h->bnd[0], 4));
+    double e[8];
+    LQ_TRY(read_scalars(h, 8, e));
+    const double H0 = combine(p, e), H1 = combine(p, e + 4);
+    const double dH = H1 - H0;
+    if (!isfinite(dH)) {
+        h->err = "non-finite energy";
+        return LQCD_ERR_NAN;
+    }
+    uint32_t w[4] = {0u, 0u, 4u, traj};
+    philox_host(w, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double u = ((double)(w[0] >> 5) * 67108864.0 + (double)(w[1] >> 6) + 0.5) / 9007199254740992.0;
+    int shift = (int)(((uint64_t)w[2] * (uint64_t)g.L[0]) >> 32);
+    int acc = 1;
+    if (p.metropolis) acc = (dH <= 0.0) || (u < exp(-dH));
+    if (!acc) {
+        LQ_CUDA(h, cudaMemcpyAsync(h->U64, h->U64_save, sizeof(double2) * 72 * (size_t)g.Vh, cudaMemcpyDeviceToDevice,
+                                   h->stream));
+        LQ_TRY(refresh_low_precision(h));
+    }
+    if (!p.roll) shift = 0;
+    if (shift) {
+        LQ_CUDA(h, cudaMemcpyAsync(h->U64_save, h->U64, sizeof(double2) * 72 * (size_t)g.Vh, cudaMemcpyDeviceToDevice,
+                                   h->stream));
+        LQ_TRY(roll_links(h, shift));
+    }
+    LQ_TRY(plaquette_sum(h, h->red_out + 8));
+    LQ_TRY(unpack_gauge(h, U));
+    double pl;
+    LQ_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    pl = h->red_host[0];
+    res->dH = dH;
+    res->H0 = H0;
+    res->H1 = H1;
+    res->plaq = pl / (18.0 * g.V);
+    res->u = u;
+    res->accepted = acc;
+    res->shift = shift;
+    res->solver_iters = h->iter_count;
+    res->site_iters = h->site_iters;
+    res->n_solves = h->solve_count;
+    res->n_force = nforce;
+    return LQCD_OK;
+}
+
+int lqcd_profile_enable(lqcd_t h, int enable)
+{
+    CHECK_H(h);
+    if (!enable) prof_flush(h);
+    h->prof.on = enable == 1 ? 0x1fu : (unsigned)enable & 0x1fu;
+    return LQCD_OK;
+}
+
+int lqcd_profile_reset(lqcd_t h)
+{
+    CHECK_H(h);
+    prof_flush(h);
+    for (int k = 0; k < 5; ++k) {
+        h->prof.launches[k] = 0;
+        h->prof.ms[k] = 0.0;
+        h->prof.bytes[k] = 0.0;
+    }
+    return LQCD_OK;
+}
+
+int lqcd_launch_count(lqcd_t h, int64_t* count)
+{
+    CHECK_H(h);
+    if (!count) return LQCD_ERR_ARG;
+    *count = h->launches;
+    return LQCD_OK;
+}
+
+int lqcd_profile_read(lqcd_t h, int id, int64_t* launches, double* ms, double* bytes)
+{
+    CHECK_H(h);
+    if (id < 0 || id > 4) return LQCD_ERR_ARG;
+    prof_flush(h);
+    if (launches) *launches = h->prof.launches[id];
+    if (ms) *ms = h->prof.ms[id];
+    if (bytes) *bytes = h->prof.bytes[id];
+    return LQCD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,578 @@
+// lqcd_common.cuh -- internal types and device helpers of the GB300 library.
+//
+// Internal field layouts (structure of arrays, one parity block after the
+// other, so that a warp reads 128-bit words of consecutive sites):
+//   double spinor  [parity][12 complex][Vh]   double2
+//   single spinor  [parity][6][Vh]            float4  (two complex each)
+//   half spinor    [parity][3][Vh]            uint4   (four complex each)
+//                  + [parity][Vh] float scale (max |component| of the site)
+//   double gauge   [mu][parity][9][Vh]        double2 (full 3x3)
+//   single gauge   [mu][parity][3][Vh]        float4  (rows 0 and 1)
+//   half gauge     [mu][parity][3][Vh]        uint2   (rows 0 and 1)
+// Row 2 of a compressed link is rebuilt as conj(row0 x row1) (SU(3)).
+// eo index of a site: lexicographic index / 2 (L3 is even).
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lqcd.h"
+
+#define LQ_HD __host__ __device__ __forceinline__
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+struct Geo {
+    int L[4];
+    int V, Vh, V3;
+    int l0, nb, bc_t;
+    int Sh;  // sites of one parity in one slab = l0 * V3 / 2
+};
+
+// coordinates of eo index i of parity p
+LQ_HD void eo_coords(const Geo& g, int p, int i, int x[4])
+{
+    int j = 2 * i;
+    x[3] = j % g.L[3];
+    int t = j / g.L[3];
+    x[2] = t % g.L[2];
+    t /= g.L[2];
+    x[1] = t % g.L[1];
+    x[0] = t / g.L[1];
+    x[3] += (x[0] + x[1] + x[2] + x[3] + p) & 1;
+}
+
+LQ_HD int lex_of(const Geo& g, const int x[4])
+{
+    return ((x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3];
+}
+
+// ---------------------------------------------------------------------------
+// complex arithmetic
+// ---------------------------------------------------------------------------
+template <class T>
+struct cx {
+    T re, im;
+};
+template <class T>
+LQ_HD cx<T> mk(T a, T b) { return cx<T>{a, b}; }
+template <class T>
+LQ_HD cx<T> operator+(cx<T> a, cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <class T>
+LQ_HD cx<T> operator-(cx<T> a, cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <class T>
+LQ_HD cx<T> operator-(cx<T> a) { return {-a.re, -a.im}; }
+template <class T>
+LQ_HD cx<T> operator*(cx<T> a, cx<T> b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+template <class T>
+LQ_HD cx<T> operator*(T s, cx<T> a) { return {s * a.re, s * a.im}; }
+template <class T>
+LQ_HD cx<T> conjx(cx<T> a) { return {a.re, -a.im}; }
+template <class T>
+LQ_HD cx<T> mul_i(cx<T> a) { return {-a.im, a.re}; }   // i a
+template <class T>
+LQ_HD cx<T> mul_mi(cx<T> a) { return {a.im, -a.re}; }  // -i a
+// a^* b
+template <class T>
+LQ_HD cx<T> cjmul(cx<T> a, cx<T> b) { return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re}; }
+
+template <class T>
+struct Spinor {
+    cx<T> c[4][3];
+};
+template <class T>
+struct HalfSp {
+    cx<T> c[2][3];
+};
+template <class T>
+struct Su3 {
+    cx<T> m[3][3];
+};
+
+template <class T>
+LQ_HD void complete_row2(Su3<T>& u)
+{
+    u.m[2][0] = conjx(u.m[0][1] * u.m[1][2] - u.m[0][2] * u.m[1][1]);
+    u.m[2][1] = conjx(u.m[0][2] * u.m[1][0] - u.m[0][0] * u.m[1][2]);
+    u.m[2][2] = conjx(u.m[0][0] * u.m[1][1] - u.m[0][1] * u.m[1][0]);
+}
+
+// w = u v  /  w = u^dag v  on the two spin rows of a half spinor
+template <class T>
+LQ_HD void su3_mul_half(const Su3<T>& u, const HalfSp<T>& h, HalfSp<T>& w)
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            w.c[s][i] = u.m[i][0] * h.c[s][0] + u.m[i][1] * h.c[s][1] + u.m[i][2] * h.c[s][2];
+}
+template <class T>
+LQ_HD void su3_dagmul_half(const Su3<T>& u, const HalfSp<T>& h, HalfSp<T>& w)
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            w.c[s][i] = cjmul(u.m[0][i], h.c[s][0]) + cjmul(u.m[1][i], h.c[s][1]) +
+                        cjmul(u.m[2][i], h.c[s][2]);
+}
+
+// ---------------------------------------------------------------------------
+// spin projection in the chiral basis (gamma_0 = [[0,-1],[-1,0]],
+// gamma_k = [[0,-i s_k],[i s_k,0]]).  (1 + sg*gamma_mu) psi has rank 2:
+//   upper half h = u + sg*Q_mu d, lower half = K_mu h,
+// u = (psi0, psi1), d = (psi2, psi3).  sg = -1 gives (1 - gamma_mu).
+// ---------------------------------------------------------------------------
+template <class T>
+LQ_HD void project(int mu, int sg, const Spinor<T>& p, HalfSp<T>& h)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        cx<T> a, b;
+        switch (mu) {
+            case 0:  // gamma_0 psi = (-d, -u): h = u - sg d
+                a = p.c[2][i]; b = p.c[3][i];
+                if (sg < 0) { h.c[0][i] = p.c[0][i] + a; h.c[1][i] = p.c[1][i] + b; }
+                else        { h.c[0][i] = p.c[0][i] - a; h.c[1][i] = p.c[1][i] - b; }
+                break;
+            case 1:  // gamma_1 psi upper = -i s1 d = (-i d1, -i d0): h = u - sg i s1 d
+                a = mul_i(p.c[3][i]); b = mul_i(p.c[2][i]);
+                if (sg < 0) { h.c[0][i] = p.c[0][i] + a; h.c[1][i] = p.c[1][i] + b; }
+                else        { h.c[0][i] = p.c[0][i] - a; h.c[1][i] = p.c[1][i] - b; }
+                break;
+            case 2:  // i s2 d = (d1, -d0)
+                a = p.c[3][i]; b = -p.c[2][i];
+                if (sg < 0) { h.c[0][i] = p.c[0][i] + a; h.c[1][i] = p.c[1][i] + b; }
+                else        { h.c[0][i] = p.c[0][i] - a; h.c[1][i] = p.c[1][i] - b; }
+                break;
+            default:  // i s3 d = (i d0, -i d1)
+                a = mul_i(p.c[2][i]); b = mul_mi(p.c[3][i]);
+                if (sg < 0) { h.c[0][i] = p.c[0][i] + a; h.c[1][i] = p.c[1][i] + b; }
+                else        { h.c[0][i] = p.c[0][i] - a; h.c[1][i] = p.c[1][i] - b; }
+                break;
+        }
+    }
+}
+
+// acc += (1 + sg*gamma_mu) psi rebuilt from its upper half w:
+//   lower half = sg * l with l = -w (mu = 0) or l = (i s_k) w (mu = k)
+template <class T>
+LQ_HD void accum_recon(int mu, int sg, const HalfSp<T>& w, Spinor<T>& acc)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        acc.c[0][i] = acc.c[0][i] + w.c[0][i];
+        acc.c[1][i] = acc.c[1][i] + w.c[1][i];
+        cx<T> l0, l1;
+        switch (mu) {
+            case 0: l0 = -w.c[0][i]; l1 = -w.c[1][i]; break;
+            case 1: l0 = mul_i(w.c[1][i]); l1 = mul_i(w.c[0][i]); break;
+            case 2: l0 = w.c[1][i]; l1 = -w.c[0][i]; break;
+            default: l0 = mul_i(w.c[0][i]); l1 = mul_mi(w.c[1][i]); break;
+        }
+        if (sg < 0) { acc.c[2][i] = acc.c[2][i] - l0; acc.c[3][i] = acc.c[3][i] - l1; }
+        else        { acc.c[2][i] = acc.c[2][i] + l0; acc.c[3][i] = acc.c[3][i] + l1; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// field views
+// ---------------------------------------------------------------------------
+enum { PREC64 = 0, PREC32 = 1, PREC16 = 2 };
+
+struct SpinorF {  // one parity block of a spinor field in some precision
+    void* v;      // double2* / float4* / uint4*
+    float* nrm;   // half only
+    int N;        // stride (sites of the parity block)
+};
+
+struct GaugeF {  // gauge field in some precision, [mu][parity][...][Vh]
+    const void* v;
+    int Vh;
+};
+
+template <int P>
+struct Real;
+template <>
+struct Real<PREC64> {
+    typedef double T;
+};
+template <>
+struct Real<PREC32> {
+    typedef float T;
+};
+template <>
+struct Real<PREC16> {
+    typedef float T;
+};
+
+// RO = true: the field is not written during the kernel (read-only path);
+// RO = false: plain coherent loads (fields updated inside a persistent kernel)
+template <class V, bool RO>
+__device__ __forceinline__ V ldv(const V* p)
+{
+    if (RO) return __ldg(p);
+    return *p;
+}
+
+template <int P, bool RO>
+struct SpIO;
+
+template <bool RO>
+struct SpIO<PREC64, RO> {
+    static __device__ __forceinline__ void load(const SpinorF& f, int i, Spinor<double>& s)
+    {
+        const double2* p = (const double2*)f.v;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 d = ldv<double2, RO>(p + (size_t)c * f.N + i);
+            s.c[c / 3][c % 3] = mk(d.x, d.y);
+        }
+    }
+    static __device__ __forceinline__ void store(const SpinorF& f, int i, const Spinor<double>& s)
+    {
+        double2* p = (double2*)f.v;
+#pragma unroll
+        for (int c = 0; c < 12; ++c)
+            p[(size_t)c * f.N + i] = make_double2(s.c[c / 3][c % 3].re, s.c[c / 3][c % 3].im);
+    }
+};
+
+template <bool RO>
+struct SpIO<PREC32, RO> {
+    static __device__ __forceinline__ void load(const SpinorF& f, int i, Spinor<float>& s)
+    {
+        const float4* p = (const float4*)f.v;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 d = ldv<float4, RO>(p + (size_t)k * f.N + i);
+            s.c[(2 * k) / 3][(2 * k) % 3] = mk(d.x, d.y);
+            s.c[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(d.z, d.w);
+        }
+    }
+    static __device__ __forceinline__ void store(const SpinorF& f, int i, const Spinor<float>& s)
+    {
+        float4* p = (float4*)f.v;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const cx<float> a = s.c[(2 * k) / 3][(2 * k) % 3];
+            const cx<float> b = s.c[(2 * k + 1) / 3][(2 * k + 1) % 3];
+            p[(size_t)k * f.N + i] = make_float4(a.re, a.im, b.re, b.im);
+        }
+    }
+};
+
+template <bool RO>
+struct SpIO<PREC16, RO> {
+    static __device__ __forceinline__ void load(const SpinorF& f, int i, Spinor<float>& s)
+    {
+        const uint4* p = (const uint4*)f.v;
+        const float sc = ldv<float, RO>(f.nrm + i);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 d = ldv<uint4, RO>(p + (size_t)k * f.N + i);
+            unsigned w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 v = __half22float2(*reinterpret_cast<__half2*>(&w[q]));
+                const int c = 4 * k + q;
+                s.c[c / 3][c % 3] = mk(v.x * sc, v.y * sc);
+            }
+        }
+    }
+    static __device__ __forceinline__ void store(const SpinorF& f, int i, const Spinor<float>& s)
+    {
+        float mx = 0.f;
+#pragma unroll
+        for (int c = 0; c < 12; ++c)
+            mx = fmaxf(mx, fmaxf(fabsf(s.c[c / 3][c % 3].re), fabsf(s.c[c / 3][c % 3].im)));
+        const float inv = mx > 0.f ? 1.0f / mx : 0.f;
+        uint4* p = (uint4*)f.v;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            unsigned w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = 4 * k + q;
+                __half2 hv = __floats2half2_rn(s.c[c / 3][c % 3].re * inv, s.c[c / 3][c % 3].im * inv);
+                w[q] = *reinterpret_cast<unsigned*>(&hv);
+            }
+            p[(size_t)k * f.N + i] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        f.nrm[i] = mx;
+    }
+};
+
+template <int P, bool RO = true>
+__device__ __forceinline__ void load_spinor(const SpinorF& f, int i, Spinor<typename Real<P>::T>& s)
+{
+    SpIO<P, RO>::load(f, i, s);
+}
+template <int P>
+__device__ __forceinline__ void store_spinor(const SpinorF& f, int i, const Spinor<typename Real<P>::T>& s)
+{
+    SpIO<P, true>::store(f, i, s);
+}
+
+// gauge links ----------------------------------------------------------------
+template <int P>
+__device__ __forceinline__ void load_link(const GaugeF& g, int mu, int par, int i, Su3<typename Real<P>::T>& u);
+
+template <>
+__device__ __forceinline__ void load_link<PREC64>(const GaugeF& g, int mu, int par, int i, Su3<double>& u)
+{
+    const double2* p = (const double2*)g.v + (size_t)(mu * 2 + par) * 9 * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        double2 d = __ldg(p + (size_t)k * g.Vh + i);
+        u.m[k / 3][k % 3] = mk(d.x, d.y);
+    }
+}
+template <>
+__device__ __forceinline__ void load_link<PREC32>(const GaugeF& g, int mu, int par, int i, Su3<float>& u)
+{
+    const float4* p = (const float4*)g.v + (size_t)(mu * 2 + par) * 3 * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float4 d = __ldg(p + (size_t)k * g.Vh + i);
+        u.m[(2 * k) / 3][(2 * k) % 3] = mk(d.x, d.y);
+        u.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(d.z, d.w);
+    }
+    complete_row2(u);
+}
+template <>
+__device__ __forceinline__ void load_link<PREC16>(const GaugeF& g, int mu, int par, int i, Su3<float>& u)
+{
+    const uint2* p = (const uint2*)g.v + (size_t)(mu * 2 + par) * 3 * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint2 d = __ldg(p + (size_t)k * g.Vh + i);
+        float2 a = __half22float2(*reinterpret_cast<__half2*>(&d.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2*>(&d.y));
+        u.m[(2 * k) / 3][(2 * k) % 3] = mk(a.x, a.y);
+        u.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(b.x, b.y);
+    }
+    complete_row2(u);
+}
+
+// ---------------------------------------------------------------------------
+// the hopping term at one output site
+//   mode 0: all hops (x0 wrap carries bc_t)
+//   mode 1: hops inside one slab only (W1)
+//   mode 2: hops between different slabs only (blocks B, C of M)
+// dag = 1 gives H^dag (projectors swapped).  acc is overwritten.
+// ---------------------------------------------------------------------------
+enum { MODE_ALL = 0, MODE_INTRA = 1, MODE_CROSS = 2 };
+
+template <int P, bool RO = true>
+__device__ __forceinline__ void hop_site(const Geo& g, int mode, int dag, int pout, int i,
+                                         const SpinorF& in, const GaugeF& U,
+                                         Spinor<typename Real<P>::T>& acc)
+{
+    typedef typename Real<P>::T T;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc.c[s][c] = mk(T(0), T(0));
+    int x[4];
+    eo_coords(g, pout, i, x);
+    const int lex = lex_of(g, x);
+    int stride = 1;
+    const int pin = 1 - pout;
+#pragma unroll
+    for (int mu = 3; mu >= 0; --mu) {
+        // forward hop x -> x + mu
+        {
+            int nl = lex + stride;
+            bool wrap = (x[mu] == g.L[mu] - 1);
+            if (wrap) nl -= g.L[mu] * stride;
+            bool use = true;
+            if (mu == 0 && mode != MODE_ALL) {
+                bool cross = ((x[0] + 1) % g.l0) == 0;
+                use = (mode == MODE_INTRA) ? !cross : cross;
+            } else if (mu != 0 && mode == MODE_CROSS) {
+                use = false;
+            }
+            if (use) {
+                Spinor<T> ps;
+                load_spinor<P, RO>(in, nl >> 1, ps);
+                Su3<T> u;
+                load_link<P>(U, mu, pout, i, u);
+                HalfSp<T> h, w;
+                const int sg = dag ? +1 : -1;
+                project(mu, sg, ps, h);
+                su3_mul_half(u, h, w);
+                if (mu == 0 && wrap && g.bc_t < 0) {
+#pragma unroll
+                    for (int s = 0; s < 2; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) w.c[s][c] = -w.c[s][c];
+                }
+                accum_recon(mu, sg, w, acc);
+            }
+        }
+        // backward hop x -> x - mu
+        {
+            int nl = lex - stride;
+            bool wrap = (x[mu] == 0);
+            if (wrap) nl += g.L[mu] * stride;
+            bool use = true;
+            if (mu == 0 && mode != MODE_ALL) {
+                bool cross = (x[0] % g.l0) == 0;
+                use = (mode == MODE_INTRA) ? !cross : cross;
+            } else if (mu != 0 && mode == MODE_CROSS) {
+                use = false;
+            }
+            if (use) {
+                Spinor<T> ps;
+                load_spinor<P, RO>(in, nl >> 1, ps);
+                Su3<T> u;
+                load_link<P>(U, mu, pin, nl >> 1, u);
+                HalfSp<T> h, w;
+                const int sg = dag ? -1 : +1;
+                project(mu, sg, ps, h);
+                su3_dagmul_half(u, h, w);
+                if (mu == 0 && wrap && g.bc_t < 0) {
+#pragma unroll
+                    for (int s = 0; s < 2; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) w.c[s][c] = -w.c[s][c];
+                }
+                accum_recon(mu, sg, w, acc);
+            }
+        }
+        stride *= g.L[mu];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Profiler {
+    unsigned on = 0;  // bit mask of the kernel ids being timed
+    struct Rec {
+        cudaEvent_t a, b;
+        int id;
+        double bytes;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[5] = {0, 0, 0, 0, 0};
+    double ms[5] = {0, 0, 0, 0, 0};
+    double bytes[5] = {0, 0, 0, 0, 0};
+};
+
+struct Work;  // solver workspace (lqcd_solver.cu)
+
+struct lqcd_ctx {
+    Geo g;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    std::string err;
+    bool have_gauge = false;
+    // internal gauge copies
+    double2* U64 = nullptr;  // [4][2][9][Vh]
+    float4* U32 = nullptr;   // [4][2][3][Vh]
+    uint2* U16 = nullptr;    // [4][2][3][Vh]
+    double2* U64_save = nullptr;
+    // double full-lattice spinor scratch fields [2][12][Vh]
+    std::vector<double2*> f64;
+    // momenta / force scratch [4][V][8]
+    double* P = nullptr;
+    double* F = nullptr;
+    // boundary scratch
+    double* bnd[4] = {nullptr, nullptr, nullptr, nullptr};
+    // reductions
+    double* red_part = nullptr;  // partial sums
+    double* red_out = nullptr;   // device scalars
+    double* red_host = nullptr;  // pinned host mirror
+    int red_blocks = 0;
+    Work* work = nullptr;
+    Profiler prof;
+    int64_t launches = 0;    // kernels launched by this handle
+    int64_t iter_count = 0;  // inner iterations since reset (trajectory stats)
+    int64_t site_iters = 0;  // inner iterations x even sites of the system
+    int solve_count = 0;
+};
+
+// error helpers
+#define LQ_CUDA(h, call)                                                                    \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            return LQCD_ERR_CUDA;                                                           \
+        }                                                                                   \
+    } while (0)
+
+#define LQ_TRY(x)                 \
+    do {                          \
+        int st_ = (x);            \
+        if (st_ != LQCD_OK) return st_; \
+    } while (0)
+
+// profiling hooks
+void prof_begin(lqcd_ctx* h, int id, cudaEvent_t* a);
+void prof_end(lqcd_ctx* h, int id, cudaEvent_t a, double bytes);
+
+// ---------------------------------------------------------------------------
+// internal host API shared by the translation units
+// ---------------------------------------------------------------------------
+SpinorF sp_view(const void* base, int prec, int parity, int Vh, float* nrm_base);
+inline SpinorF sp64(double2* base, int parity, int Vh)
+{
+    SpinorF f;
+    f.v = base + (size_t)parity * 12 * Vh;
+    f.nrm = nullptr;
+    f.N = Vh;
+    return f;
+}
+GaugeF gauge_view(lqcd_ctx* h, int prec);
+
+// fields.cu
+int pack_spinor(lqcd_ctx* h, double2* dst, const double* abi, int parity_first, int nparity);
+int unpack_spinor(lqcd_ctx* h, double* abi, const double2* src, int parity_first, int nparity);
+int pack_gauge(lqcd_ctx* h, const double* abi);
+int unpack_gauge(lqcd_ctx* h, double* abi);
+int convert_spinor(lqcd_ctx* h, SpinorF dst, int dprec, SpinorF src, int sprec, int n);
+int index_maps(lqcd_ctx* h, int32_t* maps);
+int embed_boundary(lqcd_ctx* h, double2* full, const double* coords);
+int project_boundary(lqcd_ctx* h, double* coords, const double2* full);
+int axpby_full(lqcd_ctx* h, double2* y, double a, const double2* x, double b, int colour);
+int gamma5_full(lqcd_ctx* h, double2* y, const double2* x);
+int keep_colour(lqcd_ctx* h, double2* y, int colour);
+int norm2_dev(lqcd_ctx* h, const double* x, int64_t n, double* dev_out);
+int rng_normals(lqcd_ctx* h, double* out, int64_t n, uint64_t seed, uint32_t stream, uint32_t traj,
+                double scale);
+int rng_spinor(lqcd_ctx* h, double2* full, uint64_t seed, uint32_t stream, uint32_t traj);
+int read_scalars(lqcd_ctx* h, int n, double* host);
+
+// dslash.cu
+// out(p_out) = a * x(p_out) + c * H_{p_out,1-p_out} in(1-p_out) on the output
+// sites of slabs with the given colour (-1: all); x may be null (a ignored)
+int hop_sweep(lqcd_ctx* h, int prec, int mode, int dag, int pout, int colour, SpinorF out,
+              SpinorF in, double a, SpinorF x, double c);
+
+// solver.cu
+int solver_init(lqcd_ctx* h);
+void solver_free(lqcd_ctx* h);
+// even-odd reduced solve (1 - kappa^2 H_eo H_oe) x_e = b_e on the slabs of
+// `colour` (block mode) or globally; x_e, b_e: double parity-0 views
+int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e,
+             const double2* b_e, double tol, int max_iter, int* iters_sys, double* resid_sys);
+
+// force.cu
+int force_bilinear(lqcd_ctx* h, double* F, const double2* a1, const double2* b1, int mask1,
+                   double coef1, const double2* a2, const double2* b2, int mask2, double coef2);
+int gauge_force_kick(lqcd_ctx* h, double* F, double coef);
+int plaquette_sum(lqcd_ctx* h, double* dev_out);
+int update_links(lqcd_ctx* h, const double* P, double dt);
+int roll_links(lqcd_ctx* h, int shift);
+int kinetic_sum(lqcd_ctx* h, const double* P, double* dev_out);
+int refresh_low_precision(lqcd_ctx* h);

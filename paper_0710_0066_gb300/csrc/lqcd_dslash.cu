@@ -1,0 +1,83 @@
+// lqcd_dslash.cu -- the hopping term of eq. (2) as one sweep over the output
+// sites of one parity: out = a x + c H_{p,1-p} in, optionally restricted to
+// the hops inside one x0-slab (W1) or between slabs (the blocks B, C of M),
+// and to the output sites of the slabs of one colour.
+//
+// One thread per output site.  Every neighbour is read as a full spinor
+// with 128-bit (single: float4, half: uint4) or 2x64-bit (double2) loads of
+// consecutive sites, spin-projected to a half spinor, multiplied by the
+// (rebuilt) link and accumulated; the output is written once.
+#include "lqcd_common.cuh"
+
+namespace {
+
+constexpr int HOP_BS = 128;
+
+template <int P>
+__global__ void __launch_bounds__(HOP_BS) k_hop(Geo g, int mode, int dag, int pout, int colour,
+                                               SpinorF out, SpinorF in, GaugeF U, double a, SpinorF x,
+                                               double c, int nsites)
+{
+    typedef typename Real<P>::T T;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nsites) return;
+    int i = t;
+    if (colour >= 0) {
+        const int k = t / g.Sh;
+        i = (colour + 2 * k) * g.Sh + (t - k * g.Sh);
+    }
+    Spinor<T> acc;
+    hop_site<P>(g, mode, dag, pout, i, in, U, acc);
+    const T cc = (T)c;
+    if (x.v) {
+        Spinor<T> xs;
+        load_spinor<P>(x, i, xs);
+        const T aa = (T)a;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc.c[s][q] = aa * xs.c[s][q] + cc * acc.c[s][q];
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc.c[s][q] = cc * acc.c[s][q];
+    }
+    store_spinor<P>(out, i, acc);
+}
+
+}  // namespace
+
+// algorithmic DRAM bytes of one output site: the output, the input site and
+// the eight links, each moved once (neighbour spinors reused from cache)
+double hop_site_bytes(int prec, bool with_x)
+{
+    const double sp = prec == PREC64 ? 192.0 : prec == PREC32 ? 96.0 : 52.0;
+    const double lk = prec == PREC64 ? 144.0 : prec == PREC32 ? 48.0 : 24.0;
+    return 2.0 * sp + 8.0 * lk + (with_x ? sp : 0.0);
+}
+
+int hop_sweep(lqcd_ctx* h, int prec, int mode, int dag, int pout, int colour, SpinorF out, SpinorF in,
+              double a, SpinorF x, double c)
+{
+    const Geo& g = h->g;
+    const int nsites = colour < 0 ? g.Vh : (g.nb / 2) * g.Sh;
+    const int nb = (nsites + HOP_BS - 1) / HOP_BS;
+    GaugeF U = gauge_view(h, prec);
+    cudaEvent_t ev;
+    prof_begin(h, 0, &ev);
+    if (prec == PREC64)
+        k_hop<PREC64><<<nb, HOP_BS, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+    else if (prec == PREC32)
+        k_hop<PREC32><<<nb, HOP_BS, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+    else
+        k_hop<PREC16><<<nb, HOP_BS, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+    h->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->err = std::string("hop kernel: ") + cudaGetErrorString(e);
+        return LQCD_ERR_CUDA;
+    }
+    prof_end(h, 0, ev, hop_site_bytes(prec, x.v != nullptr) * nsites);
+    return LQCD_OK;
+}

@@ -1,0 +1,529 @@
+// lqcd_force.cu -- link forces, gauge action, link update and x0 shift.
+//
+// Pseudo-fermion forces.  For a link U_mu(x) moved along T^a,
+// delta U = i w T^a U, and the derivative of 2 Re <a, H b> is
+//   2 Re[ a(x)^dag (1-g_mu) iT^a U b(x+mu) + a(x+mu)^dag (1+g_mu) (iT^a U)^dag b(x) ]
+// = -2 Im tr(T^a Y),   Y = U X1 - X2 U^dag,
+//   X1 = sum_i h_i[(1-g_mu) b(x+mu)] h_i[(1-g_mu) a(x)]^dag,
+//   X2 = sum_i h_i[(1+g_mu) b(x)]   h_i[(1+g_mu) a(x+mu)]^dag,
+// with h the two-spin upper half of the projected spinor (the lower half is
+// a unitary image of it, so the four-spin trace equals the two-spin one).
+// All of this runs in double precision on the double solution vectors.
+#include <math.h>
+
+#include "lqcd_common.cuh"
+
+namespace {
+
+constexpr int BS = 128;
+constexpr double INV_SQRT3 = 0.57735026918962576451;
+
+__device__ __forceinline__ void site_at(const Geo& g, const int x[4], int& par, int& i)
+{
+    par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    i = lex_of(g, x) >> 1;
+}
+
+__device__ __forceinline__ void shifted(const Geo& g, const int x[4], int mu, int d, int y[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) y[k] = x[k];
+    y[mu] += d;
+    if (y[mu] >= g.L[mu]) y[mu] -= g.L[mu];
+    if (y[mu] < 0) y[mu] += g.L[mu];
+}
+
+// 2 Im tr(T^a Y) for the eight Gell-Mann generators T^a = lambda^a / 2
+__device__ __forceinline__ void lie_im2(const Su3<double>& Y, double f[8])
+{
+    f[0] = Y.m[1][0].im + Y.m[0][1].im;
+    f[1] = Y.m[0][1].re - Y.m[1][0].re;
+    f[2] = Y.m[0][0].im - Y.m[1][1].im;
+    f[3] = Y.m[2][0].im + Y.m[0][2].im;
+    f[4] = Y.m[0][2].re - Y.m[2][0].re;
+    f[5] = Y.m[2][1].im + Y.m[1][2].im;
+    f[6] = Y.m[1][2].re - Y.m[2][1].re;
+    f[7] = (Y.m[0][0].im + Y.m[1][1].im - 2.0 * Y.m[2][2].im) * INV_SQRT3;
+}
+
+__device__ __forceinline__ void su3_mul(const Su3<double>& a, const Su3<double>& b, Su3<double>& c)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) c.m[i][j] = a.m[i][0] * b.m[0][j] + a.m[i][1] * b.m[1][j] + a.m[i][2] * b.m[2][j];
+}
+// c = a b^dag
+__device__ __forceinline__ void su3_mul_nd(const Su3<double>& a, const Su3<double>& b, Su3<double>& c)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            c.m[i][j] = a.m[i][0] * conjx(b.m[j][0]) + a.m[i][1] * conjx(b.m[j][1]) + a.m[i][2] * conjx(b.m[j][2]);
+}
+// c = a^dag b
+__device__ __forceinline__ void su3_mul_dn(const Su3<double>& a, const Su3<double>& b, Su3<double>& c)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            c.m[i][j] = cjmul(a.m[0][i], b.m[0][j]) + cjmul(a.m[1][i], b.m[1][j]) + cjmul(a.m[2][i], b.m[2][j]);
+}
+
+__device__ __forceinline__ void outer_acc(const HalfSp<double>& hb, const HalfSp<double>& ha, Su3<double>& X)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            X.m[i][j] = X.m[i][j] + hb.c[0][i] * conjx(ha.c[0][j]) + hb.c[1][i] * conjx(ha.c[1][j]);
+}
+
+struct BilTerm {
+    SpinorF a[2], b[2];  // parity views of the full fields
+    int mask;
+    double coef;
+    int on;
+};
+
+__device__ void bilinear_term(const Geo& g, const GaugeF& U, const BilTerm& T, int par, int i,
+                              const int x[4], double f[4][8])
+{
+    Spinor<double> ax, bx;
+    load_spinor<PREC64>(T.a[par], i, ax);
+    load_spinor<PREC64>(T.b[par], i, bx);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        const bool wrap = (x[mu] == g.L[mu] - 1);
+        if (mu == 0 && T.mask == MODE_INTRA && ((x[0] + 1) % g.l0) == 0) continue;
+        int y[4], py, iy;
+        shifted(g, x, mu, +1, y);
+        site_at(g, y, py, iy);
+        Spinor<double> ay, by;
+        load_spinor<PREC64>(T.a[py], iy, ay);
+        load_spinor<PREC64>(T.b[py], iy, by);
+        HalfSp<double> hax, hby, hay, hbx;
+        project(mu, -1, ax, hax);
+        project(mu, -1, by, hby);
+        project(mu, +1, ay, hay);
+        project(mu, +1, bx, hbx);
+        Su3<double> X1, X2, u, Y, t1, t2;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) X1.m[r][c] = X2.m[r][c] = mk(0.0, 0.0);
+        outer_acc(hby, hax, X1);
+        outer_acc(hbx, hay, X2);
+        load_link<PREC64>(U, mu, par, i, u);
+        su3_mul(u, X1, t1);
+        su3_mul_nd(X2, u, t2);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Y.m[r][c] = t1.m[r][c] - t2.m[r][c];
+        double l[8];
+        lie_im2(Y, l);
+        const double ph = (mu == 0 && wrap && g.bc_t < 0) ? -1.0 : 1.0;
+        const double s = -T.coef * ph;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) f[mu][k] += s * l[k];
+    }
+}
+
+// F[mu][site][a] += sum over the (up to two) terms
+__global__ void __launch_bounds__(BS) k_bilinear(Geo g, GaugeF U, double* F, BilTerm T1, BilTerm T2)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
+    int x[4];
+    eo_coords(g, par, i, x);
+    double f[4][8];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) f[mu][k] = 0.0;
+    if (T1.on) bilinear_term(g, U, T1, par, i, x, f);
+    if (T2.on) bilinear_term(g, U, T2, par, i, x, f);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        double* d = F + ((size_t)mu * g.V + s) * 8;
+        double4* d4 = (double4*)d;
+        double4 a = d4[0], b = d4[1];
+        a.x += f[mu][0]; a.y += f[mu][1]; a.z += f[mu][2]; a.w += f[mu][3];
+        b.x += f[mu][4]; b.y += f[mu][5]; b.z += f[mu][6]; b.w += f[mu][7];
+        d4[0] = a;
+        d4[1] = b;
+    }
+}
+
+// staple sum A with U_mu(x) A the sum of the six plaquettes through the link
+__device__ void staple(const Geo& g, const GaugeF& U, const int x[4], int mu, Su3<double>& A)
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A.m[r][c] = mk(0.0, 0.0);
+    int xm[4];
+    shifted(g, x, mu, +1, xm);
+#pragma unroll 1
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        int y[4], p, i;
+        Su3<double> a, b, c, t, s;
+        // up: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+        site_at(g, xm, p, i);
+        load_link<PREC64>(U, nu, p, i, a);
+        shifted(g, x, nu, +1, y);
+        site_at(g, y, p, i);
+        load_link<PREC64>(U, mu, p, i, b);
+        site_at(g, x, p, i);
+        load_link<PREC64>(U, nu, p, i, c);
+        su3_mul_nd(a, b, t);
+        su3_mul_nd(t, c, s);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) A.m[r][q] = A.m[r][q] + s.m[r][q];
+        // down: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
+        shifted(g, xm, nu, -1, y);
+        site_at(g, y, p, i);
+        load_link<PREC64>(U, nu, p, i, a);
+        shifted(g, x, nu, -1, y);
+        site_at(g, y, p, i);
+        load_link<PREC64>(U, mu, p, i, b);
+        load_link<PREC64>(U, nu, p, i, c);
+        // t = a^dag b^dag = (b a)^dag
+        su3_mul(b, a, s);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) t.m[r][q] = conjx(s.m[q][r]);
+        su3_mul(t, c, s);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) A.m[r][q] = A.m[r][q] + s.m[r][q];
+    }
+}
+
+// F += coef * dS_G/dw^a,  dS_G/dw^a = -beta/3 Re tr(i T^a U A) = beta/6 * 2 Im tr(T^a U A)
+__global__ void __launch_bounds__(BS) k_gauge_force(Geo g, GaugeF U, double* F, double c)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * g.V) return;
+    const int mu = t / g.V, s = t - mu * g.V;
+    const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
+    int x[4];
+    eo_coords(g, par, i, x);
+    Su3<double> A, u, Y;
+    staple(g, U, x, mu, A);
+    load_link<PREC64>(U, mu, par, i, u);
+    su3_mul(u, A, Y);
+    double l[8];
+    lie_im2(Y, l);
+    double* d = F + ((size_t)mu * g.V + s) * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d[k] += c * l[k];
+}
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+// partial sums of Re tr of the six plaquettes at each site
+__global__ void k_plaq_part(Geo g, GaugeF U, double* part)
+{
+    double acc = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+        const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
+        int x[4];
+        eo_coords(g, par, i, x);
+        for (int mu = 1; mu < 4; ++mu)
+            for (int nu = 0; nu < mu; ++nu) {
+                int y[4], p, j;
+                Su3<double> a, b, c, d, t, r;
+                load_link<PREC64>(U, mu, par, i, a);
+                shifted(g, x, mu, +1, y);
+                site_at(g, y, p, j);
+                load_link<PREC64>(U, nu, p, j, b);
+                shifted(g, x, nu, +1, y);
+                site_at(g, y, p, j);
+                load_link<PREC64>(U, mu, p, j, c);
+                load_link<PREC64>(U, nu, par, i, d);
+                su3_mul(a, b, t);
+                su3_mul_nd(t, c, r);
+                su3_mul_nd(r, d, t);
+                acc += t.m[0][0].re + t.m[1][1].re + t.m[2][2].re;
+            }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_sum_final(const double* part, int n, double* out, double scale)
+{
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += part[k];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *out = scale * acc;
+}
+
+// exp(iQ) for traceless hermitian Q by the Cayley-Hamilton form
+// exp(iQ) = f0 + f1 Q + f2 Q^2 (Morningstar & Peardon, PRD 69 (2004) 054501)
+__device__ void expiq(const Su3<double>& Q, Su3<double>& E)
+{
+    Su3<double> Q2;
+    su3_mul(Q, Q, Q2);
+    const double c1 = 0.5 * (Q2.m[0][0].re + Q2.m[1][1].re + Q2.m[2][2].re);
+    cx<double> f0, f1, f2;
+    if (c1 < 1e-12) {
+        // |Q| < 1.5e-6: series to fourth order
+        Su3<double> Q3, Q4;
+        su3_mul(Q2, Q, Q3);
+        su3_mul(Q2, Q2, Q4);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cx<double> v = mul_i(Q.m[r][c]) - 0.5 * Q2.m[r][c] - (1.0 / 6.0) * mul_i(Q3.m[r][c]) +
+                               (1.0 / 24.0) * Q4.m[r][c];
+                if (r == c) v.re += 1.0;
+                E.m[r][c] = v;
+            }
+        return;
+    }
+    // c0 = det Q (real)
+    const cx<double> det = Q.m[0][0] * (Q.m[1][1] * Q.m[2][2] - Q.m[1][2] * Q.m[2][1]) -
+                           Q.m[0][1] * (Q.m[1][0] * Q.m[2][2] - Q.m[1][2] * Q.m[2][0]) +
+                           Q.m[0][2] * (Q.m[1][0] * Q.m[2][1] - Q.m[1][1] * Q.m[2][0]);
+    const double c0 = det.re;
+    const double c0a = fabs(c0);
+    const double c0max = 2.0 * pow(c1 / 3.0, 1.5);
+    const double ratio = fmin(1.0, c0a / c0max);
+    const double theta = acos(ratio);
+    const double u = sqrt(c1 / 3.0) * cos(theta / 3.0);
+    const double w = sqrt(c1) * sin(theta / 3.0);
+    const double u2 = u * u, w2 = w * w;
+    double xi0;
+    if (fabs(w) < 0.05)
+        xi0 = 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0));
+    else
+        xi0 = sin(w) / w;
+    double s2u, c2u, su, cu;
+    sincos(2.0 * u, &s2u, &c2u);
+    sincos(u, &su, &cu);
+    const double cw = cos(w);
+    const cx<double> e2 = mk(c2u, s2u), em = mk(cu, -su);
+    const cx<double> h0 = (u2 - w2) * e2 + em * mk(8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0);
+    const cx<double> h1 = (2.0 * u) * e2 - em * mk(2.0 * u * cw, -(3.0 * u2 - w2) * xi0);
+    const cx<double> h2 = e2 - em * mk(cw, 3.0 * u * xi0);
+    const double dinv = 1.0 / (9.0 * u2 - w2);
+    f0 = dinv * h0;
+    f1 = dinv * h1;
+    f2 = dinv * h2;
+    if (c0 < 0.0) {  // f_j(-c0) = (-1)^j conj(f_j(c0))
+        f0 = conjx(f0);
+        f1 = -conjx(f1);
+        f2 = conjx(f2);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cx<double> v = f1 * Q.m[r][c] + f2 * Q2.m[r][c];
+            if (r == c) v = v + f0;
+            E.m[r][c] = v;
+        }
+}
+
+__device__ void reunitarise(Su3<double>& u)
+{
+    double n0 = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) n0 += u.m[0][j].re * u.m[0][j].re + u.m[0][j].im * u.m[0][j].im;
+    n0 = 1.0 / sqrt(n0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) u.m[0][j] = n0 * u.m[0][j];
+    cx<double> d = mk(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) d = d + cjmul(u.m[0][j], u.m[1][j]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) u.m[1][j] = u.m[1][j] - d * u.m[0][j];
+    double n1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) n1 += u.m[1][j].re * u.m[1][j].re + u.m[1][j].im * u.m[1][j].im;
+    n1 = 1.0 / sqrt(n1);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) u.m[1][j] = n1 * u.m[1][j];
+    complete_row2(u);
+}
+
+__device__ void store_link_all(double2* U64, float4* U32, uint2* U16, int Vh, int mp, int i, const Su3<double>& u)
+{
+    double2* d64 = U64 + (size_t)mp * 9 * Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d64[(size_t)k * Vh + i] = make_double2(u.m[k / 3][k % 3].re, u.m[k / 3][k % 3].im);
+    float4* d32 = U32 + (size_t)mp * 3 * Vh;
+    uint2* d16 = U16 + (size_t)mp * 3 * Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const cx<double> x = u.m[(2 * k) / 3][(2 * k) % 3], y = u.m[(2 * k + 1) / 3][(2 * k + 1) % 3];
+        d32[(size_t)k * Vh + i] = make_float4((float)x.re, (float)x.im, (float)y.re, (float)y.im);
+        __half2 hx = __floats2half2_rn((float)x.re, (float)x.im);
+        __half2 hy = __floats2half2_rn((float)y.re, (float)y.im);
+        d16[(size_t)k * Vh + i] = make_uint2(*reinterpret_cast<unsigned*>(&hx), *reinterpret_cast<unsigned*>(&hy));
+    }
+}
+
+// U_mu(x) <- exp(i dt P_mu(x)) U_mu(x), P = sum_a p^a T^a; all three copies
+__global__ void __launch_bounds__(BS) k_update(Geo g, double2* U64, float4* U32, uint2* U16, const double* P, double dt)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * g.V) return;
+    const int mu = t / g.V, s = t - mu * g.V;
+    const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
+    const double* p = P + ((size_t)mu * g.V + s) * 8;
+    double q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = dt * p[k];
+    Su3<double> Q, E, u, n;
+    const double r3 = q[7] * INV_SQRT3;
+    Q.m[0][0] = mk(0.5 * (q[2] + r3), 0.0);
+    Q.m[1][1] = mk(0.5 * (-q[2] + r3), 0.0);
+    Q.m[2][2] = mk(-r3, 0.0);
+    Q.m[0][1] = mk(0.5 * q[0], -0.5 * q[1]);
+    Q.m[1][0] = mk(0.5 * q[0], 0.5 * q[1]);
+    Q.m[0][2] = mk(0.5 * q[3], -0.5 * q[4]);
+    Q.m[2][0] = mk(0.5 * q[3], 0.5 * q[4]);
+    Q.m[1][2] = mk(0.5 * q[5], -0.5 * q[6]);
+    Q.m[2][1] = mk(0.5 * q[5], 0.5 * q[6]);
+    expiq(Q, E);
+    GaugeF G;
+    G.v = U64;
+    G.Vh = g.Vh;
+    load_link<PREC64>(G, mu, par, i, u);
+    su3_mul(E, u, n);
+    reunitarise(n);
+    store_link_all(U64, U32, U16, g.Vh, mu * 2 + par, i, n);
+}
+
+// U'_mu(x) = U_mu(x - shift 0hat)
+__global__ void k_roll(Geo g, double2* U64, float4* U32, uint2* U16, const double2* src, int shift)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * g.V) return;
+    const int mu = t / g.V, s = t - mu * g.V;
+    const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
+    int x[4], y[4], p, j;
+    eo_coords(g, par, i, x);
+    shifted(g, x, 0, -shift, y);
+    site_at(g, y, p, j);
+    GaugeF G;
+    G.v = src;
+    G.Vh = g.Vh;
+    Su3<double> u;
+    load_link<PREC64>(G, mu, p, j, u);
+    store_link_all(U64, U32, U16, g.Vh, mu * 2 + par, i, u);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+static int launch_err(lqcd_ctx* h, const char* what)
+{
+    h->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->err = std::string(what) + ": " + cudaGetErrorString(e);
+        return LQCD_ERR_CUDA;
+    }
+    return LQCD_OK;
+}
+
+static BilTerm make_term(lqcd_ctx* h, const double2* a, const double2* b, int mask, double coef)
+{
+    BilTerm T;
+    T.on = (a != nullptr && b != nullptr) ? 1 : 0;
+    for (int p = 0; p < 2; ++p) {
+        T.a[p] = sp64((double2*)a, p, h->g.Vh);
+        T.b[p] = sp64((double2*)b, p, h->g.Vh);
+    }
+    T.mask = mask;
+    T.coef = coef;
+    return T;
+}
+
+int force_bilinear(lqcd_ctx* h, double* F, const double2* a1, const double2* b1, int mask1, double coef1,
+                   const double2* a2, const double2* b2, int mask2, double coef2)
+{
+    BilTerm T1 = make_term(h, a1, b1, mask1, coef1), T2 = make_term(h, a2, b2, mask2, coef2);
+    cudaEvent_t ev;
+    prof_begin(h, 2, &ev);
+    k_bilinear<<<(h->g.V + BS - 1) / BS, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, T1, T2);
+    LQ_TRY(launch_err(h, "force kernel"));
+    const int nt = T1.on + T2.on;
+    // per site: two spinors of each term, four links, F read and written
+    prof_end(h, 2, ev, (double)h->g.V * (nt * 2.0 * 192.0 + 4.0 * 144.0 + 2.0 * 256.0));
+    return LQCD_OK;
+}
+
+int gauge_force_kick(lqcd_ctx* h, double* F, double coef)
+{
+    // coef * (beta/6) is folded in by the caller
+    cudaEvent_t ev;
+    prof_begin(h, 3, &ev);
+    k_gauge_force<<<(4 * h->g.V + BS - 1) / BS, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, coef);
+    LQ_TRY(launch_err(h, "gauge force kernel"));
+    prof_end(h, 3, ev, (double)h->g.V * (4.0 * 144.0 + 2.0 * 256.0));
+    return LQCD_OK;
+}
+
+int plaquette_sum(lqcd_ctx* h, double* dev_out)
+{
+    const int nb = h->red_blocks;
+    k_plaq_part<<<nb, 256, 0, h->stream>>>(h->g, gauge_view(h, PREC64), h->red_part);
+    k_sum_final<<<1, 1024, 0, h->stream>>>(h->red_part, nb, dev_out, 1.0);
+    h->launches += 1;
+    return launch_err(h, "plaquette kernel");
+}
+
+int update_links(lqcd_ctx* h, const double* P, double dt)
+{
+    cudaEvent_t ev;
+    prof_begin(h, 3, &ev);
+    k_update<<<(4 * h->g.V + BS - 1) / BS, BS, 0, h->stream>>>(h->g, h->U64, h->U32, h->U16, P, dt);
+    LQ_TRY(launch_err(h, "link update kernel"));
+    prof_end(h, 3, ev, (double)h->g.V * 4.0 * (2.0 * 144.0 + 64.0 + 48.0 + 24.0));
+    return LQCD_OK;
+}
+
+int roll_links(lqcd_ctx* h, int shift)
+{
+    // src: the saved copy (caller copies the current field there first)
+    k_roll<<<(4 * h->g.V + BS - 1) / BS, BS, 0, h->stream>>>(h->g, h->U64, h->U32, h->U16, h->U64_save, shift);
+    return launch_err(h, "roll kernel");
+}
+
+int kinetic_sum(lqcd_ctx* h, const double* P, double* dev_out)
+{
+    return norm2_dev(h, P, (int64_t)32 * h->g.V, dev_out);
+}

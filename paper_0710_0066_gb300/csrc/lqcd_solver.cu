@@ -1,0 +1,741 @@
+// lqcd_solver.cu -- persistent batched solver for the even-odd reduced
+// operator  A = 1 - kappa^2 H_eo H_oe  on a batch of independent systems:
+// every x0-slab of one colour (W1 restricted to the slab, Sec. 1) or the
+// whole lattice (M, the S4 solver of Sec. 3).
+//
+// One cooperative launch runs the whole solve:
+//   outer loop (double):  r = b - A x, stop when |r| <= tol |b| per system;
+//   inner loop (double, single or half storage, FP32 arithmetic):
+//     BiCGstab on A e = r / |r| to a relative residual inner_tol;
+//   x += |r| e.
+// All systems iterate together; a converged system stops updating.  Every
+// reduction is per system, in double, in a fixed order (warp shuffles, then
+// the per-CTA partials summed in CTA order), so results are deterministic
+// and identical in every CTA.  The CTAs meet at a software grid barrier
+// whose wait is bounded (about two seconds): on time-out the kernel records
+// LQCD_ERR_TIMEOUT and every CTA returns.
+#include <algorithm>
+
+#include "lqcd_common.cuh"
+
+namespace {
+
+constexpr int SBS = 256;
+constexpr int NSYS_MAX = 64;
+constexpr int NQ = 3;
+constexpr long long SPIN_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
+
+struct SolveArgs {
+    Geo g;
+    int mode;  // MODE_INTRA: slabs, MODE_ALL: whole lattice
+    double k2;
+    int nsys, cps;
+    int slab0, slabstep;
+    int nsite;
+    GaugeF U64, UP;
+    SpinorF b, x, r64;  // double, parity 0
+    SpinorF t64;        // double, parity 1
+    SpinorF r, rh, p, v, s, t;  // inner precision, parity 0
+    SpinorF tmp;        // inner precision, parity 1
+    SpinorF e;          // inner solution (single; double for the double solver)
+    double tol, inner_tol;
+    int max_iter, max_outer, max_inner;
+    double* part;       // [NQ][grid]
+    unsigned* bar;
+    int* status;
+    int* iters;         // [nsys]
+    double* resid;      // [nsys]
+    int* outer_out;
+};
+
+struct SysSt {
+    double bn2, rn2, rr, itol2;
+    double2 rho, alpha, omega, beta;
+    int active, idone, it, itc;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool grid_sync(const SolveArgs& A, unsigned& epoch)
+{
+    __shared__ int s_bad;
+    __syncthreads();
+    ++epoch;
+    if (threadIdx.x == 0) {
+        const unsigned target = epoch * gridDim.x;
+        __threadfence();
+        atomicAdd(A.bar, 1u);
+        const long long t0 = clock64();
+        int bad = 0;
+        while (ld_acquire(A.bar) < target) {
+            if (*(volatile int*)A.status == LQCD_ERR_TIMEOUT) { bad = 1; break; }
+            if (clock64() - t0 > SPIN_LIMIT) {
+                atomicExch(A.status, LQCD_ERR_TIMEOUT);
+                bad = 1;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_bad = bad;
+    }
+    __syncthreads();
+    return s_bad == 0;
+}
+
+// CTA sum of up to three doubles -> part[q][cta]
+__device__ void reduce_put(const SolveArgs& A, double a, double b, double c, int nq)
+{
+    __shared__ double sh[NQ][SBS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][w] = a;
+        sh[1][w] = b;
+        sh[2][w] = c;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nq) {
+        double v = 0.0;
+        for (int k = 0; k < SBS / 32; ++k) v += sh[threadIdx.x][k];
+        A.part[threadIdx.x * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+// per-system totals of the partials (every CTA computes all of them)
+__device__ void gather(const SolveArgs& A, int nq, double (*ssum)[NQ])
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int npairs = A.nsys * nq;
+    for (int k = w; k < npairs; k += SBS / 32) {
+        const int s = k / nq, q = k % nq;
+        double v = 0.0;
+        for (int c = lane; c < A.cps; c += 32) v += A.part[q * gridDim.x + s * A.cps + c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) ssum[s][q] = v;
+    }
+    __syncthreads();
+}
+
+// per-site dot products in the storage arithmetic (T), accumulated over the
+// sites of a thread and across threads in double
+template <class T>
+__device__ __forceinline__ void cdot_acc(const Spinor<T>& a, const Spinor<T>& b, double& re, double& im)
+{
+    T sr = 0, si = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sr += a.c[s][c].re * b.c[s][c].re + a.c[s][c].im * b.c[s][c].im;
+            si += a.c[s][c].re * b.c[s][c].im - a.c[s][c].im * b.c[s][c].re;
+        }
+    re += (double)sr;
+    im += (double)si;
+}
+template <class T>
+__device__ __forceinline__ double nrm_acc(const Spinor<T>& a)
+{
+    T r = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r += a.c[s][c].re * a.c[s][c].re + a.c[s][c].im * a.c[s][c].im;
+    return (double)r;
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b)
+{
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+#define FOR_SITES for (int j_ = cin * SBS + (int)threadIdx.x; j_ < A.nsite; j_ += A.cps * SBS)
+#define SYNC_OR_RETURN \
+    if (!grid_sync(A, epoch)) return
+
+template <int P>
+__global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
+{
+    typedef typename Real<P>::T T;
+    constexpr int PE = (P == PREC64) ? PREC64 : PREC32;
+    typedef typename Real<PE>::T TE;
+    const int cta = blockIdx.x, tid = threadIdx.x;
+    const int sys = cta / A.cps, cin = cta - sys * A.cps;
+    const int base = (A.mode == MODE_INTRA) ? (A.slab0 + sys * A.slabstep) * A.g.Sh : 0;
+    __shared__ SysSt S[NSYS_MAX];
+    __shared__ double ssum[NSYS_MAX][NQ];
+    __shared__ int s_ctl;
+    unsigned epoch = 0;
+
+    // ---- x = 0, r64 = b, |b|^2
+    {
+        double q = 0.0;
+        FOR_SITES
+        {
+            const int i = base + j_;
+            Spinor<double> bb, z;
+            load_spinor<PREC64, true>(A.b, i, bb);
+            store_spinor<PREC64>(A.r64, i, bb);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) z.c[s][c] = mk(0.0, 0.0);
+            store_spinor<PREC64>(A.x, i, z);
+            q += nrm_acc(bb);
+        }
+        reduce_put(A, q, 0.0, 0.0, 1);
+        SYNC_OR_RETURN;
+        gather(A, 1, ssum);
+        if (tid == 0)
+            for (int s = 0; s < A.nsys; ++s) {
+                S[s].bn2 = ssum[s][0];
+                S[s].rn2 = ssum[s][0];
+                S[s].it = 0;
+            }
+        __syncthreads();
+    }
+
+    int outer = 0, final_ctl = 0;
+    for (;;) {
+        if (tid == 0) {
+            int any = 0, maxit = 0, bad = 0;
+            for (int s = 0; s < A.nsys; ++s) {
+                const double lim = A.tol * A.tol * S[s].bn2;
+                const bool nan = !isfinite(S[s].rn2);
+                bad |= nan;
+                S[s].active = (!nan && S[s].rn2 > lim && S[s].bn2 > 0.0) ? 1 : 0;
+                any |= S[s].active;
+                maxit = max(maxit, S[s].it);
+            }
+            s_ctl = bad ? 3 : !any ? 0 : (outer >= A.max_outer || maxit >= A.max_iter) ? 2 : 1;
+        }
+        __syncthreads();
+        if (s_ctl != 1) {
+            final_ctl = s_ctl;
+            break;
+        }
+        ++outer;
+
+        // ---- inner start: r = rh = p = r64 / |r64|, e = 0
+        {
+            double q = 0.0;
+            if (S[sys].active) {
+                const double sc = 1.0 / sqrt(S[sys].rn2);
+                FOR_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<double> r6;
+                    load_spinor<PREC64, false>(A.r64, i, r6);
+                    Spinor<T> r;
+                    Spinor<TE> z;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            r.c[s][c] = mk((T)(sc * r6.c[s][c].re), (T)(sc * r6.c[s][c].im));
+                            z.c[s][c] = mk((TE)0, (TE)0);
+                        }
+                    store_spinor<P>(A.r, i, r);
+                    load_spinor<P, false>(A.r, i, r);  // the stored (rounded) vector
+                    store_spinor<P>(A.rh, i, r);
+                    store_spinor<P>(A.p, i, r);
+                    store_spinor<PE>(A.e, i, z);
+                    q += nrm_acc(r);
+                }
+            }
+            reduce_put(A, q, 0.0, 0.0, 1);
+            SYNC_OR_RETURN;
+            gather(A, 1, ssum);
+            if (tid == 0)
+                for (int s = 0; s < A.nsys; ++s) {
+                    S[s].rho = make_double2(ssum[s][0], 0.0);
+                    S[s].idone = !S[s].active;
+                    S[s].itc = 0;
+                    const double need = 0.5 * A.tol * sqrt(S[s].bn2 / fmax(S[s].rn2, 1e-300));
+                    const double it = fmax(A.inner_tol, need);
+                    S[s].itol2 = it * it;
+                }
+            __syncthreads();
+        }
+
+        // ---- BiCGstab
+        for (;;) {
+            if (tid == 0) {
+                int any = 0;
+                for (int s = 0; s < A.nsys; ++s) any |= (!S[s].idone && S[s].it < A.max_iter);
+                s_ctl = any;
+            }
+            __syncthreads();
+            if (!s_ctl) break;
+            const bool act = !S[sys].idone && S[sys].it < A.max_iter;
+
+            // tmp = H_oe p
+            if (act) FOR_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<T> a;
+                    hop_site<P, false>(A.g, A.mode, 0, 1, i, A.p, A.UP, a);
+                    store_spinor<P>(A.tmp, i, a);
+                }
+            SYNC_OR_RETURN;
+            // v = p - k2 H_eo tmp ; <rh, v>
+            {
+                double qr = 0.0, qi = 0.0;
+                if (act) {
+                    const T k2 = (T)A.k2;
+                    FOR_SITES
+                    {
+                        const int i = base + j_;
+                        Spinor<T> a, pp, rh;
+                        hop_site<P, false>(A.g, A.mode, 0, 0, i, A.tmp, A.UP, a);
+                        load_spinor<P, false>(A.p, i, pp);
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) a.c[s][c] = pp.c[s][c] - k2 * a.c[s][c];
+                        store_spinor<P>(A.v, i, a);
+                        load_spinor<P, false>(A.v, i, a);
+                        load_spinor<P, false>(A.rh, i, rh);
+                        cdot_acc(rh, a, qr, qi);
+                    }
+                }
+                reduce_put(A, qr, qi, 0.0, 2);
+                SYNC_OR_RETURN;
+                gather(A, 2, ssum);
+                if (tid == 0)
+                    for (int s = 0; s < A.nsys; ++s) {
+                        if (S[s].idone || S[s].it >= A.max_iter) continue;
+                        const double2 d = make_double2(ssum[s][0], ssum[s][1]);
+                        const double2 al = cdiv(S[s].rho, d);
+                        if (!finite2(al) || (d.x == 0.0 && d.y == 0.0)) {
+                            S[s].idone = 1;
+                            S[s].alpha = make_double2(0.0, 0.0);
+                        } else {
+                            S[s].alpha = al;
+                        }
+                    }
+                __syncthreads();
+            }
+            const bool act2 = act && !S[sys].idone;
+            // s = r - alpha v
+            if (act2) {
+                const cx<T> al = mk((T)S[sys].alpha.x, (T)S[sys].alpha.y);
+                FOR_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<T> r, v;
+                    load_spinor<P, false>(A.r, i, r);
+                    load_spinor<P, false>(A.v, i, v);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) r.c[s][c] = r.c[s][c] - al * v.c[s][c];
+                    store_spinor<P>(A.s, i, r);
+                }
+            }
+            SYNC_OR_RETURN;
+            // tmp = H_oe s
+            if (act2) FOR_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<T> a;
+                    hop_site<P, false>(A.g, A.mode, 0, 1, i, A.s, A.UP, a);
+                    store_spinor<P>(A.tmp, i, a);
+                }
+            SYNC_OR_RETURN;
+            // t = s - k2 H_eo tmp ; <t, s>, <t, t>
+            {
+                double qr = 0.0, qi = 0.0, qt = 0.0;
+                if (act2) {
+                    const T k2 = (T)A.k2;
+                    FOR_SITES
+                    {
+                        const int i = base + j_;
+                        Spinor<T> a, ss;
+                        hop_site<P, false>(A.g, A.mode, 0, 0, i, A.tmp, A.UP, a);
+                        load_spinor<P, false>(A.s, i, ss);
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) a.c[s][c] = ss.c[s][c] - k2 * a.c[s][c];
+                        store_spinor<P>(A.t, i, a);
+                        load_spinor<P, false>(A.t, i, a);
+                        cdot_acc(a, ss, qr, qi);
+                        qt += nrm_acc(a);
+                    }
+                }
+                reduce_put(A, qr, qi, qt, 3);
+                SYNC_OR_RETURN;
+                gather(A, 3, ssum);
+                if (tid == 0)
+                    for (int s = 0; s < A.nsys; ++s) {
+                        if (S[s].idone || S[s].it >= A.max_iter) continue;
+                        const double tt = ssum[s][2];
+                        const double2 om = make_double2(ssum[s][0] / tt, ssum[s][1] / tt);
+                        if (!(tt > 0.0) || !finite2(om)) {
+                            S[s].omega = make_double2(0.0, 0.0);
+                            S[s].idone = 2;  // keep alpha p, stop afterwards
+                        } else {
+                            S[s].omega = om;
+                        }
+                    }
+                __syncthreads();
+            }
+            // e += alpha p + omega s ; r = s - omega t ; <rh, r>, |r|^2
+            {
+                double qr = 0.0, qi = 0.0, qn = 0.0;
+                if (act2) {
+                    const cx<T> al = mk((T)S[sys].alpha.x, (T)S[sys].alpha.y);
+                    const cx<T> om = mk((T)S[sys].omega.x, (T)S[sys].omega.y);
+                    FOR_SITES
+                    {
+                        const int i = base + j_;
+                        Spinor<T> pp, ss, tt, rh;
+                        Spinor<TE> ee;
+                        load_spinor<PE, false>(A.e, i, ee);
+                        load_spinor<P, false>(A.p, i, pp);
+                        load_spinor<P, false>(A.s, i, ss);
+                        load_spinor<P, false>(A.t, i, tt);
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const cx<T> d = al * pp.c[s][c] + om * ss.c[s][c];
+                                ee.c[s][c] = ee.c[s][c] + mk((TE)d.re, (TE)d.im);
+                                ss.c[s][c] = ss.c[s][c] - om * tt.c[s][c];
+                            }
+                        store_spinor<PE>(A.e, i, ee);
+                        store_spinor<P>(A.r, i, ss);
+                        load_spinor<P, false>(A.r, i, ss);
+                        load_spinor<P, false>(A.rh, i, rh);
+                        cdot_acc(rh, ss, qr, qi);
+                        qn += nrm_acc(ss);
+                    }
+                }
+                reduce_put(A, qr, qi, qn, 3);
+                SYNC_OR_RETURN;
+                gather(A, 3, ssum);
+                if (tid == 0)
+                    for (int s = 0; s < A.nsys; ++s) {
+                        if (S[s].idone == 1 || S[s].it >= A.max_iter) continue;
+                        S[s].it += 1;
+                        S[s].itc += 1;
+                        if (S[s].itc >= A.max_inner) S[s].idone = 2;
+                        const double2 rn = make_double2(ssum[s][0], ssum[s][1]);
+                        S[s].rr = ssum[s][2];
+                        if (S[s].idone == 2 || !(S[s].rr > S[s].itol2) || !finite2(rn)) {
+                            S[s].idone = 1;
+                            continue;
+                        }
+                        S[s].beta = cmul(cdiv(rn, S[s].rho), cdiv(S[s].alpha, S[s].omega));
+                        if (!finite2(S[s].beta)) S[s].idone = 1;
+                        S[s].rho = rn;
+                    }
+                __syncthreads();
+            }
+            // p = r + beta (p - omega v)
+            if (act2 && !S[sys].idone) {
+                const cx<T> be = mk((T)S[sys].beta.x, (T)S[sys].beta.y);
+                const cx<T> om = mk((T)S[sys].omega.x, (T)S[sys].omega.y);
+                FOR_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<T> r, pp, v;
+                    load_spinor<P, false>(A.r, i, r);
+                    load_spinor<P, false>(A.p, i, pp);
+                    load_spinor<P, false>(A.v, i, v);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) r.c[s][c] = r.c[s][c] + be * (pp.c[s][c] - om * v.c[s][c]);
+                    store_spinor<P>(A.p, i, r);
+                }
+            }
+            SYNC_OR_RETURN;
+        }
+
+        // ---- x += |r64| e (double)
+        if (S[sys].active) {
+            const double sc = sqrt(S[sys].rn2);
+            FOR_SITES
+            {
+                const int i = base + j_;
+                Spinor<double> xx;
+                Spinor<TE> ee;
+                load_spinor<PREC64, false>(A.x, i, xx);
+                load_spinor<PE, false>(A.e, i, ee);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        xx.c[s][c] = xx.c[s][c] + mk(sc * (double)ee.c[s][c].re, sc * (double)ee.c[s][c].im);
+                store_spinor<PREC64>(A.x, i, xx);
+            }
+        }
+        SYNC_OR_RETURN;
+        // ---- t64 = H_oe x (double)
+        if (S[sys].active) FOR_SITES
+            {
+                const int i = base + j_;
+                Spinor<double> a;
+                hop_site<PREC64, false>(A.g, A.mode, 0, 1, i, A.x, A.U64, a);
+                store_spinor<PREC64>(A.t64, i, a);
+            }
+        SYNC_OR_RETURN;
+        // ---- r64 = b - x + k2 H_eo t64 ; |r64|^2
+        {
+            double q = 0.0;
+            if (S[sys].active) {
+                FOR_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<double> a, xx, bb;
+                    hop_site<PREC64, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, a);
+                    load_spinor<PREC64, false>(A.x, i, xx);
+                    load_spinor<PREC64, true>(A.b, i, bb);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) a.c[s][c] = bb.c[s][c] - xx.c[s][c] + A.k2 * a.c[s][c];
+                    store_spinor<PREC64>(A.r64, i, a);
+                    q += nrm_acc(a);
+                }
+            }
+            reduce_put(A, q, 0.0, 0.0, 1);
+            SYNC_OR_RETURN;
+            gather(A, 1, ssum);
+            if (tid == 0)
+                for (int s = 0; s < A.nsys; ++s)
+                    if (S[s].active) S[s].rn2 = ssum[s][0];
+            __syncthreads();
+        }
+    }
+
+    if (cta == 0 && tid == 0) {
+        for (int s = 0; s < A.nsys; ++s) {
+            A.iters[s] = S[s].it;
+            A.resid[s] = S[s].bn2 > 0.0 ? sqrt(S[s].rn2 / S[s].bn2) : 0.0;
+        }
+        *A.outer_out = outer;
+        if (final_ctl == 3) atomicCAS(A.status, 0, LQCD_ERR_NAN);
+        if (final_ctl == 2) atomicCAS(A.status, 0, LQCD_ERR_NOCONVERGE);
+    }
+}
+
+#undef FOR_SITES
+#undef SYNC_OR_RETURN
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Work {
+    double2* vec[8] = {nullptr};  // inner vectors, each sized for a double half field
+    double2* r64 = nullptr;
+    double2* t64 = nullptr;
+    double* part = nullptr;
+    unsigned* bar = nullptr;
+    int* status = nullptr;
+    int* iters = nullptr;
+    double* resid = nullptr;
+    int* outer = nullptr;
+    int* h_status = nullptr;  // pinned mirror: status, outer, iters[NSYS_MAX]
+    double* h_resid = nullptr;
+    int gmax[3] = {0, 0, 0};  // co-resident CTAs per precision
+};
+
+static SpinorF inner_view(double2* buf, int prec, int Vh)
+{
+    SpinorF f;
+    f.v = buf;
+    f.N = Vh;
+    // half: the per-site scales follow the 3*Vh uint4 words
+    f.nrm = prec == PREC16 ? (float*)((uint4*)buf + (size_t)3 * Vh) : nullptr;
+    return f;
+}
+
+int solver_init(lqcd_ctx* h)
+{
+    Work* w = new Work();
+    h->work = w;
+    const int Vh = h->g.Vh;
+    for (int k = 0; k < 8; ++k) LQ_CUDA(h, cudaMalloc(&w->vec[k], sizeof(double2) * 12 * (size_t)Vh));
+    LQ_CUDA(h, cudaMalloc(&w->r64, sizeof(double2) * 12 * (size_t)Vh));
+    LQ_CUDA(h, cudaMalloc(&w->t64, sizeof(double2) * 12 * (size_t)Vh));
+    int occ[3];
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_solve<PREC64>, SBS, 0));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_solve<PREC32>, SBS, 0));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_solve<PREC16>, SBS, 0));
+    int gm = 0;
+    for (int k = 0; k < 3; ++k) {
+        w->gmax[k] = std::max(1, occ[k]) * h->num_sms;
+        gm = std::max(gm, w->gmax[k]);
+    }
+    LQ_CUDA(h, cudaMalloc(&w->part, sizeof(double) * NQ * (size_t)gm));
+    LQ_CUDA(h, cudaMalloc(&w->bar, sizeof(unsigned) * 4));
+    LQ_CUDA(h, cudaMalloc(&w->status, sizeof(int) * 4));
+    LQ_CUDA(h, cudaMalloc(&w->iters, sizeof(int) * NSYS_MAX));
+    LQ_CUDA(h, cudaMalloc(&w->resid, sizeof(double) * NSYS_MAX));
+    LQ_CUDA(h, cudaMalloc(&w->outer, sizeof(int) * 4));
+    LQ_CUDA(h, cudaMallocHost(&w->h_status, sizeof(int) * (NSYS_MAX + 4)));
+    LQ_CUDA(h, cudaMallocHost(&w->h_resid, sizeof(double) * NSYS_MAX));
+    return LQCD_OK;
+}
+
+void solver_free(lqcd_ctx* h)
+{
+    Work* w = h->work;
+    if (!w) return;
+    for (int k = 0; k < 8; ++k) cudaFree(w->vec[k]);
+    cudaFree(w->r64);
+    cudaFree(w->t64);
+    cudaFree(w->part);
+    cudaFree(w->bar);
+    cudaFree(w->status);
+    cudaFree(w->iters);
+    cudaFree(w->resid);
+    cudaFree(w->outer);
+    cudaFreeHost(w->h_status);
+    cudaFreeHost(w->h_resid);
+    delete w;
+    h->work = nullptr;
+}
+
+// algorithmic DRAM bytes per system site: one inner iteration and one outer
+// cycle (each vector and the eight links moved once per phase)
+static void solver_site_bytes(int prec, double* inner, double* outer)
+{
+    const double sp = prec == PREC64 ? 192.0 : prec == PREC32 ? 96.0 : 52.0;
+    const double lk = prec == PREC64 ? 1152.0 : prec == PREC32 ? 384.0 : 192.0;
+    const double se = prec == PREC64 ? 192.0 : 96.0;
+    *inner = 24.0 * sp + 4.0 * lk + 2.0 * se;
+    *outer = (192.0 + 3.0 * sp + se) + (2.0 * 192.0 + se) + (2.0 * 192.0 + 1152.0) + (4.0 * 192.0 + 1152.0);
+}
+
+int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e, const double2* b_e,
+             double tol, int max_iter, int* iters_sys, double* resid_sys)
+{
+    Work* w = h->work;
+    const Geo& g = h->g;
+    SolveArgs A;
+    A.g = g;
+    A.mode = mode;
+    A.k2 = kappa * kappa;
+    if (mode == MODE_INTRA) {
+        A.nsys = colour < 0 ? g.nb : g.nb / 2;
+        A.slab0 = colour < 0 ? 0 : colour;
+        A.slabstep = colour < 0 ? 1 : 2;
+        A.nsite = g.Sh;
+    } else {
+        A.nsys = 1;
+        A.slab0 = 0;
+        A.slabstep = 1;
+        A.nsite = g.Vh;
+    }
+    if (A.nsys > NSYS_MAX) {
+        h->err = "too many slabs for one batched solve";
+        return LQCD_ERR_GEOM;
+    }
+    const int want = (A.nsite + SBS - 1) / SBS;
+    A.cps = std::max(1, std::min(w->gmax[prec] / A.nsys, want));
+    const int G = A.cps * A.nsys;
+    A.U64 = gauge_view(h, PREC64);
+    A.UP = gauge_view(h, prec);
+    A.b = sp64((double2*)b_e, 0, g.Vh);
+    A.x = sp64(x_e, 0, g.Vh);
+    A.r64 = sp64(w->r64, 0, g.Vh);
+    A.t64 = sp64(w->t64, 0, g.Vh);
+    A.r = inner_view(w->vec[0], prec, g.Vh);
+    A.rh = inner_view(w->vec[1], prec, g.Vh);
+    A.p = inner_view(w->vec[2], prec, g.Vh);
+    A.v = inner_view(w->vec[3], prec, g.Vh);
+    A.s = inner_view(w->vec[4], prec, g.Vh);
+    A.t = inner_view(w->vec[5], prec, g.Vh);
+    A.tmp = inner_view(w->vec[6], prec, g.Vh);
+    A.e = inner_view(w->vec[7], prec == PREC64 ? PREC64 : PREC32, g.Vh);
+    A.tol = tol;
+    A.inner_tol = prec == PREC64 ? 0.0 : prec == PREC32 ? 1e-5 : 2e-3;
+    A.max_iter = max_iter;
+    A.max_outer = prec == PREC64 ? 8 : 40;
+    A.max_inner = prec == PREC64 ? max_iter : prec == PREC32 ? 4000 : 600;
+    A.part = w->part;
+    A.bar = w->bar;
+    A.status = w->status;
+    A.iters = w->iters;
+    A.resid = w->resid;
+    A.outer_out = w->outer;
+    LQ_CUDA(h, cudaMemsetAsync(w->bar, 0, sizeof(unsigned) * 4, h->stream));
+    LQ_CUDA(h, cudaMemsetAsync(w->status, 0, sizeof(int) * 4, h->stream));
+    void* args[] = {&A};
+    const void* fn = prec == PREC64 ? (const void*)k_solve<PREC64>
+                     : prec == PREC32 ? (const void*)k_solve<PREC32>
+                                      : (const void*)k_solve<PREC16>;
+    cudaEvent_t ev;
+    prof_begin(h, 1, &ev);
+    LQ_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(G), dim3(SBS), args, 0, h->stream));
+    h->launches += 1;
+    prof_end(h, 1, ev, 0.0);
+    const size_t rec = h->prof.recs.size();
+    LQ_CUDA(h, cudaMemcpyAsync(w->h_status, w->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LQ_CUDA(h, cudaMemcpyAsync(w->h_status + 1, w->outer, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LQ_CUDA(h, cudaMemcpyAsync(w->h_status + 4, w->iters, sizeof(int) * A.nsys, cudaMemcpyDeviceToHost,
+                               h->stream));
+    LQ_CUDA(h, cudaMemcpyAsync(w->h_resid, w->resid, sizeof(double) * A.nsys, cudaMemcpyDeviceToHost,
+                               h->stream));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    const int st = w->h_status[0];
+    const int nouter = w->h_status[1];
+    double bi, bo;
+    solver_site_bytes(prec, &bi, &bo);
+    int64_t itsum = 0;
+    for (int s = 0; s < A.nsys; ++s) {
+        itsum += w->h_status[4 + s];
+        if (iters_sys) iters_sys[s] = w->h_status[4 + s];
+        if (resid_sys) resid_sys[s] = w->h_resid[s];
+    }
+    if (ev && rec > 0 && rec <= h->prof.recs.size())
+        h->prof.recs[rec - 1].bytes = (double)A.nsite * ((double)itsum * bi + (double)nouter * A.nsys * bo);
+    h->iter_count += itsum;
+    h->site_iters += itsum * (int64_t)A.nsite;
+    h->solve_count += 1;
+    if (st == LQCD_ERR_TIMEOUT) {
+        h->err = "solver: grid barrier wait timed out";
+        return LQCD_ERR_TIMEOUT;
+    }
+    if (st == LQCD_ERR_NAN) {
+        h->err = "solver: non-finite residual";
+        return LQCD_ERR_NAN;
+    }
+    if (st == LQCD_ERR_NOCONVERGE) {
+        int mx = 0;
+        double rmax = 0.0;
+        for (int s = 0; s < A.nsys; ++s) {
+            mx = std::max(mx, w->h_status[4 + s]);
+            rmax = std::max(rmax, w->h_resid[s]);
+        }
+        char buf[160];
+        snprintf(buf, sizeof(buf), "solver: no convergence (prec %d, %d outer cycles, %d inner iterations, residual %.3e)",
+                 prec, nouter, mx, rmax);
+        h->err = buf;
+        return LQCD_ERR_NOCONVERGE;
+    }
+    return LQCD_OK;
+}

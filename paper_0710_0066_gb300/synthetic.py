@@ -64,9 +64,7 @@ def random_links_torch(L, eps, seed, device):
         b = min(4 * V, a + chunk)
         h = torch.randn((b - a, 8), generator=g, device=device, dtype=torch.float64)
         H = torch.einsum("na,aij->nij", h.to(torch.complex128), T)
-        w, vec = torch.linalg.eigh(H)
-        ph = torch.exp(1j * eps * w.to(torch.complex128))
-        U[a:b] = torch.einsum("nij,nj,nkj->nik", vec, ph, vec.conj())
+        U[a:b] = torch.linalg.matrix_exp(1j * eps * H)
     return U.reshape(4, V, 3, 3)
 
 
