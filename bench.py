@@ -33,11 +33,27 @@ sys.path.insert(0, ROOT)
 # ---------------------------------------------------------------------------
 WL = dict(L=(32, 16, 16, 16), l0=4, kappa=0.1575, beta=5.6, eps=0.6, seed=2009, tau=1.0,
           nlevels=3, scheme=(1, 1, 1), nsteps=(2, 4, 8), lam=0.1931833275037836,
-          level_gauge=0, level_w1=1, level_schur=2, tol=1e-10, max_iter=20000)
+          level_gauge=0, level_w1=1, level_schur=2, tol=1e-10, max_iter=20000, therm=40)
 WORKLOAD_NAME = ("Schwarz-HMC trajectory 16^3x32, l0=4 (8 x0-slabs, red/black), kappa=0.1575, "
                  "beta=5.6, tau=1, Omelyan (lambda=0.1932) on 3 time scales: gauge / W1 / boundary "
-                 "Schur force, n=(2,4,8); eps=0.6 synthetic links")
+                 "Schur force, n=(2,4,8); links exp(i 0.6 H) thermalised by 40 pure-gauge HMC "
+                 "trajectories at beta=5.6")
 DSLASH_L = (64, 32, 32, 32)
+
+
+def thermalise(lat, U, beta, ntraj, seed):
+    """seeded pure-gauge HMC at beta from a rough random start (the paper's
+    inputs are thermalised beta = 5.6 fields): 20 trajectories without the
+    accept/reject step, the rest with it"""
+    from paper_0710_0066_gb300 import lqcd
+
+    prm = lqcd.hmc_params(beta, 0.0, 1.0, 1, (lqcd.SW,), (10,), 0, -1, -1, lam=0.1931833275037836,
+                          roll=0, metropolis=0, precision=lqcd.PREC_F64, tol=1e-10)
+    res = None
+    for t in range(ntraj):
+        prm.metropolis = 1 if t >= min(20, ntraj // 2) else 0
+        U, res = lat.hmc_trajectory(U, prm, seed, 1000000 + t)
+    return U, res
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -186,6 +202,7 @@ def run_ours(args):
     L, l0 = WL["L"], WL["l0"]
     lat = lqcd.Lattice(L, l0, -1)
     U0 = syn.random_links_torch(L, WL["eps"], WL["seed"] + rank, "cuda").contiguous()
+    U0, rth = thermalise(lat, U0, WL["beta"], WL["therm"], WL["seed"] + rank)
 
     def params(prec):
         return lqcd.hmc_params(WL["beta"], WL["kappa"], WL["tau"], WL["nlevels"], WL["scheme"], WL["nsteps"],
@@ -210,6 +227,7 @@ def run_ours(args):
     l0_launch = lqcd.lqcd_launch_count(lat.h)
     clocks = Clocks(local)
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     step_ms, results, U_in = [], [], []
     for k in range(args.steps):
         flush.zero_()
@@ -224,6 +242,7 @@ def run_ours(args):
         step_ms.append(a.elapsed_time(b))
         results.append(res)
         traj += 1
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     launches = lqcd.lqcd_launch_count(lat.h) - l0_launch
     n_sol, ms_sol, by_sol = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
@@ -315,6 +334,7 @@ def run_ours(args):
                      "kernel_share_of_step": ms_sol / total_ms if total_ms else None},
         "dslash": dslash,
         "fp64_form": fp64,
+        "thermalisation": {"trajectories": WL["therm"], "plaq": rth.plaq if rth else None},
         "trajectory": {"dH": [r.dH for r in results], "accepted": [r.accepted for r in results],
                        "plaq": results[-1].plaq, "solver_iters": [r.solver_iters for r in results],
                        "n_solves": results[-1].n_solves, "n_force": results[-1].n_force,
@@ -332,8 +352,61 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_case(args):
+    """small single-kernel cases for profiler captures (a few GB on the device)"""
+    import torch
+
+    from paper_0710_0066_gb300 import lqcd, synthetic as syn
+
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(WL["seed"])
+    prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
+    if args.case == "solver":
+        # the batched slab solve (8 slabs) and the global solve of the workload
+        L, l0 = WL["L"], WL["l0"]
+        lat = lqcd.Lattice(L, l0, -1)
+        U = syn.random_links_torch(L, WL["eps"], WL["seed"], "cuda").contiguous()
+        U, _ = thermalise(lat, U, WL["beta"], 20, WL["seed"])
+        lat.set_gauge(U)
+        b = torch.randn((lat.V, 4, 3), dtype=torch.complex128, device="cuda", generator=g)
+        lqcd.lqcd_profile_enable(lat.h, 1 << lqcd.KERNEL_SOLVER)
+        out = {}
+        for name in ("block", "global"):
+            lqcd.lqcd_profile_reset(lat.h)
+            if name == "block":
+                x, it, rs = lat.block_solve(b, WL["kappa"], -1, 0, prec, tol=WL["tol"])
+                it, rs = it[:lat.nb], max(rs[:lat.nb])
+            else:
+                x, it, rs = lat.solve(b, WL["kappa"], 0, prec, tol=WL["tol"])
+            n, ms, by = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
+            out[name] = {"iters": it, "resid": rs, "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6}
+        print(json.dumps({"case": "solver", "lattice": "x".join(map(str, L)), "precision": args.precision,
+                          **out}), flush=True)
+        lat.close()
+    else:
+        # even-odd hopping sweep at 24^3 x 48 (fields larger than L2)
+        L = (48, 24, 24, 24)
+        lat = lqcd.Lattice(L, 8, -1)
+        U = syn.random_links_torch(L, WL["eps"], WL["seed"], "cuda").contiguous()
+        lat.set_gauge(U)
+        x = torch.randn((lat.Vh, 4, 3), dtype=torch.complex128, device="cuda", generator=g)
+        lqcd.lqcd_profile_enable(lat.h, 1 << lqcd.KERNEL_HOP)
+        out = {}
+        for name, pr in (("f32", lqcd.PREC_F32), ("f16", lqcd.PREC_F16), ("f64", lqcd.PREC_F64)):
+            lqcd.lqcd_profile_reset(lat.h)
+            for _ in range(3):
+                lat.dslash_eo(x, 0, 0.0, 0, lqcd.OP_HOP, pr)
+            n, ms, by = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_HOP)
+            out[name] = {"ms": ms / n, "gbs": by / ms / 1e6}
+        print(json.dumps({"case": "dslash", "lattice": "x".join(map(str, L)), **out}), flush=True)
+        lat.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default=None, choices=["solver", "dslash"],
+                    help="run one small kernel case instead of the benchmark (profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -344,7 +417,9 @@ def main():
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
