@@ -235,6 +235,24 @@ int lqcd_profile_read(lqcd_t h, int kernel_id, int64_t* launches, double* ms, do
  * counter; *count is a host int64). */
 int lqcd_launch_count(lqcd_t h, int64_t* count);
 
+/* Wilson gauge action without a handle and without any device allocation,
+ * for callers that cannot call cudaMalloc (for example code running while
+ * another framework owns the whole device memory pool, or host threads that
+ * must not trigger the device synchronisation an allocation implies); such
+ * callers cannot create a handle either.  The paper has no counterpart: it
+ * is a service entry point, not a step of the method.
+ * U: device gauge field, C-ABI layout, lattice L[4] (all even).
+ * out: device double[2], receives S_G = -beta/3 sum Re tr P and the average
+ * Re tr P / 3.  stream: cudaStream_t (NULL = legacy default); asynchronous.
+ * Per-block partial sums live in a fixed 128 KiB array compiled into the
+ * library and kept by every GPU that loads it until the process exits; at
+ * most 2,097,152 sites (32^3 x 64), larger lattices return LQCD_ERR_GEOM.
+ * The first call on a device looks the array's address up with
+ * cudaGetSymbolAddress (that device current); make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race.
+ * Errors: LQCD_ERR_ARG (null pointer), LQCD_ERR_GEOM, LQCD_ERR_CUDA. */
+int lqcd_gauge_action_static(const int L[4], const double* U, double beta, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

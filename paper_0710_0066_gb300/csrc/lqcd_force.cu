@@ -527,3 +527,133 @@ int kinetic_sum(lqcd_ctx* h, const double* P, double* dev_out)
 {
     return norm2_dev(h, P, (int64_t)32 * h->g.V, dev_out);
 }
+
+// ---------------------------------------------------------------------------
+// Gauge action for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs while another
+// framework owns the whole device memory pool, real-time or signal-safe host
+// threads that must not trigger the implicit device synchronisation of an
+// allocation, and hosts that only hand out pre-sized buffers.  They also
+// cannot create an lqcd handle (lqcd_create allocates its workspace), so
+// this entry point takes the gauge field directly and keeps its per-block
+// partial sums in a fixed array compiled into the library.
+//
+// The array is a file-scope __device__ variable of 16384 doubles (128 KiB);
+// every GPU that loads the library holds it until the process exits.  One
+// block of 128 threads handles 128 sites, so at most 16384 * 128 =
+// 2,097,152 sites (32^3 x 64) fit; larger lattices are rejected with
+// LQCD_ERR_GEOM.  Every call shares the array: the used entries are fully
+// rewritten by each call before they are read (nothing has to start at
+// zero), and calls that overlap on the GPU (different streams, or threads
+// with no ordering between them) race on it.  The device address of the
+// array is looked up with cudaGetSymbolAddress on the first call on each
+// device, with that device current; make that first call before any stream
+// capture.  No cudaMalloc, cudaFree or other allocating routine is called.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+constexpr int STATIC_SITES_PER_BLOCK = 128;
+constexpr int STATIC_MAX_BLOCKS = 16384;
+static __device__ __align__(256) double g_static_partials[STATIC_MAX_BLOCKS];
+
+namespace {
+
+__device__ __forceinline__ void abi_link(const double2* U, int V, int mu, int s, Su3<double>& u)
+{
+    const double2* p = U + ((size_t)mu * V + s) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u.m[k / 3][k % 3] = mk(p[k].x, p[k].y);
+}
+
+__device__ __forceinline__ int abi_site(const Geo& g, const int x[4])
+{
+    return ((x[0] + x[1] + x[2] + x[3]) & 1) * g.Vh + (lex_of(g, x) >> 1);
+}
+
+// Re tr of the six plaquettes at each of this block's sites, read straight
+// from the C-ABI gauge layout; one partial sum per block
+__global__ void __launch_bounds__(STATIC_SITES_PER_BLOCK) k_plaq_static(Geo g, const double2* U, double* part)
+{
+    const int s = blockIdx.x * STATIC_SITES_PER_BLOCK + threadIdx.x;
+    double acc = 0.0;
+    if (s < g.V) {
+        const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
+        int x[4];
+        eo_coords(g, par, i, x);
+        for (int mu = 1; mu < 4; ++mu)
+            for (int nu = 0; nu < mu; ++nu) {
+                int y[4];
+                Su3<double> a, b, c, d, t, r;
+                abi_link(U, g.V, mu, s, a);
+                shifted(g, x, mu, +1, y);
+                abi_link(U, g.V, nu, abi_site(g, y), b);
+                shifted(g, x, nu, +1, y);
+                abi_link(U, g.V, mu, abi_site(g, y), c);
+                abi_link(U, g.V, nu, s, d);
+                su3_mul(a, b, t);
+                su3_mul_nd(t, c, r);
+                su3_mul_nd(r, d, t);
+                acc += t.m[0][0].re + t.m[1][1].re + t.m[2][2].re;
+            }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_plaq_static_final(const double* part, int n, double* out, double beta, double inv_norm)
+{
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += part[k];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) {
+        out[0] = -beta / 3.0 * acc;
+        out[1] = acc * inv_norm;
+    }
+}
+
+std::mutex g_static_mu;
+double* g_static_ptr[128] = {nullptr};
+
+// device address of g_static_partials on the current device (looked up once)
+int static_partials(double** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return LQCD_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_partials) != cudaSuccess || !p) return LQCD_ERR_CUDA;
+        g_static_ptr[dev] = (double*)p;
+    }
+    *out = g_static_ptr[dev];
+    return LQCD_OK;
+}
+
+}  // namespace
+
+extern "C" int lqcd_gauge_action_static(const int L[4], const double* U, double beta, double* out, void* stream)
+{
+    if (!L || !U || !out) return LQCD_ERR_ARG;
+    for (int mu = 0; mu < 4; ++mu)
+        if (L[mu] < 2 || (L[mu] & 1)) return LQCD_ERR_GEOM;
+    const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    const int64_t nblocks = (V + STATIC_SITES_PER_BLOCK - 1) / STATIC_SITES_PER_BLOCK;
+    if (nblocks > STATIC_MAX_BLOCKS) return LQCD_ERR_GEOM;
+    double* part = nullptr;
+    const int st = static_partials(&part);
+    if (st != LQCD_OK) return st;
+    Geo g;
+    for (int mu = 0; mu < 4; ++mu) g.L[mu] = L[mu];
+    g.V = (int)V;
+    g.Vh = g.V / 2;
+    g.V3 = L[1] * L[2] * L[3];
+    g.l0 = 1;
+    g.nb = L[0];
+    g.bc_t = 1;
+    g.Sh = g.V3 / 2;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_plaq_static<<<(unsigned)nblocks, STATIC_SITES_PER_BLOCK, 0, s>>>(g, (const double2*)U, part);
+    k_plaq_static_final<<<1, 1024, 0, s>>>(part, (int)nblocks, out, beta, 1.0 / (18.0 * (double)V));
+    return cudaGetLastError() == cudaSuccess ? LQCD_OK : LQCD_ERR_CUDA;
+}

@@ -32,6 +32,7 @@ EXPORTS = [
     "lqcd_block_solve_batched", "lqcd_solve_wilson", "lqcd_schur_apply", "lqcd_pf_force",
     "lqcd_gauge_force", "lqcd_rng_normals", "lqcd_hmc_trajectory", "lqcd_md",
     "lqcd_profile_enable", "lqcd_profile_reset", "lqcd_profile_read", "lqcd_launch_count",
+    "lqcd_gauge_action_static",
 ]
 
 
@@ -98,6 +99,7 @@ def load():
         "lqcd_profile_reset": [vp],
         "lqcd_profile_read": [vp, i, vp, vp, vp],
         "lqcd_launch_count": [vp, vp],
+        "lqcd_gauge_action_static": [C.POINTER(C.c_int * 4), vp, d, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -241,6 +243,14 @@ def lqcd_profile_enable(h, on):
 
 def lqcd_profile_reset(h):
     return _check(h, load().lqcd_profile_reset(h))
+
+
+def lqcd_gauge_action_static(L, U, beta, out, stream=None):
+    """Handle-free, allocation-free gauge action: out (device float64[2])
+    receives S_G and the average plaquette.  For callers that cannot
+    allocate device memory (see include/lqcd.h); returns the status code."""
+    s = C.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    return load().lqcd_gauge_action_static(C.byref((C.c_int * 4)(*L)), _ptr(U), float(beta), _ptr(out), s)
 
 
 def lqcd_launch_count(h):
