@@ -411,7 +411,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f16", choices=["f16", "f32", "f64"])
+    ap.add_argument("--precision", default="f32", choices=["f16", "f32", "f64"],
+                    help="storage of the inner Krylov iterations (outer residuals stay double)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")

@@ -125,7 +125,7 @@ int pf_w1(lqcd_ctx* h, double* F, const double2* phi, double kappa, double coef,
     if (S_dev) LQ_TRY(norm2_dev(h, (const double*)eta, (int64_t)48 * h->g.Vh, S_dev));
     if (!F) return LQCD_OK;
     LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, xi, eta, c.tol, c.max_iter, nullptr, nullptr));
-    return force_bilinear(h, F, xi, eta, MODE_INTRA, kappa * coef, nullptr, nullptr, 0, 0.0);
+    return force_bilinear(h, F, xi, eta, MODE_INTRA, kappa * coef, nullptr, nullptr, 0, 0.0, c.prec);
 }
 
 // F += coef * dS/dw for S = |R^-1 phi|^2 (phi: device boundary coordinates)
@@ -145,7 +145,7 @@ int pf_schur(lqcd_ctx* h, double* F, const double* phi, double kappa, double coe
     LQ_TRY(embed_boundary(h, et, eta));
     LQ_TRY(hop_full(h, MODE_INTRA, 1, 1, E, et, 1.0, et, -kappa));
     LQ_TRY(solve_full(h, MODE_ALL, -1, 1, c.prec, kappa, chi, E, c.tol, c.max_iter, nullptr, nullptr));
-    return force_bilinear(h, F, et, psi, MODE_INTRA, -kappa * coef, chi, psi, MODE_ALL, kappa * coef);
+    return force_bilinear(h, F, et, psi, MODE_INTRA, -kappa * coef, chi, psi, MODE_ALL, kappa * coef, c.prec);
 }
 
 // ---------------------------------------------------------------------------
@@ -236,7 +236,7 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const double2* phi1,
             LQ_TRY(update_links(h, P, o.dt));
             continue;
         }
-        if (p.level_gauge == o.level) LQ_TRY(gauge_force_kick(h, P, -o.dt * p.beta / 6.0));
+        if (p.level_gauge == o.level) LQ_TRY(gauge_force_kick(h, P, -o.dt * p.beta / 6.0, p.precision));
         if (p.level_w1 == o.level) {
             LQ_TRY(pf_w1(h, P, phi1, p.kappa, -o.dt, c, nullptr));
             ++*nforce;
@@ -652,7 +652,7 @@ int lqcd_gauge_force(lqcd_t h, double* F, double beta, double* S_out, double* pl
 {
     CHECK_H(h);
     NEED_GAUGE(h);
-    if (F) LQ_TRY(gauge_force_kick(h, F, beta / 6.0));
+    if (F) LQ_TRY(gauge_force_kick(h, F, beta / 6.0, PREC64));
     LQ_TRY(plaquette_sum(h, h->red_out));
     double s;
     LQ_TRY(read_scalars(h, 1, &s));

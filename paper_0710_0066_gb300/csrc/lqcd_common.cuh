@@ -369,10 +369,23 @@ __device__ __forceinline__ void load_link<PREC16>(const GaugeF& g, int mu, int p
 // ---------------------------------------------------------------------------
 enum { MODE_ALL = 0, MODE_INTRA = 1, MODE_CROSS = 2 };
 
+// ld(j, spinor) provides the input spinor at eo index j of parity 1-pout
+template <int P, class Loader>
+__device__ __forceinline__ void hop_site_ld(const Geo& g, int mode, int dag, int pout, int i, Loader ld,
+                                            const GaugeF& U, Spinor<typename Real<P>::T>& acc);
+
 template <int P, bool RO = true>
 __device__ __forceinline__ void hop_site(const Geo& g, int mode, int dag, int pout, int i,
                                          const SpinorF& in, const GaugeF& U,
                                          Spinor<typename Real<P>::T>& acc)
+{
+    hop_site_ld<P>(g, mode, dag, pout, i,
+                   [&](int j, Spinor<typename Real<P>::T>& s) { load_spinor<P, RO>(in, j, s); }, U, acc);
+}
+
+template <int P, class Loader>
+__device__ __forceinline__ void hop_site_ld(const Geo& g, int mode, int dag, int pout, int i, Loader ld,
+                                            const GaugeF& U, Spinor<typename Real<P>::T>& acc)
 {
     typedef typename Real<P>::T T;
 #pragma unroll
@@ -400,7 +413,7 @@ __device__ __forceinline__ void hop_site(const Geo& g, int mode, int dag, int po
             }
             if (use) {
                 Spinor<T> ps;
-                load_spinor<P, RO>(in, nl >> 1, ps);
+                ld(nl >> 1, ps);
                 Su3<T> u;
                 load_link<P>(U, mu, pout, i, u);
                 HalfSp<T> h, w;
@@ -430,7 +443,7 @@ __device__ __forceinline__ void hop_site(const Geo& g, int mode, int dag, int po
             }
             if (use) {
                 Spinor<T> ps;
-                load_spinor<P, RO>(in, nl >> 1, ps);
+                ld(nl >> 1, ps);
                 Su3<T> u;
                 load_link<P>(U, mu, pin, nl >> 1, u);
                 HalfSp<T> h, w;
@@ -568,9 +581,11 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
              const double2* b_e, double tol, int max_iter, int* iters_sys, double* resid_sys);
 
 // force.cu
+// prec: PREC64 runs the link arithmetic in double, otherwise in single
+// precision on the single-precision links (results accumulated in double)
 int force_bilinear(lqcd_ctx* h, double* F, const double2* a1, const double2* b1, int mask1,
-                   double coef1, const double2* a2, const double2* b2, int mask2, double coef2);
-int gauge_force_kick(lqcd_ctx* h, double* F, double coef);
+                   double coef1, const double2* a2, const double2* b2, int mask2, double coef2, int prec);
+int gauge_force_kick(lqcd_ctx* h, double* F, double coef, int prec);
 int plaquette_sum(lqcd_ctx* h, double* dev_out);
 int update_links(lqcd_ctx* h, const double* P, double dt);
 int roll_links(lqcd_ctx* h, int shift);

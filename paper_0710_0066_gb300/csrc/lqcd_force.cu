@@ -34,19 +34,21 @@ __device__ __forceinline__ void shifted(const Geo& g, const int x[4], int mu, in
 }
 
 // 2 Im tr(T^a Y) for the eight Gell-Mann generators T^a = lambda^a / 2
-__device__ __forceinline__ void lie_im2(const Su3<double>& Y, double f[8])
+template <class T>
+__device__ __forceinline__ void lie_im2(const Su3<T>& Y, double f[8])
 {
-    f[0] = Y.m[1][0].im + Y.m[0][1].im;
-    f[1] = Y.m[0][1].re - Y.m[1][0].re;
-    f[2] = Y.m[0][0].im - Y.m[1][1].im;
-    f[3] = Y.m[2][0].im + Y.m[0][2].im;
-    f[4] = Y.m[0][2].re - Y.m[2][0].re;
-    f[5] = Y.m[2][1].im + Y.m[1][2].im;
-    f[6] = Y.m[1][2].re - Y.m[2][1].re;
-    f[7] = (Y.m[0][0].im + Y.m[1][1].im - 2.0 * Y.m[2][2].im) * INV_SQRT3;
+    f[0] = (double)(Y.m[1][0].im + Y.m[0][1].im);
+    f[1] = (double)(Y.m[0][1].re - Y.m[1][0].re);
+    f[2] = (double)(Y.m[0][0].im - Y.m[1][1].im);
+    f[3] = (double)(Y.m[2][0].im + Y.m[0][2].im);
+    f[4] = (double)(Y.m[0][2].re - Y.m[2][0].re);
+    f[5] = (double)(Y.m[2][1].im + Y.m[1][2].im);
+    f[6] = (double)(Y.m[1][2].re - Y.m[2][1].re);
+    f[7] = (double)(Y.m[0][0].im + Y.m[1][1].im - T(2) * Y.m[2][2].im) * INV_SQRT3;
 }
 
-__device__ __forceinline__ void su3_mul(const Su3<double>& a, const Su3<double>& b, Su3<double>& c)
+template <class T>
+__device__ __forceinline__ void su3_mul(const Su3<T>& a, const Su3<T>& b, Su3<T>& c)
 {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -54,7 +56,8 @@ __device__ __forceinline__ void su3_mul(const Su3<double>& a, const Su3<double>&
         for (int j = 0; j < 3; ++j) c.m[i][j] = a.m[i][0] * b.m[0][j] + a.m[i][1] * b.m[1][j] + a.m[i][2] * b.m[2][j];
 }
 // c = a b^dag
-__device__ __forceinline__ void su3_mul_nd(const Su3<double>& a, const Su3<double>& b, Su3<double>& c)
+template <class T>
+__device__ __forceinline__ void su3_mul_nd(const Su3<T>& a, const Su3<T>& b, Su3<T>& c)
 {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -62,17 +65,9 @@ __device__ __forceinline__ void su3_mul_nd(const Su3<double>& a, const Su3<doubl
         for (int j = 0; j < 3; ++j)
             c.m[i][j] = a.m[i][0] * conjx(b.m[j][0]) + a.m[i][1] * conjx(b.m[j][1]) + a.m[i][2] * conjx(b.m[j][2]);
 }
-// c = a^dag b
-__device__ __forceinline__ void su3_mul_dn(const Su3<double>& a, const Su3<double>& b, Su3<double>& c)
-{
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            c.m[i][j] = cjmul(a.m[0][i], b.m[0][j]) + cjmul(a.m[1][i], b.m[1][j]) + cjmul(a.m[2][i], b.m[2][j]);
-}
 
-__device__ __forceinline__ void outer_acc(const HalfSp<double>& hb, const HalfSp<double>& ha, Su3<double>& X)
+template <class T>
+__device__ __forceinline__ void outer_acc(const HalfSp<T>& hb, const HalfSp<T>& ha, Su3<T>& X)
 {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -82,105 +77,115 @@ __device__ __forceinline__ void outer_acc(const HalfSp<double>& hb, const HalfSp
 }
 
 struct BilTerm {
-    SpinorF a[2], b[2];  // parity views of the full fields
+    SpinorF a[2], b[2];  // parity views of the full double fields
     int mask;
     double coef;
     int on;
 };
 
-__device__ void bilinear_term(const Geo& g, const GaugeF& U, const BilTerm& T, int par, int i,
-                              const int x[4], double f[4][8])
+template <class T>
+__device__ __forceinline__ void load_as(const SpinorF& f, int i, Spinor<T>& s)
 {
-    Spinor<double> ax, bx;
-    load_spinor<PREC64>(T.a[par], i, ax);
-    load_spinor<PREC64>(T.b[par], i, bx);
-#pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-        const bool wrap = (x[mu] == g.L[mu] - 1);
-        if (mu == 0 && T.mask == MODE_INTRA && ((x[0] + 1) % g.l0) == 0) continue;
-        int y[4], py, iy;
-        shifted(g, x, mu, +1, y);
-        site_at(g, y, py, iy);
-        Spinor<double> ay, by;
-        load_spinor<PREC64>(T.a[py], iy, ay);
-        load_spinor<PREC64>(T.b[py], iy, by);
-        HalfSp<double> hax, hby, hay, hbx;
-        project(mu, -1, ax, hax);
-        project(mu, -1, by, hby);
-        project(mu, +1, ay, hay);
-        project(mu, +1, bx, hbx);
-        Su3<double> X1, X2, u, Y, t1, t2;
+    Spinor<double> d;
+    load_spinor<PREC64>(f, i, d);
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) X1.m[r][c] = X2.m[r][c] = mk(0.0, 0.0);
-        outer_acc(hby, hax, X1);
-        outer_acc(hbx, hay, X2);
-        load_link<PREC64>(U, mu, par, i, u);
-        su3_mul(u, X1, t1);
-        su3_mul_nd(X2, u, t2);
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) Y.m[r][c] = t1.m[r][c] - t2.m[r][c];
-        double l[8];
-        lie_im2(Y, l);
-        const double ph = (mu == 0 && wrap && g.bc_t < 0) ? -1.0 : 1.0;
-        const double s = -T.coef * ph;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) f[mu][k] += s * l[k];
-    }
+        for (int c = 0; c < 3; ++c) s.c[a][c] = mk((T)d.c[a][c].re, (T)d.c[a][c].im);
 }
 
-// F[mu][site][a] += sum over the (up to two) terms
-__global__ void __launch_bounds__(BS) k_bilinear(Geo g, GaugeF U, double* F, BilTerm T1, BilTerm T2)
+// one term for the link (x, mu) in the arithmetic of link precision PL
+template <int PL>
+__device__ __forceinline__ void bilinear_link(const Geo& g, const GaugeF& U, const BilTerm& T, int mu, int par,
+                                              int i, const int x[4], double f[8])
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.V) return;
-    const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
-    int x[4];
-    eo_coords(g, par, i, x);
-    double f[4][8];
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) f[mu][k] = 0.0;
-    if (T1.on) bilinear_term(g, U, T1, par, i, x, f);
-    if (T2.on) bilinear_term(g, U, T2, par, i, x, f);
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-        double* d = F + ((size_t)mu * g.V + s) * 8;
-        double4* d4 = (double4*)d;
-        double4 a = d4[0], b = d4[1];
-        a.x += f[mu][0]; a.y += f[mu][1]; a.z += f[mu][2]; a.w += f[mu][3];
-        b.x += f[mu][4]; b.y += f[mu][5]; b.z += f[mu][6]; b.w += f[mu][7];
-        d4[0] = a;
-        d4[1] = b;
+    typedef typename Real<PL>::T R;
+    if (mu == 0 && T.mask == MODE_INTRA && ((x[0] + 1) % g.l0) == 0) return;
+    const bool wrap = (x[mu] == g.L[mu] - 1);
+    int y[4], py, iy;
+    shifted(g, x, mu, +1, y);
+    site_at(g, y, py, iy);
+    HalfSp<R> hax, hby, hay, hbx;
+    {
+        Spinor<R> s;
+        load_as(T.a[par], i, s);
+        project(mu, -1, s, hax);
+        load_as(T.b[par], i, s);
+        project(mu, +1, s, hbx);
+        load_as(T.a[py], iy, s);
+        project(mu, +1, s, hay);
+        load_as(T.b[py], iy, s);
+        project(mu, -1, s, hby);
     }
-}
-
-// staple sum A with U_mu(x) A the sum of the six plaquettes through the link
-__device__ void staple(const Geo& g, const GaugeF& U, const int x[4], int mu, Su3<double>& A)
-{
+    Su3<R> X1, X2, u, Y, t1, t2;
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) A.m[r][c] = mk(0.0, 0.0);
+        for (int c = 0; c < 3; ++c) X1.m[r][c] = X2.m[r][c] = mk(R(0), R(0));
+    outer_acc(hby, hax, X1);
+    outer_acc(hbx, hay, X2);
+    load_link<PL>(U, mu, par, i, u);
+    su3_mul(u, X1, t1);
+    su3_mul_nd(X2, u, t2);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Y.m[r][c] = t1.m[r][c] - t2.m[r][c];
+    double l[8];
+    lie_im2(Y, l);
+    const double ph = (mu == 0 && wrap && g.bc_t < 0) ? -1.0 : 1.0;
+    const double s = -T.coef * ph;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] += s * l[k];
+}
+
+// F[mu][site][a] += sum over the (up to two) terms; one thread per link
+template <int PL>
+__global__ void __launch_bounds__(BS) k_bilinear(Geo g, GaugeF U, double* F, BilTerm T1, BilTerm T2)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * g.V) return;
+    const int mu = t / g.V, s = t - mu * g.V;
+    const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
+    int x[4];
+    eo_coords(g, par, i, x);
+    double f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = 0.0;
+    if (T1.on) bilinear_link<PL>(g, U, T1, mu, par, i, x, f);
+    if (T2.on) bilinear_link<PL>(g, U, T2, mu, par, i, x, f);
+    double4* d4 = (double4*)(F + ((size_t)mu * g.V + s) * 8);
+    double4 a = d4[0], b = d4[1];
+    a.x += f[0]; a.y += f[1]; a.z += f[2]; a.w += f[3];
+    b.x += f[4]; b.y += f[5]; b.z += f[6]; b.w += f[7];
+    d4[0] = a;
+    d4[1] = b;
+}
+
+// staple sum A with U_mu(x) A the sum of the six plaquettes through the link
+template <int P>
+__device__ void staple(const Geo& g, const GaugeF& U, const int x[4], int mu, Su3<typename Real<P>::T>& A)
+{
+    typedef typename Real<P>::T R;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A.m[r][c] = mk(R(0), R(0));
     int xm[4];
     shifted(g, x, mu, +1, xm);
 #pragma unroll 1
     for (int nu = 0; nu < 4; ++nu) {
         if (nu == mu) continue;
         int y[4], p, i;
-        Su3<double> a, b, c, t, s;
+        Su3<R> a, b, c, t, s;
         // up: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
         site_at(g, xm, p, i);
-        load_link<PREC64>(U, nu, p, i, a);
+        load_link<P>(U, nu, p, i, a);
         shifted(g, x, nu, +1, y);
         site_at(g, y, p, i);
-        load_link<PREC64>(U, mu, p, i, b);
+        load_link<P>(U, mu, p, i, b);
         site_at(g, x, p, i);
-        load_link<PREC64>(U, nu, p, i, c);
+        load_link<P>(U, nu, p, i, c);
         su3_mul_nd(a, b, t);
         su3_mul_nd(t, c, s);
 #pragma unroll
@@ -190,11 +195,11 @@ __device__ void staple(const Geo& g, const GaugeF& U, const int x[4], int mu, Su
         // down: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
         shifted(g, xm, nu, -1, y);
         site_at(g, y, p, i);
-        load_link<PREC64>(U, nu, p, i, a);
+        load_link<P>(U, nu, p, i, a);
         shifted(g, x, nu, -1, y);
         site_at(g, y, p, i);
-        load_link<PREC64>(U, mu, p, i, b);
-        load_link<PREC64>(U, nu, p, i, c);
+        load_link<P>(U, mu, p, i, b);
+        load_link<P>(U, nu, p, i, c);
         // t = a^dag b^dag = (b a)^dag
         su3_mul(b, a, s);
 #pragma unroll
@@ -210,17 +215,19 @@ __device__ void staple(const Geo& g, const GaugeF& U, const int x[4], int mu, Su
 }
 
 // F += coef * dS_G/dw^a,  dS_G/dw^a = -beta/3 Re tr(i T^a U A) = beta/6 * 2 Im tr(T^a U A)
+template <int P>
 __global__ void __launch_bounds__(BS) k_gauge_force(Geo g, GaugeF U, double* F, double c)
 {
+    typedef typename Real<P>::T R;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * g.V) return;
     const int mu = t / g.V, s = t - mu * g.V;
     const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
     int x[4];
     eo_coords(g, par, i, x);
-    Su3<double> A, u, Y;
-    staple(g, U, x, mu, A);
-    load_link<PREC64>(U, mu, par, i, u);
+    Su3<R> A, u, Y;
+    staple<P>(g, U, x, mu, A);
+    load_link<P>(U, mu, par, i, u);
     su3_mul(u, A, Y);
     double l[8];
     lie_im2(Y, l);
@@ -473,12 +480,16 @@ static BilTerm make_term(lqcd_ctx* h, const double2* a, const double2* b, int ma
 }
 
 int force_bilinear(lqcd_ctx* h, double* F, const double2* a1, const double2* b1, int mask1, double coef1,
-                   const double2* a2, const double2* b2, int mask2, double coef2)
+                   const double2* a2, const double2* b2, int mask2, double coef2, int prec)
 {
     BilTerm T1 = make_term(h, a1, b1, mask1, coef1), T2 = make_term(h, a2, b2, mask2, coef2);
     cudaEvent_t ev;
     prof_begin(h, 2, &ev);
-    k_bilinear<<<(h->g.V + BS - 1) / BS, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, T1, T2);
+    const int nb = (4 * h->g.V + BS - 1) / BS;
+    if (prec == PREC64)
+        k_bilinear<PREC64><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, T1, T2);
+    else
+        k_bilinear<PREC32><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC32), F, T1, T2);
     LQ_TRY(launch_err(h, "force kernel"));
     const int nt = T1.on + T2.on;
     // per site: two spinors of each term, four links, F read and written
@@ -486,12 +497,16 @@ int force_bilinear(lqcd_ctx* h, double* F, const double2* a1, const double2* b1,
     return LQCD_OK;
 }
 
-int gauge_force_kick(lqcd_ctx* h, double* F, double coef)
+int gauge_force_kick(lqcd_ctx* h, double* F, double coef, int prec)
 {
     // coef * (beta/6) is folded in by the caller
     cudaEvent_t ev;
     prof_begin(h, 3, &ev);
-    k_gauge_force<<<(4 * h->g.V + BS - 1) / BS, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, coef);
+    const int nb = (4 * h->g.V + BS - 1) / BS;
+    if (prec == PREC64)
+        k_gauge_force<PREC64><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, coef);
+    else
+        k_gauge_force<PREC32><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC32), F, coef);
     LQ_TRY(launch_err(h, "gauge force kernel"));
     prof_end(h, 3, ev, (double)h->g.V * (4.0 * 144.0 + 2.0 * 256.0));
     return LQCD_OK;

@@ -8,12 +8,17 @@
 //   inner loop (double, single or half storage, FP32 arithmetic):
 //     BiCGstab on A e = r / |r| to a relative residual inner_tol;
 //   x += |r| e.
-// All systems iterate together; a converged system stops updating.  Every
-// reduction is per system, in double, in a fixed order (warp shuffles, then
-// the per-CTA partials summed in CTA order), so results are deterministic
-// and identical in every CTA.  The CTAs meet at a software grid barrier
-// whose wait is bounded (about two seconds): on time-out the kernel records
-// LQCD_ERR_TIMEOUT and every CTA returns.
+// Each system is handled by its own group of CTAs (cps CTAs per system).
+// Reductions are per system, in double, in a fixed order (warp shuffles,
+// then the group's per-CTA partials summed in CTA order), so every CTA of a
+// group computes bitwise the same scalars and takes the same decisions.
+// Loop termination across systems is agreed through per-system state flags
+// that a group publishes before a barrier and every CTA reads after it.
+// The CTAs meet at a software grid barrier whose wait is bounded (about two
+// seconds): on time-out the kernel records LQCD_ERR_TIMEOUT and every CTA
+// returns.
+#include <stdio.h>
+
 #include <algorithm>
 
 #include "lqcd_common.cuh"
@@ -24,6 +29,9 @@ constexpr int SBS = 256;
 constexpr int NSYS_MAX = 64;
 constexpr int NQ = 3;
 constexpr long long SPIN_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
+
+// per-system state codes in the flag arrays
+enum { F_ACTIVE = 0, F_DONE = 1, F_NAN = 2, F_MAXIT = 3 };
 
 struct SolveArgs {
     Geo g;
@@ -41,6 +49,8 @@ struct SolveArgs {
     double tol, inner_tol;
     int max_iter, max_outer, max_inner;
     double* part;       // [NQ][grid]
+    int* iflag;         // [nsys] inner-loop state
+    int* oflag;         // [nsys] outer-loop state
     unsigned* bar;
     int* status;
     int* iters;         // [nsys]
@@ -48,7 +58,7 @@ struct SolveArgs {
     int* outer_out;
 };
 
-struct SysSt {
+struct SysSt {  // the CTA's own system
     double bn2, rn2, rr, itol2;
     double2 rho, alpha, omega, beta;
     int active, idone, it, itc;
@@ -112,20 +122,43 @@ __device__ void reduce_put(const SolveArgs& A, double a, double b, double c, int
     }
 }
 
-// per-system totals of the partials (every CTA computes all of them)
-__device__ void gather(const SolveArgs& A, int nq, double (*ssum)[NQ])
+// totals of the own system's partials: warp q sums quantity q
+__device__ void gather_own(const SolveArgs& A, int sys, int nq, double* out)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int npairs = A.nsys * nq;
-    for (int k = w; k < npairs; k += SBS / 32) {
-        const int s = k / nq, q = k % nq;
+    if (w < nq) {
+        const double* p = A.part + (size_t)w * gridDim.x + (size_t)sys * A.cps;
         double v = 0.0;
-        for (int c = lane; c < A.cps; c += 32) v += A.part[q * gridDim.x + s * A.cps + c];
+        for (int c = lane; c < A.cps; c += 32) v += p[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) ssum[s][q] = v;
+        if (lane == 0) out[w] = v;
     }
     __syncthreads();
+}
+
+// OR / max over the systems' flags (read by every CTA after a barrier)
+__device__ void read_flags(const int* flags, int nsys, int* any_active, int* worst)
+{
+    __shared__ int s_a, s_w;
+    if (threadIdx.x < 32) {
+        int a = 0, m = 0;
+        for (int s = threadIdx.x; s < nsys; s += 32) {
+            const int f = flags[s];
+            a |= (f == F_ACTIVE);
+            m = max(m, f);
+        }
+        a = __any_sync(0xffffffffu, a);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) {
+            s_a = a;
+            s_w = m;
+        }
+    }
+    __syncthreads();
+    *any_active = s_a;
+    *worst = s_w;
 }
 
 // per-site dot products in the storage arithmetic (T), accumulated over the
@@ -167,22 +200,43 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
 #define FOR_SITES for (int j_ = cin * SBS + (int)threadIdx.x; j_ < A.nsite; j_ += A.cps * SBS)
+// element-wise phases of the single-precision inner solver run over 16-byte
+// words (one float4 = two complex components) instead of whole sites: six
+// times the parallelism and few live registers per thread
+#define FOR_WORDS for (int f_ = cin * SBS + (int)threadIdx.x; f_ < 6 * A.nsite; f_ += A.cps * SBS)
+#define WORD_ADDR const size_t a = (size_t)(f_ / A.nsite) * A.g.Vh + base + (f_ % A.nsite)
+#define W4(f) ((float4*)(f).v)
 #define SYNC_OR_RETURN \
     if (!grid_sync(A, epoch)) return
 
+// y + a x for the two complex numbers of a word
+__device__ __forceinline__ float4 caxpy2(float2 a, float4 x, float4 y)
+{
+    return make_float4(y.x + a.x * x.x - a.y * x.y, y.y + a.x * x.y + a.y * x.x, y.z + a.x * x.z - a.y * x.w,
+                       y.w + a.x * x.w + a.y * x.z);
+}
+__device__ __forceinline__ void cdot2(float4 a, float4 b, double& re, double& im)
+{
+    re += (double)(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
+    im += (double)(a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z);
+}
+__device__ __forceinline__ double nrm2w(float4 a) { return (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w); }
+
 template <int P>
-__global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
+__global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 {
     typedef typename Real<P>::T T;
     constexpr int PE = (P == PREC64) ? PREC64 : PREC32;
     typedef typename Real<PE>::T TE;
+    constexpr bool WORDS = (P == PREC32);
     const int cta = blockIdx.x, tid = threadIdx.x;
     const int sys = cta / A.cps, cin = cta - sys * A.cps;
+    const bool leader = (cin == 0 && tid == 0);  // publishes the system's flags
     const int base = (A.mode == MODE_INTRA) ? (A.slab0 + sys * A.slabstep) * A.g.Sh : 0;
-    __shared__ SysSt S[NSYS_MAX];
-    __shared__ double ssum[NSYS_MAX][NQ];
-    __shared__ int s_ctl;
+    __shared__ SysSt S;
+    __shared__ double red[NQ];
     unsigned epoch = 0;
+    int any_active = 0, worst = 0;
 
     // ---- x = 0, r64 = b, |b|^2
     {
@@ -202,33 +256,32 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
         }
         reduce_put(A, q, 0.0, 0.0, 1);
         SYNC_OR_RETURN;
-        gather(A, 1, ssum);
-        if (tid == 0)
-            for (int s = 0; s < A.nsys; ++s) {
-                S[s].bn2 = ssum[s][0];
-                S[s].rn2 = ssum[s][0];
-                S[s].it = 0;
-            }
+        gather_own(A, sys, 1, red);
+        if (tid == 0) {
+            S.bn2 = red[0];
+            S.rn2 = red[0];
+            S.it = 0;
+        }
         __syncthreads();
     }
 
-    int outer = 0, final_ctl = 0;
+    int outer = 0, final_flag = F_DONE;
     for (;;) {
+        // publish the system's state, then agree on continuing
         if (tid == 0) {
-            int any = 0, maxit = 0, bad = 0;
-            for (int s = 0; s < A.nsys; ++s) {
-                const double lim = A.tol * A.tol * S[s].bn2;
-                const bool nan = !isfinite(S[s].rn2);
-                bad |= nan;
-                S[s].active = (!nan && S[s].rn2 > lim && S[s].bn2 > 0.0) ? 1 : 0;
-                any |= S[s].active;
-                maxit = max(maxit, S[s].it);
+            const bool nan = !isfinite(S.rn2);
+            const bool conv = !(S.rn2 > A.tol * A.tol * S.bn2) || !(S.bn2 > 0.0);
+            S.active = (!nan && !conv) ? 1 : 0;
+            if (leader) {
+                int f = nan ? F_NAN : conv ? F_DONE : F_ACTIVE;
+                if (f == F_ACTIVE && (outer >= A.max_outer || S.it >= A.max_iter)) f = F_MAXIT;
+                A.oflag[sys] = f;
             }
-            s_ctl = bad ? 3 : !any ? 0 : (outer >= A.max_outer || maxit >= A.max_iter) ? 2 : 1;
         }
-        __syncthreads();
-        if (s_ctl != 1) {
-            final_ctl = s_ctl;
+        SYNC_OR_RETURN;
+        read_flags(A.oflag, A.nsys, &any_active, &worst);
+        if (worst >= F_NAN || !any_active) {
+            final_flag = worst;
             break;
         }
         ++outer;
@@ -236,8 +289,24 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
         // ---- inner start: r = rh = p = r64 / |r64|, e = 0
         {
             double q = 0.0;
-            if (S[sys].active) {
-                const double sc = 1.0 / sqrt(S[sys].rn2);
+            if (S.active && WORDS) {
+                const double sc = 1.0 / sqrt(S.rn2);
+                const double2* r6 = (const double2*)A.r64.v;
+                FOR_WORDS
+                {
+                    const int k = f_ / A.nsite, i = base + (f_ % A.nsite);
+                    const size_t a = (size_t)k * A.g.Vh + i;
+                    const double2 d0 = r6[(size_t)(2 * k) * A.g.Vh + i], d1 = r6[(size_t)(2 * k + 1) * A.g.Vh + i];
+                    const float4 w = make_float4((float)(sc * d0.x), (float)(sc * d0.y), (float)(sc * d1.x),
+                                                 (float)(sc * d1.y));
+                    W4(A.r)[a] = w;
+                    W4(A.rh)[a] = w;
+                    W4(A.p)[a] = w;
+                    W4(A.e)[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    q += nrm2w(w);
+                }
+            } else if (S.active) {
+                const double sc = 1.0 / sqrt(S.rn2);
                 FOR_SITES
                 {
                     const int i = base + j_;
@@ -262,30 +331,22 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
             }
             reduce_put(A, q, 0.0, 0.0, 1);
             SYNC_OR_RETURN;
-            gather(A, 1, ssum);
-            if (tid == 0)
-                for (int s = 0; s < A.nsys; ++s) {
-                    S[s].rho = make_double2(ssum[s][0], 0.0);
-                    S[s].idone = !S[s].active;
-                    S[s].itc = 0;
-                    const double need = 0.5 * A.tol * sqrt(S[s].bn2 / fmax(S[s].rn2, 1e-300));
-                    const double it = fmax(A.inner_tol, need);
-                    S[s].itol2 = it * it;
-                }
+            gather_own(A, sys, 1, red);
+            if (tid == 0) {
+                S.rho = make_double2(red[0], 0.0);
+                S.idone = !S.active;
+                S.itc = 0;
+                const double need = 0.5 * A.tol * sqrt(S.bn2 / fmax(S.rn2, 1e-300));
+                const double it = fmax(A.inner_tol, need);
+                S.itol2 = it * it;
+                if (leader) A.iflag[sys] = S.idone ? F_DONE : F_ACTIVE;
+            }
             __syncthreads();
         }
 
-        // ---- BiCGstab
+        // ---- BiCGstab: seven barriers per iteration
         for (;;) {
-            if (tid == 0) {
-                int any = 0;
-                for (int s = 0; s < A.nsys; ++s) any |= (!S[s].idone && S[s].it < A.max_iter);
-                s_ctl = any;
-            }
-            __syncthreads();
-            if (!s_ctl) break;
-            const bool act = !S[sys].idone && S[sys].it < A.max_iter;
-
+            const bool act = !S.idone;
             // tmp = H_oe p
             if (act) FOR_SITES
                 {
@@ -295,6 +356,8 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
                     store_spinor<P>(A.tmp, i, a);
                 }
             SYNC_OR_RETURN;
+            read_flags(A.iflag, A.nsys, &any_active, &worst);
+            if (!any_active) break;
             // v = p - k2 H_eo tmp ; <rh, v>
             {
                 double qr = 0.0, qi = 0.0;
@@ -311,32 +374,37 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
 #pragma unroll
                             for (int c = 0; c < 3; ++c) a.c[s][c] = pp.c[s][c] - k2 * a.c[s][c];
                         store_spinor<P>(A.v, i, a);
-                        load_spinor<P, false>(A.v, i, a);
+                        if (P == PREC16) load_spinor<P, false>(A.v, i, a);
                         load_spinor<P, false>(A.rh, i, rh);
                         cdot_acc(rh, a, qr, qi);
                     }
                 }
                 reduce_put(A, qr, qi, 0.0, 2);
                 SYNC_OR_RETURN;
-                gather(A, 2, ssum);
-                if (tid == 0)
-                    for (int s = 0; s < A.nsys; ++s) {
-                        if (S[s].idone || S[s].it >= A.max_iter) continue;
-                        const double2 d = make_double2(ssum[s][0], ssum[s][1]);
-                        const double2 al = cdiv(S[s].rho, d);
-                        if (!finite2(al) || (d.x == 0.0 && d.y == 0.0)) {
-                            S[s].idone = 1;
-                            S[s].alpha = make_double2(0.0, 0.0);
-                        } else {
-                            S[s].alpha = al;
-                        }
+                gather_own(A, sys, 2, red);
+                if (tid == 0 && act) {
+                    const double2 d = make_double2(red[0], red[1]);
+                    const double2 al = cdiv(S.rho, d);
+                    if (!finite2(al) || (d.x == 0.0 && d.y == 0.0)) {
+                        S.idone = 1;
+                        S.alpha = make_double2(0.0, 0.0);
+                    } else {
+                        S.alpha = al;
                     }
+                }
                 __syncthreads();
             }
-            const bool act2 = act && !S[sys].idone;
+            const bool act2 = act && !S.idone;
             // s = r - alpha v
-            if (act2) {
-                const cx<T> al = mk((T)S[sys].alpha.x, (T)S[sys].alpha.y);
+            if (act2 && WORDS) {
+                const float2 al = make_float2(-(float)S.alpha.x, -(float)S.alpha.y);
+                FOR_WORDS
+                {
+                    WORD_ADDR;
+                    W4(A.s)[a] = caxpy2(al, W4(A.v)[a], W4(A.r)[a]);
+                }
+            } else if (act2) {
+                const cx<T> al = mk((T)S.alpha.x, (T)S.alpha.y);
                 FOR_SITES
                 {
                     const int i = base + j_;
@@ -376,34 +444,46 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
 #pragma unroll
                             for (int c = 0; c < 3; ++c) a.c[s][c] = ss.c[s][c] - k2 * a.c[s][c];
                         store_spinor<P>(A.t, i, a);
-                        load_spinor<P, false>(A.t, i, a);
+                        if (P == PREC16) load_spinor<P, false>(A.t, i, a);
                         cdot_acc(a, ss, qr, qi);
                         qt += nrm_acc(a);
                     }
                 }
                 reduce_put(A, qr, qi, qt, 3);
                 SYNC_OR_RETURN;
-                gather(A, 3, ssum);
-                if (tid == 0)
-                    for (int s = 0; s < A.nsys; ++s) {
-                        if (S[s].idone || S[s].it >= A.max_iter) continue;
-                        const double tt = ssum[s][2];
-                        const double2 om = make_double2(ssum[s][0] / tt, ssum[s][1] / tt);
-                        if (!(tt > 0.0) || !finite2(om)) {
-                            S[s].omega = make_double2(0.0, 0.0);
-                            S[s].idone = 2;  // keep alpha p, stop afterwards
-                        } else {
-                            S[s].omega = om;
-                        }
+                gather_own(A, sys, 3, red);
+                if (tid == 0 && act2) {
+                    const double tt = red[2];
+                    const double2 om = make_double2(red[0] / tt, red[1] / tt);
+                    if (!(tt > 0.0) || !finite2(om)) {
+                        S.omega = make_double2(0.0, 0.0);
+                        S.idone = 2;  // keep alpha p, stop afterwards
+                    } else {
+                        S.omega = om;
                     }
+                }
                 __syncthreads();
             }
             // e += alpha p + omega s ; r = s - omega t ; <rh, r>, |r|^2
             {
                 double qr = 0.0, qi = 0.0, qn = 0.0;
-                if (act2) {
-                    const cx<T> al = mk((T)S[sys].alpha.x, (T)S[sys].alpha.y);
-                    const cx<T> om = mk((T)S[sys].omega.x, (T)S[sys].omega.y);
+                if (act2 && WORDS) {
+                    const float2 al = make_float2((float)S.alpha.x, (float)S.alpha.y);
+                    const float2 om = make_float2((float)S.omega.x, (float)S.omega.y);
+                    const float2 mom = make_float2(-om.x, -om.y);
+                    FOR_WORDS
+                    {
+                        WORD_ADDR;
+                        const float4 ss = W4(A.s)[a];
+                        W4(A.e)[a] = caxpy2(om, ss, caxpy2(al, W4(A.p)[a], W4(A.e)[a]));
+                        const float4 rr = caxpy2(mom, W4(A.t)[a], ss);
+                        W4(A.r)[a] = rr;
+                        cdot2(W4(A.rh)[a], rr, qr, qi);
+                        qn += nrm2w(rr);
+                    }
+                } else if (act2) {
+                    const cx<T> al = mk((T)S.alpha.x, (T)S.alpha.y);
+                    const cx<T> om = mk((T)S.omega.x, (T)S.omega.y);
                     FOR_SITES
                     {
                         const int i = base + j_;
@@ -423,7 +503,7 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
                             }
                         store_spinor<PE>(A.e, i, ee);
                         store_spinor<P>(A.r, i, ss);
-                        load_spinor<P, false>(A.r, i, ss);
+                        if (P == PREC16) load_spinor<P, false>(A.r, i, ss);
                         load_spinor<P, false>(A.rh, i, rh);
                         cdot_acc(rh, ss, qr, qi);
                         qn += nrm_acc(ss);
@@ -431,29 +511,37 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
                 }
                 reduce_put(A, qr, qi, qn, 3);
                 SYNC_OR_RETURN;
-                gather(A, 3, ssum);
-                if (tid == 0)
-                    for (int s = 0; s < A.nsys; ++s) {
-                        if (S[s].idone == 1 || S[s].it >= A.max_iter) continue;
-                        S[s].it += 1;
-                        S[s].itc += 1;
-                        if (S[s].itc >= A.max_inner) S[s].idone = 2;
-                        const double2 rn = make_double2(ssum[s][0], ssum[s][1]);
-                        S[s].rr = ssum[s][2];
-                        if (S[s].idone == 2 || !(S[s].rr > S[s].itol2) || !finite2(rn)) {
-                            S[s].idone = 1;
-                            continue;
-                        }
-                        S[s].beta = cmul(cdiv(rn, S[s].rho), cdiv(S[s].alpha, S[s].omega));
-                        if (!finite2(S[s].beta)) S[s].idone = 1;
-                        S[s].rho = rn;
+                gather_own(A, sys, 3, red);
+                if (tid == 0 && act2) {
+                    S.it += 1;
+                    S.itc += 1;
+                    const double2 rn = make_double2(red[0], red[1]);
+                    S.rr = red[2];
+                    if (S.idone == 2 || S.itc >= A.max_inner || S.it >= A.max_iter || !(S.rr > S.itol2) ||
+                        !finite2(rn)) {
+                        S.idone = 1;
+                    } else {
+                        S.beta = cmul(cdiv(rn, S.rho), cdiv(S.alpha, S.omega));
+                        if (!finite2(S.beta)) S.idone = 1;
+                        S.rho = rn;
                     }
+                }
+                if (tid == 0 && S.idone) S.idone = 1;
+                if (leader) A.iflag[sys] = S.idone ? F_DONE : F_ACTIVE;
                 __syncthreads();
             }
             // p = r + beta (p - omega v)
-            if (act2 && !S[sys].idone) {
-                const cx<T> be = mk((T)S[sys].beta.x, (T)S[sys].beta.y);
-                const cx<T> om = mk((T)S[sys].omega.x, (T)S[sys].omega.y);
+            if (act2 && !S.idone && WORDS) {
+                const float2 be = make_float2((float)S.beta.x, (float)S.beta.y);
+                const float2 mom = make_float2(-(float)S.omega.x, -(float)S.omega.y);
+                FOR_WORDS
+                {
+                    WORD_ADDR;
+                    W4(A.p)[a] = caxpy2(be, caxpy2(mom, W4(A.v)[a], W4(A.p)[a]), W4(A.r)[a]);
+                }
+            } else if (act2 && !S.idone) {
+                const cx<T> be = mk((T)S.beta.x, (T)S.beta.y);
+                const cx<T> om = mk((T)S.omega.x, (T)S.omega.y);
                 FOR_SITES
                 {
                     const int i = base + j_;
@@ -472,8 +560,21 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
         }
 
         // ---- x += |r64| e (double)
-        if (S[sys].active) {
-            const double sc = sqrt(S[sys].rn2);
+        if (S.active && WORDS) {
+            const double sc = sqrt(S.rn2);
+            double2* xx = (double2*)A.x.v;
+            FOR_WORDS
+            {
+                const int k = f_ / A.nsite, i = base + (f_ % A.nsite);
+                const float4 w = W4(A.e)[(size_t)k * A.g.Vh + i];
+                double2* x0 = xx + (size_t)(2 * k) * A.g.Vh + i;
+                double2* x1 = xx + (size_t)(2 * k + 1) * A.g.Vh + i;
+                const double2 a0 = *x0, a1 = *x1;
+                *x0 = make_double2(a0.x + sc * w.x, a0.y + sc * w.y);
+                *x1 = make_double2(a1.x + sc * w.z, a1.y + sc * w.w);
+            }
+        } else if (S.active) {
+            const double sc = sqrt(S.rn2);
             FOR_SITES
             {
                 const int i = base + j_;
@@ -491,7 +592,7 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
         }
         SYNC_OR_RETURN;
         // ---- t64 = H_oe x (double)
-        if (S[sys].active) FOR_SITES
+        if (S.active) FOR_SITES
             {
                 const int i = base + j_;
                 Spinor<double> a;
@@ -502,7 +603,7 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
         // ---- r64 = b - x + k2 H_eo t64 ; |r64|^2
         {
             double q = 0.0;
-            if (S[sys].active) {
+            if (S.active) {
                 FOR_SITES
                 {
                     const int i = base + j_;
@@ -520,26 +621,25 @@ __global__ void __launch_bounds__(SBS) k_solve(SolveArgs A)
             }
             reduce_put(A, q, 0.0, 0.0, 1);
             SYNC_OR_RETURN;
-            gather(A, 1, ssum);
-            if (tid == 0)
-                for (int s = 0; s < A.nsys; ++s)
-                    if (S[s].active) S[s].rn2 = ssum[s][0];
+            gather_own(A, sys, 1, red);
+            if (tid == 0 && S.active) S.rn2 = red[0];
             __syncthreads();
         }
     }
 
-    if (cta == 0 && tid == 0) {
-        for (int s = 0; s < A.nsys; ++s) {
-            A.iters[s] = S[s].it;
-            A.resid[s] = S[s].bn2 > 0.0 ? sqrt(S[s].rn2 / S[s].bn2) : 0.0;
-        }
-        *A.outer_out = outer;
-        if (final_ctl == 3) atomicCAS(A.status, 0, LQCD_ERR_NAN);
-        if (final_ctl == 2) atomicCAS(A.status, 0, LQCD_ERR_NOCONVERGE);
+    if (leader) {
+        A.iters[sys] = S.it;
+        A.resid[sys] = S.bn2 > 0.0 ? sqrt(S.rn2 / S.bn2) : 0.0;
+        if (sys == 0) *A.outer_out = outer;
+        if (final_flag == F_NAN) atomicCAS(A.status, 0, LQCD_ERR_NAN);
+        if (final_flag == F_MAXIT) atomicCAS(A.status, 0, LQCD_ERR_NOCONVERGE);
     }
 }
 
 #undef FOR_SITES
+#undef FOR_WORDS
+#undef WORD_ADDR
+#undef W4
 #undef SYNC_OR_RETURN
 
 }  // namespace
@@ -552,6 +652,7 @@ struct Work {
     double2* r64 = nullptr;
     double2* t64 = nullptr;
     double* part = nullptr;
+    int* flags = nullptr;         // [2][NSYS_MAX]
     unsigned* bar = nullptr;
     int* status = nullptr;
     int* iters = nullptr;
@@ -590,6 +691,7 @@ int solver_init(lqcd_ctx* h)
         gm = std::max(gm, w->gmax[k]);
     }
     LQ_CUDA(h, cudaMalloc(&w->part, sizeof(double) * NQ * (size_t)gm));
+    LQ_CUDA(h, cudaMalloc(&w->flags, sizeof(int) * 2 * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->bar, sizeof(unsigned) * 4));
     LQ_CUDA(h, cudaMalloc(&w->status, sizeof(int) * 4));
     LQ_CUDA(h, cudaMalloc(&w->iters, sizeof(int) * NSYS_MAX));
@@ -608,6 +710,7 @@ void solver_free(lqcd_ctx* h)
     cudaFree(w->r64);
     cudaFree(w->t64);
     cudaFree(w->part);
+    cudaFree(w->flags);
     cudaFree(w->bar);
     cudaFree(w->status);
     cudaFree(w->iters);
@@ -677,6 +780,8 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.max_outer = prec == PREC64 ? 8 : 40;
     A.max_inner = prec == PREC64 ? max_iter : prec == PREC32 ? 4000 : 600;
     A.part = w->part;
+    A.iflag = w->flags;
+    A.oflag = w->flags + NSYS_MAX;
     A.bar = w->bar;
     A.status = w->status;
     A.iters = w->iters;

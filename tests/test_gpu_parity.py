@@ -142,7 +142,10 @@ def test_pf_force_w1(setup, prec):
     S, F = lat.pf_force(cuda(phi), kappa, lqcd.TERM_W1, prec, tol=1e-12)
     So, Fo = olat.pf_w1(U, kappa, phi, tol=1e-13)
     assert abs(S - So) < 1e-9 * So
-    assert rel(F, Fo) < 1e-7
+    # double link arithmetic for the double form; the mixed forms evaluate the
+    # force in single precision (unit roundoff 6e-8 over ~30-term sums),
+    # within the 1e-5 force tolerance
+    assert rel(F, Fo) < (1e-9 if prec == lqcd.PREC_F64 else 1e-5)
 
 
 @pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32])
@@ -152,7 +155,10 @@ def test_pf_force_schur(setup, prec):
     S, F = lat.pf_force(cuda(phi), kappa, lqcd.TERM_SCHUR, prec, tol=1e-12)
     So, Fo = olat.pf_schur(U, kappa, phi, route=1, tol=1e-13)
     assert abs(S - So) < 1e-9 * So
-    assert rel(F, Fo) < 1e-7
+    # double link arithmetic for the double form; the mixed forms evaluate the
+    # force in single precision (unit roundoff 6e-8 over ~30-term sums),
+    # within the 1e-5 force tolerance
+    assert rel(F, Fo) < (1e-9 if prec == lqcd.PREC_F64 else 1e-5)
 
 
 def test_rng_normals_match_oracle(setup):
