@@ -306,6 +306,23 @@ def run_ours(args):
             dslash[name] = {"gbs": by / ms / 1e6, "ms": ms / n, "bytes_per_launch": by / n}
         latd.close()
 
+    # ---- force-profile diagnostic (Sec. 3, Fig. 1) on the thermalised field:
+    # mean |F| on space-like links per time slice for each action term
+    profile = {}
+    if not args.no_dslash:
+        lat.set_gauge(U)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(WL["seed"] + 11)
+        eta1 = torch.randn((lat.V, 4, 3), dtype=torch.complex128, device="cuda", generator=g) * math.sqrt(0.5)
+        phi1 = lat.block_dslash(eta1, WL["kappa"])
+        eta2 = torch.randn(lat.boundary().shape, dtype=torch.complex128, device="cuda", generator=g) * math.sqrt(0.5)
+        phi2 = lat.schur(eta2.contiguous(), WL["kappa"], lqcd.SCHUR_R, lqcd.PREC_F32, tol=WL["tol"])
+        _, Fw = lat.pf_force(phi1, WL["kappa"], lqcd.TERM_W1, lqcd.PREC_F32, tol=WL["tol"])
+        _, Fs = lat.pf_force(phi2, WL["kappa"], lqcd.TERM_SCHUR, lqcd.PREC_F32, tol=WL["tol"])
+        _, _, Fg = lat.gauge_force(WL["beta"])
+        for name, F in (("gauge", Fg), ("w1", Fw), ("schur", Fs)):
+            profile[name] = [round(v, 5) for v in lat.force_profile(F)[0].tolist()]
+
     # ---- oracle on the host cores (bounded sample)
     site_iters = statistics.mean(r.site_iters for r in results)
     m_apps = 4.0 * site_iters / lat.V
@@ -333,6 +350,7 @@ def run_ours(args):
                      "peak_kind": peak_kind, "launches": n_sol,
                      "kernel_share_of_step": ms_sol / total_ms if total_ms else None},
         "dslash": dslash,
+        "force_profile_spatial": profile,
         "fp64_form": fp64,
         "thermalisation": {"trajectories": WL["therm"], "plaq": rth.plaq if rth else None},
         "trajectory": {"dH": [r.dH for r in results], "accepted": [r.accepted for r in results],

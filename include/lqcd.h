@@ -163,6 +163,13 @@ int lqcd_pf_force(lqcd_t h, double* F, const double* phi, double kappa, int term
  * receive S_G and the average Re tr P / 3.  Synchronous. */
 int lqcd_gauge_force(lqcd_t h, double* F, double beta, double* S_out, double* plaq_out);
 
+/* Average force per time slice, the diagnostic of Sec. 3 (Fig. 1: "average
+ * force on spatial links as a function of x0"): out (device double[2][L0])
+ * receives, for each x0, the mean over the slice's space-like links
+ * (row 0) and time-like links (row 1) of |F| = (sum_a F_a^2)^(1/2).
+ * F: device forces double[4][V][8] (e.g. from lqcd_pf_force).  Asynchronous. */
+int lqcd_force_profile(lqcd_t h, const double* F, double* out);
+
 /* Philox4x32-10 normal deviates (Salmon et al., SC'11) as used by the HMC
  * heatbath: out[k] (device double[n]) for counter (k/2 lo, k/2 hi, stream,
  * traj) and key (seed lo, seed hi); two 53-bit uniforms per counter and
@@ -187,6 +194,16 @@ typedef struct {
     int precision;      /* LQCD_PREC_* for every solve */
     double tol;         /* relative residual of every solve */
     int max_iter;
+    /* position-dependent step size (Sec. 2): the step of link U_mu(x) is
+     * dt * s(x0), one table for space-like and one for time-like links.
+     * step_scheme: 0 none (s = 1), 1/2/3 the paper's schemes A (period 6),
+     * B (period 8), C (period 16), repeated along x0 (L0 must be a multiple
+     * of the period; scheme A's space-like s(5) is read as 0.2, the value
+     * that gives the stated average 0.525).  step_scale: optional host
+     * table double[2][L0] (row 0 space-like, row 1 time-like) overriding
+     * step_scheme.  s = 0 freezes a link. */
+    int step_scheme;
+    const double* step_scale;
 } lqcd_hmc_params;
 
 typedef struct {

@@ -947,6 +947,81 @@ static void reunit(cplx* u)
     u[8] = conj(u[0] * u[4] - u[1] * u[3]);
 }
 
+/* average force per time slice (Sec. 3, Fig. 1): out[x0] = mean over the
+ * space-like links of slice x0 of |F| (Euclidean norm of the 8 coefficients),
+ * out[L0 + x0] the same for the time-like links */
+void lqo_force_profile(const lqo_geom* gi, const double* F, double* out)
+{
+    G g = mkg(gi);
+    memset(out, 0, sizeof(double) * 2 * g.L[0]);
+    for (int s = 0; s < g.V; ++s) {
+        int x[4];
+        coords_of(&g, s, x);
+        for (int mu = 0; mu < 4; ++mu) {
+            double n = 0;
+            for (int a = 0; a < 8; ++a) n += F[((size_t)mu * g.V + s) * 8 + a] * F[((size_t)mu * g.V + s) * 8 + a];
+            out[(mu == 0 ? g.L[0] : 0) + x[0]] += sqrt(n);
+        }
+    }
+    for (int t = 0; t < g.L[0]; ++t) {
+        out[t] /= 3.0 * g.V3;
+        out[g.L[0] + t] /= g.V3;
+    }
+}
+
+/* position-dependent step size (Sec. 2): the step of link U_mu(x) is
+ * dt * s(x0) with one table for space-like and one for time-like links,
+ * repeated with the scheme's period along x0.  scale: [2][L0] (row 0
+ * space-like, row 1 time-like) or NULL for s = 1. */
+static double link_scale(const G* g, const double* scale, size_t l)
+{
+    if (!scale) return 1.0;
+    int mu = (int)(l / g->V), s = (int)(l % g->V), x[4];
+    coords_of(g, s, x);
+    return scale[(mu == 0 ? g->L[0] : 0) + x[0]];
+}
+
+/* the schemes of Sec. 2 as [2][L0] tables; returns -1 when L0 is not a
+ * multiple of the period.  Scheme A's space-like value at x0 = 5 is printed
+ * as "2"; 0.2 is the value that reproduces the stated average 0.525. */
+int lqo_step_scheme(int scheme, int L0, double* out)
+{
+    static const double As[6] = {0.2, 0.5, 1, 1, 0.5, 0.2}, At[6] = {0.2, 0.5, 1, 0.5, 0.2, 0};
+    static const double Bs[8] = {0, 0.5, 1, 1, 1, 1, 0.5, 0}, Bt[8] = {0, 0.5, 1, 1, 1, 0.5, 0, 0};
+    static const double Cs[16] = {0, 0.25, 0.5, 1, 1, 1, 1, 0.25, 0.25, 1, 1, 1, 1, 0.5, 0.25, 0};
+    static const double Ct[16] = {0, 0, 0.25, 0.5, 1, 1, 0.25, 0, 0.25, 1, 1, 1, 0.5, 0.25, 0, 0};
+    const double *sp, *tm;
+    int per;
+    if (scheme == 1) { sp = As; tm = At; per = 6; }
+    else if (scheme == 2) { sp = Bs; tm = Bt; per = 8; }
+    else if (scheme == 3) { sp = Cs; tm = Ct; per = 16; }
+    else return -1;
+    if (L0 % per) return -1;
+    for (int t = 0; t < L0; ++t) {
+        out[t] = sp[t % per];
+        out[L0 + t] = tm[t % per];
+    }
+    return 0;
+}
+
+void lqo_update_U_scaled(const lqo_geom* gi, double* Ud, const double* P, double dt, const double* scale)
+{
+    G g = mkg(gi);
+    cplx* U = (cplx*)Ud;
+    init_generators();
+    for (size_t l = 0; l < (size_t)4 * g.V; ++l) {
+        cplx X[9] = {0}, E[9], nu[9];
+        const double dl = dt * link_scale(&g, scale, l);
+        if (dl == 0.0) continue; /* a frozen link */
+        for (int c = 0; c < 8; ++c)
+            for (int i = 0; i < 9; ++i) X[i] += dl * P[l * 8 + c] * (&TG[c][0][0])[i];
+        lqo_su3_expi((const double*)X, (double*)E);
+        mm(E, U + l * 9, nu);
+        reunit(nu);
+        memcpy(U + l * 9, nu, sizeof(nu));
+    }
+}
+
 void lqo_update_U(const lqo_geom* gi, double* Ud, const double* P, double dt)
 {
     G g = mkg(gi);
@@ -1067,10 +1142,10 @@ static void T_P(md_t* m, int j, double dt)
         any = 1;
     }
     if (!any) return;
-    for (size_t i = 0; i < nl; ++i) m->P[i] -= dt * m->F[i];
+    for (size_t i = 0; i < nl; ++i) m->P[i] -= dt * link_scale(m->g, p->step_scale, i / 8) * m->F[i];
 }
 
-static void T_U(md_t* m, double dt) { lqo_update_U(m->gi, m->U, m->P, dt); }
+static void T_U(md_t* m, double dt) { lqo_update_U_scaled(m->gi, m->U, m->P, dt, m->prm->step_scale); }
 
 /* elementary step of level j with step size dt, eqs. (4)-(7) */
 static void step(md_t* m, int j, double dt)

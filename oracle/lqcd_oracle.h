@@ -49,6 +49,7 @@ typedef struct {
     int metropolis;   /* 1: accept/reject; 0: always keep the new field */
     double tol;       /* relative residual of every linear solve */
     int maxit;
+    const double* step_scale; /* NULL, or [2][L0] s(x0) for space-like / time-like links */
 } lqo_hmc_params;
 
 typedef struct {
@@ -98,6 +99,9 @@ void lqo_gauge_force(const lqo_geom* g, const double* U, double beta, double* F)
 double lqo_plaquette(const lqo_geom* g, const double* U);
 void lqo_su3_expi(const double* X, double* E);
 void lqo_update_U(const lqo_geom* g, double* U, const double* P, double dt);
+void lqo_update_U_scaled(const lqo_geom* g, double* U, const double* P, double dt, const double* scale);
+int  lqo_step_scheme(int scheme, int L0, double* out);
+void lqo_force_profile(const lqo_geom* g, const double* F, double* out);
 void lqo_roll_x0(const lqo_geom* g, double* U, int shift);
 void lqo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void lqo_normals(uint64_t seed, uint32_t stream, uint32_t traj, int64_t n, double* out);

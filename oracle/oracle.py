@@ -29,6 +29,7 @@ class HmcParams(C.Structure):
         ("level_gauge", C.c_int), ("level_w1", C.c_int), ("level_schur", C.c_int),
         ("pf_init", C.c_int), ("roll", C.c_int), ("schur_route", C.c_int),
         ("metropolis", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
+        ("step_scale", C.c_void_p),
     ]
 
 
@@ -191,6 +192,11 @@ class Lattice:
             raise RuntimeError("oracle Schur force: a solve did not converge")
         return S.value, F
 
+    def force_profile(self, F):
+        out = np.zeros((2, self.L[0]))
+        lib().lqo_force_profile(C.byref(self.g), _p(np.ascontiguousarray(F)), _p(out))
+        return out
+
     def gauge_action(self, U, beta):
         return lib().lqo_gauge_action(C.byref(self.g), _p(U), C.c_double(beta))
 
@@ -251,12 +257,26 @@ def metropolis_uniforms(seed, traj, L0):
 
 def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w1=0,
                level_schur=0, lam=1.0 / 6.0, pf_init=0, roll=0, schur_route=1, metropolis=1,
-               tol=1e-12, maxit=50000):
+               tol=1e-12, maxit=50000, step_scale=None):
+    """step_scale: None, or a float64 array (2, L0) of s(x0) for space-like /
+    time-like links (see step_scheme)"""
     sc = list(scheme) + [0] * (4 - len(scheme))
     ns = list(nsteps) + [1] * (4 - len(nsteps))
-    return HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * 4)(*sc), (C.c_int * 4)(*ns),
-                     level_gauge, level_w1, level_schur, pf_init, roll, schur_route, metropolis,
-                     tol, maxit)
+    p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * 4)(*sc), (C.c_int * 4)(*ns),
+                  level_gauge, level_w1, level_schur, pf_init, roll, schur_route, metropolis,
+                  tol, maxit, None)
+    if step_scale is not None:
+        p._scale = np.ascontiguousarray(step_scale, dtype=np.float64)
+        p.step_scale = p._scale.ctypes.data
+    return p
+
+
+def step_scheme(scheme, L0):
+    """s(x0) tables of the step-size schemes A (1), B (2), C (3): (2, L0)"""
+    out = np.zeros((2, L0))
+    if lib().lqo_step_scheme(int(scheme), int(L0), _p(out)) != 0:
+        raise ValueError("scheme %d does not tile L0 = %d" % (scheme, L0))
+    return out
 
 
 def md(lat, U, P, phi1, phi2, prm):

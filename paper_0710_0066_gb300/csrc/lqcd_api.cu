@@ -118,19 +118,19 @@ int schur_op(lqcd_ctx* h, double* out, const double* in, double kappa, int op, c
 
 // F += coef * dS/dw for S = |W1^-1 phi|^2; *S_dev (device) receives S
 int pf_w1(lqcd_ctx* h, double* F, const double2* phi, double kappa, double coef, const SolveCfg& c,
-          double* S_dev)
+          double* S_dev, const double* ss = nullptr)
 {
     double2 *eta = fld(h, F_A), *xi = fld(h, F_B);
     LQ_TRY(solve_full(h, MODE_INTRA, -1, 0, c.prec, kappa, eta, phi, c.tol, c.max_iter, nullptr, nullptr));
     if (S_dev) LQ_TRY(norm2_dev(h, (const double*)eta, (int64_t)48 * h->g.Vh, S_dev));
     if (!F) return LQCD_OK;
     LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, xi, eta, c.tol, c.max_iter, nullptr, nullptr));
-    return force_bilinear(h, F, xi, eta, MODE_INTRA, kappa * coef, nullptr, nullptr, 0, 0.0, c.prec);
+    return force_bilinear(h, F, xi, eta, MODE_INTRA, kappa * coef, nullptr, nullptr, 0, 0.0, c.prec, ss);
 }
 
 // F += coef * dS/dw for S = |R^-1 phi|^2 (phi: device boundary coordinates)
 int pf_schur(lqcd_ctx* h, double* F, const double* phi, double kappa, double coef, const SolveCfg& c,
-             double* S_dev)
+             double* S_dev, const double* ss = nullptr)
 {
     double2 *A = fld(h, F_A), *psi = fld(h, F_B), *C = fld(h, F_C), *et = fld(h, F_D), *E = fld(h, F_E),
             *chi = fld(h, F_G);
@@ -145,7 +145,7 @@ int pf_schur(lqcd_ctx* h, double* F, const double* phi, double kappa, double coe
     LQ_TRY(embed_boundary(h, et, eta));
     LQ_TRY(hop_full(h, MODE_INTRA, 1, 1, E, et, 1.0, et, -kappa));
     LQ_TRY(solve_full(h, MODE_ALL, -1, 1, c.prec, kappa, chi, E, c.tol, c.max_iter, nullptr, nullptr));
-    return force_bilinear(h, F, et, psi, MODE_INTRA, -kappa * coef, chi, psi, MODE_ALL, kappa * coef, c.prec);
+    return force_bilinear(h, F, et, psi, MODE_INTRA, -kappa * coef, chi, psi, MODE_ALL, kappa * coef, c.prec, ss);
 }
 
 // ---------------------------------------------------------------------------
@@ -221,6 +221,46 @@ int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
             h->err = "hmc params: term level out of range";
             return LQCD_ERR_ARG;
         }
+    if (!p->step_scale && p->step_scheme) {
+        const int per[4] = {0, 6, 8, 16};
+        if (p->step_scheme < 0 || p->step_scheme > 3 || h->g.L[0] % per[p->step_scheme]) {
+            h->err = "hmc params: step_scheme unknown or its period does not divide L0";
+            return LQCD_ERR_ARG;
+        }
+    }
+    return LQCD_OK;
+}
+
+// step-size schemes of Sec. 2 (space-like, time-like values over one period)
+void scheme_table(int scheme, int L0, double* out)
+{
+    static const double a_sp[6] = {0.2, 0.5, 1.0, 1.0, 0.5, 0.2};  // s(5): printed "2", read 0.2
+    static const double a_tm[6] = {0.2, 0.5, 1.0, 0.5, 0.2, 0.0};
+    static const double b_sp[8] = {0.0, 0.5, 1.0, 1.0, 1.0, 1.0, 0.5, 0.0};
+    static const double b_tm[8] = {0.0, 0.5, 1.0, 1.0, 1.0, 0.5, 0.0, 0.0};
+    static const double c_sp[16] = {0.0, 0.25, 0.5, 1.0, 1.0, 1.0, 1.0, 0.25, 0.25, 1.0, 1.0, 1.0, 1.0, 0.5, 0.25, 0.0};
+    static const double c_tm[16] = {0.0, 0.0, 0.25, 0.5, 1.0, 1.0, 0.25, 0.0, 0.25, 1.0, 1.0, 1.0, 0.5, 0.25, 0.0, 0.0};
+    const double* sp = scheme == 1 ? a_sp : scheme == 2 ? b_sp : c_sp;
+    const double* tm = scheme == 1 ? a_tm : scheme == 2 ? b_tm : c_tm;
+    const int per = scheme == 1 ? 6 : scheme == 2 ? 8 : 16;
+    for (int t = 0; t < L0; ++t) {
+        out[t] = sp[t % per];
+        out[L0 + t] = tm[t % per];
+    }
+}
+
+// device step-size table of this MD, or null for s = 1
+int md_scale_table(lqcd_ctx* h, const lqcd_hmc_params& p, const double** out)
+{
+    *out = nullptr;
+    if (!p.step_scale && !p.step_scheme) return LQCD_OK;
+    const int L0 = h->g.L[0];
+    std::vector<double> tab(2 * L0);
+    if (p.step_scale) std::copy(p.step_scale, p.step_scale + 2 * L0, tab.begin());
+    else scheme_table(p.step_scheme, L0, tab.data());
+    LQ_CUDA(h, cudaMemcpyAsync(h->d_sscale, tab.data(), sizeof(double) * 2 * L0, cudaMemcpyHostToDevice, h->stream));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    *out = h->d_sscale;
     return LQCD_OK;
 }
 
@@ -231,18 +271,20 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const double2* phi1,
     const double dt = p.tau / p.nsteps[top];
     for (int i = 0; i < p.nsteps[top]; ++i) build_step(p, top, dt, ops);
     SolveCfg c{p.precision, p.tol, p.max_iter};
+    const double* ss = nullptr;
+    LQ_TRY(md_scale_table(h, p, &ss));
     for (const Op& o : ops) {
         if (o.kind == 1) {
-            LQ_TRY(update_links(h, P, o.dt));
+            LQ_TRY(update_links(h, P, o.dt, ss));
             continue;
         }
-        if (p.level_gauge == o.level) LQ_TRY(gauge_force_kick(h, P, -o.dt * p.beta / 6.0, p.precision));
+        if (p.level_gauge == o.level) LQ_TRY(gauge_force_kick(h, P, -o.dt * p.beta / 6.0, p.precision, ss));
         if (p.level_w1 == o.level) {
-            LQ_TRY(pf_w1(h, P, phi1, p.kappa, -o.dt, c, nullptr));
+            LQ_TRY(pf_w1(h, P, phi1, p.kappa, -o.dt, c, nullptr, ss));
             ++*nforce;
         }
         if (p.level_schur == o.level) {
-            LQ_TRY(pf_schur(h, P, phi2, p.kappa, -o.dt, c, nullptr));
+            LQ_TRY(pf_schur(h, P, phi2, p.kappa, -o.dt, c, nullptr, ss));
             ++*nforce;
         }
     }
@@ -421,6 +463,7 @@ int lqcd_create(lqcd_t* out, const int L[4], int l0, int bc_t, void* stream)
     for (int k = 0; k < NFIELD; ++k) LQ_CUDA(h, cudaMalloc(&h->f64[k], sizeof(double2) * 24 * Vh));
     LQ_CUDA(h, cudaMalloc(&h->P, sizeof(double) * 32 * (size_t)g.V));
     LQ_CUDA(h, cudaMalloc(&h->F, sizeof(double) * 32 * (size_t)g.V));
+    LQ_CUDA(h, cudaMalloc(&h->d_sscale, sizeof(double) * 2 * (size_t)g.L[0]));
     const size_t nb2 = 2 * (size_t)nbnd_of(g);
     for (int k = 0; k < 4; ++k) LQ_CUDA(h, cudaMalloc(&h->bnd[k], sizeof(double) * std::max<size_t>(nb2, 2)));
     h->red_blocks = reduction_blocks();
@@ -444,6 +487,7 @@ int lqcd_destroy(lqcd_t h)
     for (double2* f : h->f64) cudaFree(f);
     cudaFree(h->P);
     cudaFree(h->F);
+    cudaFree(h->d_sscale);
     for (int k = 0; k < 4; ++k) cudaFree(h->bnd[k]);
     cudaFree(h->red_part);
     cudaFree(h->red_out);
@@ -806,6 +850,13 @@ int lqcd_profile_reset(lqcd_t h)
         h->prof.bytes[k] = 0.0;
     }
     return LQCD_OK;
+}
+
+int lqcd_force_profile(lqcd_t h, const double* F, double* out)
+{
+    CHECK_H(h);
+    NEED(F && out, "null force / output pointer");
+    return force_profile(h, F, out);
 }
 
 int lqcd_launch_count(lqcd_t h, int64_t* count)

@@ -508,6 +508,7 @@ struct lqcd_ctx {
     int red_blocks = 0;
     Work* work = nullptr;
     Profiler prof;
+    double* d_sscale = nullptr;  // step-size table [2][L0] of the current MD
     int64_t launches = 0;    // kernels launched by this handle
     int64_t iter_count = 0;  // inner iterations since reset (trajectory stats)
     int64_t site_iters = 0;  // inner iterations x even sites of the system
@@ -582,12 +583,16 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
 
 // force.cu
 // prec: PREC64 runs the link arithmetic in double, otherwise in single
-// precision on the single-precision links (results accumulated in double)
+// precision on the single-precision links (results accumulated in double).
+// ss: device step-size table [2][L0] (row 0 space-like, row 1 time-like
+// links) multiplying each link's contribution, or null for s = 1.
 int force_bilinear(lqcd_ctx* h, double* F, const double2* a1, const double2* b1, int mask1,
-                   double coef1, const double2* a2, const double2* b2, int mask2, double coef2, int prec);
-int gauge_force_kick(lqcd_ctx* h, double* F, double coef, int prec);
+                   double coef1, const double2* a2, const double2* b2, int mask2, double coef2, int prec,
+                   const double* ss = nullptr);
+int gauge_force_kick(lqcd_ctx* h, double* F, double coef, int prec, const double* ss = nullptr);
 int plaquette_sum(lqcd_ctx* h, double* dev_out);
-int update_links(lqcd_ctx* h, const double* P, double dt);
+int force_profile(lqcd_ctx* h, const double* F, double* out);
+int update_links(lqcd_ctx* h, const double* P, double dt, const double* ss = nullptr);
 int roll_links(lqcd_ctx* h, int shift);
 int kinetic_sum(lqcd_ctx* h, const double* P, double* dev_out);
 int refresh_low_precision(lqcd_ctx* h);

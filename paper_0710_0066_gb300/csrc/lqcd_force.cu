@@ -139,9 +139,15 @@ __device__ __forceinline__ void bilinear_link(const Geo& g, const GaugeF& U, con
     for (int k = 0; k < 8; ++k) f[k] += s * l[k];
 }
 
+// step-size factor of link (x, mu) (Sec. 2); 1 without a table
+__device__ __forceinline__ double link_scale(const Geo& g, const double* ss, int mu, int x0)
+{
+    return ss ? ss[(mu == 0 ? g.L[0] : 0) + x0] : 1.0;
+}
+
 // F[mu][site][a] += sum over the (up to two) terms; one thread per link
 template <int PL>
-__global__ void __launch_bounds__(BS) k_bilinear(Geo g, GaugeF U, double* F, BilTerm T1, BilTerm T2)
+__global__ void __launch_bounds__(BS) k_bilinear(Geo g, GaugeF U, double* F, BilTerm T1, BilTerm T2, const double* ss)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * g.V) return;
@@ -149,6 +155,8 @@ __global__ void __launch_bounds__(BS) k_bilinear(Geo g, GaugeF U, double* F, Bil
     const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
     int x[4];
     eo_coords(g, par, i, x);
+    const double sc = link_scale(g, ss, mu, x[0]);
+    if (sc == 0.0) return;
     double f[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) f[k] = 0.0;
@@ -156,8 +164,8 @@ __global__ void __launch_bounds__(BS) k_bilinear(Geo g, GaugeF U, double* F, Bil
     if (T2.on) bilinear_link<PL>(g, U, T2, mu, par, i, x, f);
     double4* d4 = (double4*)(F + ((size_t)mu * g.V + s) * 8);
     double4 a = d4[0], b = d4[1];
-    a.x += f[0]; a.y += f[1]; a.z += f[2]; a.w += f[3];
-    b.x += f[4]; b.y += f[5]; b.z += f[6]; b.w += f[7];
+    a.x += sc * f[0]; a.y += sc * f[1]; a.z += sc * f[2]; a.w += sc * f[3];
+    b.x += sc * f[4]; b.y += sc * f[5]; b.z += sc * f[6]; b.w += sc * f[7];
     d4[0] = a;
     d4[1] = b;
 }
@@ -216,7 +224,7 @@ __device__ void staple(const Geo& g, const GaugeF& U, const int x[4], int mu, Su
 
 // F += coef * dS_G/dw^a,  dS_G/dw^a = -beta/3 Re tr(i T^a U A) = beta/6 * 2 Im tr(T^a U A)
 template <int P>
-__global__ void __launch_bounds__(BS) k_gauge_force(Geo g, GaugeF U, double* F, double c)
+__global__ void __launch_bounds__(BS) k_gauge_force(Geo g, GaugeF U, double* F, double c, const double* ss)
 {
     typedef typename Real<P>::T R;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,6 +233,8 @@ __global__ void __launch_bounds__(BS) k_gauge_force(Geo g, GaugeF U, double* F, 
     const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
     int x[4];
     eo_coords(g, par, i, x);
+    c *= link_scale(g, ss, mu, x[0]);
+    if (c == 0.0) return;
     Su3<R> A, u, Y;
     staple<P>(g, U, x, mu, A);
     load_link<P>(U, mu, par, i, u);
@@ -290,6 +300,38 @@ __global__ void k_sum_final(const double* part, int n, double* out, double scale
     for (int k = threadIdx.x; k < n; k += blockDim.x) acc += part[k];
     acc = block_sum(acc);
     if (threadIdx.x == 0) *out = scale * acc;
+}
+
+// average force per time slice (the diagnostic of Sec. 3, Fig. 1): block
+// x0 sums |F| = (sum_a F_a^2)^(1/2) over the slice's space-like links (out[x0])
+// and its time-like links (out[L0 + x0]) in a fixed order
+__global__ void k_force_profile(Geo g, const double* F, double* out)
+{
+    const int x0 = blockIdx.x;
+    double sp = 0.0, tm = 0.0;
+    for (int l3 = threadIdx.x; l3 < g.V3; l3 += blockDim.x) {
+        const int lex = x0 * g.V3 + l3;
+        int x[4];
+        x[3] = l3 % g.L[3];
+        x[2] = (l3 / g.L[3]) % g.L[2];
+        x[1] = l3 / (g.L[3] * g.L[2]);
+        x[0] = x0;
+        const int s = ((x[0] + x[1] + x[2] + x[3]) & 1) * g.Vh + (lex >> 1);
+        for (int mu = 0; mu < 4; ++mu) {
+            const double* f = F + ((size_t)mu * g.V + s) * 8;
+            double n = 0.0;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) n += f[a] * f[a];
+            if (mu == 0) tm += sqrt(n);
+            else sp += sqrt(n);
+        }
+    }
+    sp = block_sum(sp);
+    tm = block_sum(tm);
+    if (threadIdx.x == 0) {
+        out[x0] = sp / (3.0 * g.V3);
+        out[g.L[0] + x0] = tm / g.V3;
+    }
 }
 
 // exp(iQ) for traceless hermitian Q by the Cayley-Hamilton form
@@ -400,12 +442,15 @@ __device__ void store_link_all(double2* U64, float4* U32, uint2* U16, int Vh, in
 }
 
 // U_mu(x) <- exp(i dt P_mu(x)) U_mu(x), P = sum_a p^a T^a; all three copies
-__global__ void __launch_bounds__(BS) k_update(Geo g, double2* U64, float4* U32, uint2* U16, const double* P, double dt)
+__global__ void __launch_bounds__(BS) k_update(Geo g, double2* U64, float4* U32, uint2* U16, const double* P, double dt,
+                                              const double* ss)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4 * g.V) return;
     const int mu = t / g.V, s = t - mu * g.V;
     const int par = s >= g.Vh ? 1 : 0, i = s - par * g.Vh;
+    dt *= link_scale(g, ss, mu, (2 * i) / g.V3);
+    if (dt == 0.0) return;  // a frozen link
     const double* p = P + ((size_t)mu * g.V + s) * 8;
     double q[8];
 #pragma unroll
@@ -480,16 +525,16 @@ static BilTerm make_term(lqcd_ctx* h, const double2* a, const double2* b, int ma
 }
 
 int force_bilinear(lqcd_ctx* h, double* F, const double2* a1, const double2* b1, int mask1, double coef1,
-                   const double2* a2, const double2* b2, int mask2, double coef2, int prec)
+                   const double2* a2, const double2* b2, int mask2, double coef2, int prec, const double* ss)
 {
     BilTerm T1 = make_term(h, a1, b1, mask1, coef1), T2 = make_term(h, a2, b2, mask2, coef2);
     cudaEvent_t ev;
     prof_begin(h, 2, &ev);
     const int nb = (4 * h->g.V + BS - 1) / BS;
     if (prec == PREC64)
-        k_bilinear<PREC64><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, T1, T2);
+        k_bilinear<PREC64><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, T1, T2, ss);
     else
-        k_bilinear<PREC32><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC32), F, T1, T2);
+        k_bilinear<PREC32><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC32), F, T1, T2, ss);
     LQ_TRY(launch_err(h, "force kernel"));
     const int nt = T1.on + T2.on;
     // per site: two spinors of each term, four links, F read and written
@@ -497,16 +542,16 @@ int force_bilinear(lqcd_ctx* h, double* F, const double2* a1, const double2* b1,
     return LQCD_OK;
 }
 
-int gauge_force_kick(lqcd_ctx* h, double* F, double coef, int prec)
+int gauge_force_kick(lqcd_ctx* h, double* F, double coef, int prec, const double* ss)
 {
     // coef * (beta/6) is folded in by the caller
     cudaEvent_t ev;
     prof_begin(h, 3, &ev);
     const int nb = (4 * h->g.V + BS - 1) / BS;
     if (prec == PREC64)
-        k_gauge_force<PREC64><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, coef);
+        k_gauge_force<PREC64><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC64), F, coef, ss);
     else
-        k_gauge_force<PREC32><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC32), F, coef);
+        k_gauge_force<PREC32><<<nb, BS, 0, h->stream>>>(h->g, gauge_view(h, PREC32), F, coef, ss);
     LQ_TRY(launch_err(h, "gauge force kernel"));
     prof_end(h, 3, ev, (double)h->g.V * (4.0 * 144.0 + 2.0 * 256.0));
     return LQCD_OK;
@@ -521,11 +566,11 @@ int plaquette_sum(lqcd_ctx* h, double* dev_out)
     return launch_err(h, "plaquette kernel");
 }
 
-int update_links(lqcd_ctx* h, const double* P, double dt)
+int update_links(lqcd_ctx* h, const double* P, double dt, const double* ss)
 {
     cudaEvent_t ev;
     prof_begin(h, 3, &ev);
-    k_update<<<(4 * h->g.V + BS - 1) / BS, BS, 0, h->stream>>>(h->g, h->U64, h->U32, h->U16, P, dt);
+    k_update<<<(4 * h->g.V + BS - 1) / BS, BS, 0, h->stream>>>(h->g, h->U64, h->U32, h->U16, P, dt, ss);
     LQ_TRY(launch_err(h, "link update kernel"));
     prof_end(h, 3, ev, (double)h->g.V * 4.0 * (2.0 * 144.0 + 64.0 + 48.0 + 24.0));
     return LQCD_OK;
@@ -536,6 +581,12 @@ int roll_links(lqcd_ctx* h, int shift)
     // src: the saved copy (caller copies the current field there first)
     k_roll<<<(4 * h->g.V + BS - 1) / BS, BS, 0, h->stream>>>(h->g, h->U64, h->U32, h->U16, h->U64_save, shift);
     return launch_err(h, "roll kernel");
+}
+
+int force_profile(lqcd_ctx* h, const double* F, double* out)
+{
+    k_force_profile<<<h->g.L[0], 256, 0, h->stream>>>(h->g, F, out);
+    return launch_err(h, "force profile kernel");
 }
 
 int kinetic_sum(lqcd_ctx* h, const double* P, double* dev_out)

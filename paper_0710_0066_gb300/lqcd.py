@@ -32,7 +32,7 @@ EXPORTS = [
     "lqcd_block_solve_batched", "lqcd_solve_wilson", "lqcd_schur_apply", "lqcd_pf_force",
     "lqcd_gauge_force", "lqcd_rng_normals", "lqcd_hmc_trajectory", "lqcd_md",
     "lqcd_profile_enable", "lqcd_profile_reset", "lqcd_profile_read", "lqcd_launch_count",
-    "lqcd_gauge_action_static",
+    "lqcd_gauge_action_static", "lqcd_force_profile",
 ]
 
 
@@ -42,7 +42,7 @@ class HmcParams(C.Structure):
         ("nlevels", C.c_int), ("scheme", C.c_int * 4), ("nsteps", C.c_int * 4),
         ("level_gauge", C.c_int), ("level_w1", C.c_int), ("level_schur", C.c_int),
         ("pf_init", C.c_int), ("roll", C.c_int), ("metropolis", C.c_int), ("precision", C.c_int),
-        ("tol", C.c_double), ("max_iter", C.c_int),
+        ("tol", C.c_double), ("max_iter", C.c_int), ("step_scheme", C.c_int), ("step_scale", C.c_void_p),
     ]
 
 
@@ -57,12 +57,20 @@ class HmcResult(C.Structure):
 
 def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w1=0, level_schur=0,
                lam=1.0 / 6.0, pf_init=0, roll=0, metropolis=1, precision=PREC_F64, tol=1e-10,
-               max_iter=20000):
+               max_iter=20000, step_scheme=0, step_scale=None):
+    """step_scale: None or a host float64 array (2, L0) of s(x0) (space-like,
+    time-like rows); it is kept alive on the returned object"""
     sc = list(scheme) + [0] * (4 - len(scheme))
     ns = list(nsteps) + [1] * (4 - len(nsteps))
-    return HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * 4)(*sc), (C.c_int * 4)(*ns),
-                     level_gauge, level_w1, level_schur, pf_init, roll, metropolis, precision, tol,
-                     max_iter)
+    p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * 4)(*sc), (C.c_int * 4)(*ns),
+                  level_gauge, level_w1, level_schur, pf_init, roll, metropolis, precision, tol,
+                  max_iter, step_scheme, None)
+    if step_scale is not None:
+        import numpy as np
+
+        p._scale = np.ascontiguousarray(step_scale, dtype=np.float64)
+        p.step_scale = p._scale.ctypes.data
+    return p
 
 
 _lib = None
@@ -100,6 +108,7 @@ def load():
         "lqcd_profile_read": [vp, i, vp, vp, vp],
         "lqcd_launch_count": [vp, vp],
         "lqcd_gauge_action_static": [C.POINTER(C.c_int * 4), vp, d, vp, vp],
+        "lqcd_force_profile": [vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -253,6 +262,10 @@ def lqcd_gauge_action_static(L, U, beta, out, stream=None):
     return load().lqcd_gauge_action_static(C.byref((C.c_int * 4)(*L)), _ptr(U), float(beta), _ptr(out), s)
 
 
+def lqcd_force_profile(h, F, out):
+    return _check(h, load().lqcd_force_profile(h, _ptr(F), _ptr(out)))
+
+
 def lqcd_launch_count(h):
     n = C.c_int64(0)
     _check(h, load().lqcd_launch_count(h, C.byref(n)))
@@ -349,6 +362,12 @@ class Lattice:
         F = self.momenta() if force else None
         S = lqcd_pf_force(self.h, F, phi.contiguous(), kappa, term, precision, tol, max_iter)
         return S, F
+
+    def force_profile(self, F):
+        """mean |F| per time slice: (2, L0) for space-like / time-like links"""
+        out = torch.empty((2, self.L[0]), dtype=torch.float64, device=self.dev)
+        lqcd_force_profile(self.h, F.contiguous(), out)
+        return out
 
     def gauge_force(self, beta, force=True):
         F = self.momenta() if force else None

@@ -207,3 +207,46 @@ def test_hmc_trajectory_matches_oracle(pf_init):
     assert res.accepted == ores.accepted and res.shift == ores.shift
     assert rel(U1, Uo) < 1e-9
     lat.close()
+
+
+@pytest.mark.parametrize("scheme,L,l0,kappa", [(2, (8, 4, 4, 4), 2, 0.15), (1, (12, 4, 4, 4), 2, 0.12)])
+def test_md_step_scheme_matches_oracle(scheme, L, l0, kappa):
+    """position-dependent step sizes (Sec. 2): per-link dt * s(x0); links
+    with s = 0 stay frozen (kappa = 0.12 at 12x4^3: at 0.15 this random field
+    makes M itself nearly singular)"""
+    beta = 5.6
+    U = syn.random_links(L, 0.3, 21)
+    olat = O.Lattice(L, l0, -1)
+    P = syn.gaussian_momenta(olat.V, 22)
+    eta1 = syn.gaussian_spinor(olat.V, 23)
+    eta2 = syn.gaussian_complex(olat.bnd_shape(), 24)
+    phi1 = olat.W1(U, kappa, eta1)
+    phi2 = olat.schur(U, kappa, eta2, O.R, tol=1e-14)
+    s = O.step_scheme(scheme, L[0])
+    lat = lqcd.Lattice(L, l0, -1)
+    prm = lqcd.hmc_params(beta, kappa, 0.4, 2, (lqcd.SW, lqcd.LF), [2, 2], 0, 1, 1, tol=1e-12, step_scheme=scheme)
+    oprm = O.hmc_params(beta, kappa, 0.4, 2, (O.SW, O.LF), [2, 2], 0, 1, 1, tol=1e-13, step_scale=s)
+    U1, P1 = lat.md(cuda(U), cuda(P), cuda(phi1), cuda(phi2), prm)
+    Uo, Po, st = O.md(olat, U, P, phi1, phi2, oprm)
+    assert st == 0
+    assert rel(U1, Uo) < 1e-9 and rel(P1, Po) < 1e-8
+    # the same through an explicit table
+    prm2 = lqcd.hmc_params(beta, kappa, 0.4, 2, (lqcd.SW, lqcd.LF), [2, 2], 0, 1, 1, tol=1e-12, step_scale=s)
+    U2, P2 = lat.md(cuda(U), cuda(P), cuda(phi1), cuda(phi2), prm2)
+    assert torch.equal(U1, U2) and torch.equal(P1, P2)
+    m = olat.index_maps()
+    x0 = m[0] // (L[1] * L[2] * L[3])
+    U1n = U1.cpu().numpy()
+    for mu in range(4):
+        frozen = s[1 if mu == 0 else 0][x0] == 0
+        assert np.array_equal(U1n[mu, frozen], U[mu, frozen])
+    lat.close()
+
+
+def test_force_profile_matches_oracle(setup):
+    lat, olat, U, kappa, seed = setup
+    phi = syn.gaussian_complex(olat.bnd_shape(), seed + 9)
+    S, F = lat.pf_force(cuda(phi), kappa, lqcd.TERM_SCHUR, lqcd.PREC_F64, tol=1e-12)
+    prof = lat.force_profile(F).cpu().numpy()
+    ref = olat.force_profile(F.cpu().numpy())
+    assert rel(prof, ref) < 1e-13

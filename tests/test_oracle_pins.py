@@ -502,3 +502,55 @@ def test_exp_minus_dH_average():
     w = np.array(w)
     err = w.std(ddof=1) / math.sqrt(len(w))
     assert abs(w.mean() - 1) < 2.5 * err + 1e-3, (w.mean(), err)
+
+
+# ---------------------------------------------------------------------------
+# position-dependent step sizes (Sec. 2, schemes A, B, C)
+# ---------------------------------------------------------------------------
+def test_step_scheme_averages_match_the_paper():
+    """the paper states the average of s over all links: 0.525 for scheme A
+    (L0 = 24) and about 0.59 for B and C (L0 = 32)"""
+    for scheme, L0, want, tol in [(1, 24, 0.525, 1e-12), (2, 32, 0.59, 0.01), (3, 32, 0.59, 0.015)]:
+        s = O.step_scheme(scheme, L0)
+        avg = (3 * s[0].mean() + s[1].mean()) / 4  # three space-like, one time-like link per site
+        assert abs(avg - want) < tol, (scheme, avg)
+    # the periods are 6, 8 and 16 time slices
+    assert np.array_equal(O.step_scheme(1, 24)[:, :6], O.step_scheme(1, 24)[:, 6:12])
+    with pytest.raises(ValueError):
+        O.step_scheme(2, 12)
+
+
+def test_step_scale_freezes_links_and_stays_reversible():
+    L = (8, 2, 2, 2)
+    lat, U, P, eta1, eta2 = _setup(L, 2, 0.3, 101)
+    phi1 = lat.W1(U, 0.15, eta1)  # heatbath fields
+    phi2 = lat.schur(U, 0.15, eta2, O.R, tol=1e-14)
+    s = O.step_scheme(2, 8)
+    prm = O.hmc_params(5.6, 0.15, 0.3, 2, (O.SW, O.LF), [2, 2], 0, 1, 1, tol=1e-13, step_scale=s)
+    U1, P1, st = O.md(lat, U, P, phi1, phi2, prm)
+    assert st == 0
+    m = lat.index_maps()
+    x0 = m[0] // (L[1] * L[2] * L[3])
+    for mu in range(4):
+        frozen = (s[1 if mu == 0 else 0][x0] == 0)
+        assert np.array_equal(U1[mu, frozen], U[mu, frozen])
+        assert np.array_equal(P1[mu, frozen], P[mu, frozen])
+        assert np.max(np.abs(U1[mu, ~frozen] - U[mu, ~frozen])) > 1e-3
+    U2, P2, st = O.md(lat, U1, -P1, phi1, phi2, prm)
+    assert np.max(np.abs(U2 - U)) < 1e-11
+
+
+def test_force_profile_closed_form():
+    """Fig. 1 diagnostic: mean |F| per time slice; a force whose 8 coefficients
+    equal c(mu, x0) on every link gives sqrt(8) c exactly"""
+    L = (6, 2, 4, 2)
+    lat = O.Lattice(L, 1, -1)
+    m = lat.index_maps()
+    x0 = m[0] // (L[1] * L[2] * L[3])
+    F = np.zeros((4, lat.V, 8))
+    for mu in range(4):
+        F[mu] = (1.0 + 0.5 * mu + 0.25 * x0)[:, None]
+    prof = lat.force_profile(F)
+    t = np.arange(L[0])
+    assert np.allclose(prof[0], np.sqrt(8) * (1.0 + 0.25 * t + 0.5 * 2), rtol=1e-14)  # mean of mu = 1, 2, 3
+    assert np.allclose(prof[1], np.sqrt(8) * (1.0 + 0.25 * t), rtol=1e-14)
