@@ -43,6 +43,7 @@ typedef struct {
     int L[4];
     int l0, bc_t, nb;
     int V, Vh, V3;
+    int l0s, nbs; /* iterated decomposition: sub-slabs of thickness l0s = l0/2 */
 } G;
 
 int lqo_geom_check(const lqo_geom* g)
@@ -51,6 +52,7 @@ int lqo_geom_check(const lqo_geom* g)
         if (g->L[mu] < 2 || (g->L[mu] & 1)) return -2;
     if (g->l0 < 1 || g->L[0] % (2 * g->l0)) return -2;
     if (g->bc_t != 1 && g->bc_t != -1) return -1;
+    if (g->l0s && (g->l0s < 1 || g->l0 != 2 * g->l0s)) return -2;
     return 0;
 }
 
@@ -64,6 +66,8 @@ static G mkg(const lqo_geom* in)
     g.V = g.L[0] * g.V3;
     g.Vh = g.V / 2;
     g.nb = g.L[0] / g.l0;
+    g.l0s = in->l0s;
+    g.nbs = g.l0s ? g.L[0] / g.l0s : 0;
     return g;
 }
 
@@ -113,30 +117,40 @@ static int slab_of(const G* g, int s)
 
 /* neighbour / phase / slab tables of the last geometry used, filled from
  * shift_of and slab_of above (only a cache of their values) */
+static int sub_of(const G* g, int s)
+{
+    int x[4];
+    coords_of(g, s, x);
+    return g->l0s ? x[0] / g->l0s : 0;
+}
+
 static struct {
-    int L[4], l0, bc_t, V;
+    int L[4], l0, bc_t, V, l0s;
     int* nbr;     /* [s][mu][dir 0:+,1:-] */
     double* ph;
     int* slab;
-} TAB = {{0, 0, 0, 0}, 0, 0, 0, NULL, NULL, NULL};
+    int* sub;
+} TAB = {{0, 0, 0, 0}, 0, 0, 0, 0, NULL, NULL, NULL, NULL};
 
 static void tables(const G* g)
 {
-    if (TAB.nbr && TAB.V == g->V && TAB.l0 == g->l0 && TAB.bc_t == g->bc_t &&
+    if (TAB.nbr && TAB.V == g->V && TAB.l0 == g->l0 && TAB.bc_t == g->bc_t && TAB.l0s == g->l0s &&
         !memcmp(TAB.L, g->L, sizeof(TAB.L)))
         return;
-    free(TAB.nbr); free(TAB.ph); free(TAB.slab);
+    free(TAB.nbr); free(TAB.ph); free(TAB.slab); free(TAB.sub);
     TAB.nbr = malloc(sizeof(int) * (size_t)g->V * 8);
     TAB.ph = malloc(sizeof(double) * (size_t)g->V * 8);
     TAB.slab = malloc(sizeof(int) * (size_t)g->V);
+    TAB.sub = malloc(sizeof(int) * (size_t)g->V);
     for (int s = 0; s < g->V; ++s) {
         TAB.slab[s] = slab_of(g, s);
+        TAB.sub[s] = sub_of(g, s);
         for (int mu = 0; mu < 4; ++mu)
             for (int d = 0; d < 2; ++d)
                 TAB.nbr[(s * 4 + mu) * 2 + d] = shift_of(g, s, mu, d ? -1 : +1, &TAB.ph[(s * 4 + mu) * 2 + d]);
     }
     memcpy(TAB.L, g->L, sizeof(TAB.L));
-    TAB.V = g->V; TAB.l0 = g->l0; TAB.bc_t = g->bc_t;
+    TAB.V = g->V; TAB.l0 = g->l0; TAB.bc_t = g->bc_t; TAB.l0s = g->l0s;
 }
 
 /* index maps, each of length V in checkerboard site order:
@@ -286,12 +300,19 @@ static void dag(const cplx* a, cplx* b) /* b = a^dagger */
 /*  mode ALL: every hop; INTRA: hops inside one slab (W1);             */
 /*  CROSS: hops between different slabs (the blocks B, C of M).        */
 /* ------------------------------------------------------------------ */
+/* which hops a mode keeps: ALL; INTRA / CROSS: inside one slab / between
+ * slabs; INTRA2: inside one sub-slab (W2); CROSS2: between the two
+ * sub-slabs of one slab (the blocks B2, C2 of W1) */
 static int hop_in(const G* g, int s, int t, int mode)
 {
     (void)g;
     if (mode == LQO_HOP_ALL) return 1;
     int same = TAB.slab[s] == TAB.slab[t];
-    return mode == LQO_HOP_INTRA ? same : !same;
+    if (mode == LQO_HOP_INTRA) return same;
+    if (mode == LQO_HOP_CROSS) return !same;
+    int same2 = TAB.sub[s] == TAB.sub[t];
+    if (mode == LQO_HOP_INTRA2) return same2;
+    return same && !same2;
 }
 
 static void hop_c(const G* g, const cplx* U, const cplx* in, cplx* out, int mode, int dagger)
@@ -824,6 +845,268 @@ int lqo_pf_schur(const lqo_geom* gi, const double* Ud, double kappa, const doubl
 }
 
 /* ------------------------------------------------------------------ */
+/* iterated decomposition (Sec. 1: l0^(2) = l0^(1)/2, W2 = M restricted */
+/* to the sub-slabs).  With the sites of W1 ordered red|black by the     */
+/* sub-slab colour, W1 = [[A2, B2], [C2, D2]], W2 = diag(A2, D2), and     */
+/* B2, C2 = -kappa H on the hops between the two sub-slabs of one slab.  */
+/* Block LU: det W1 = det W2 det R2 with                                  */
+/*   R2 = E2 (1 - C2 A2^-1 B2 D2^-1) E2^dag                               */
+/* on the range of C2: the first time slice of each black sub-slab,      */
+/* spin projected with (1+g0)/2 (its last slice borders the next slab,   */
+/* which W1 does not reach).  det M = det R1 det R2 det W2.               */
+/* Boundary field layout: [nbs/2][V3][2][3] complex, same spin basis as  */
+/* face 0 of the first level.                                             */
+/* ------------------------------------------------------------------ */
+static void keep_colour2(const G* g, cplx* f, int colour)
+{
+    if (colour < 0) return;
+    for (int s = 0; s < g->V; ++s)
+        if (sub_of(g, s) % 2 != colour) memset(f + (size_t)s * 12, 0, sizeof(cplx) * 12);
+}
+
+/* x = W2^-1 b on the sub-slabs of one colour (-1: all) */
+static int block_solve2_c(const G* g, const cplx* U, double kappa, cplx* x, const cplx* b, int colour,
+                          int dagger, double tol, int maxit, int* iters)
+{
+    size_t n = (size_t)g->V * 12;
+    cplx* bb = malloc(sizeof(cplx) * n);
+    memcpy(bb, b, sizeof(cplx) * n);
+    keep_colour2(g, bb, colour);
+    opctx o = {g, U, kappa, LQO_HOP_INTRA2, dagger};
+    int st = cgnr(op_1mkH, &o, n, x, bb, tol, maxit, iters);
+    free(bb);
+    return st;
+}
+
+int lqo_block_solve2(const lqo_geom* gi, const double* U, double kappa, double* x, const double* b,
+                     int colour, int dagger, double tol, int maxit, int* iters)
+{
+    G g = mkg(gi);
+    if (!g.l0s) return -2;
+    return block_solve2_c(&g, (const cplx*)U, kappa, (cplx*)x, (const cplx*)b, colour, dagger, tol, maxit,
+                          iters);
+}
+
+void lqo_apply_W2(const lqo_geom* gi, const double* U, double kappa, const double* in, double* out,
+                  int dagger)
+{
+    G g = mkg(gi);
+    apply_1mkH(&g, (const cplx*)U, kappa, (const cplx*)in, (cplx*)out, LQO_HOP_INTRA2, dagger);
+}
+
+int lqo_nbnd2(const lqo_geom* gi)
+{
+    G g = mkg(gi);
+    return (g.nbs / 2) * g.V3 * 6;
+}
+
+static int face2_site(const G* g, int j, int lex3)
+{
+    int x[4];
+    x[0] = (2 * j + 1) * g->l0s;
+    x[3] = lex3 % g->L[3];
+    x[2] = (lex3 / g->L[3]) % g->L[2];
+    x[1] = lex3 / (g->L[3] * g->L[2]);
+    return site_of(g, x);
+}
+
+static void embed2_c(const G* g, const cplx* c, cplx* full)
+{
+    init_basis();
+    memset(full, 0, sizeof(cplx) * (size_t)g->V * 12);
+    for (int j = 0; j < g->nbs / 2; ++j)
+        for (int l3 = 0; l3 < g->V3; ++l3) {
+            int s = face2_site(g, j, l3);
+            const cplx* cc = c + ((size_t)j * g->V3 + l3) * 6;
+            for (int sp = 0; sp < 4; ++sp)
+                for (int col = 0; col < 3; ++col)
+                    for (int i = 0; i < 2; ++i)
+                        full[(size_t)s * 12 + sp * 3 + col] += BASIS[0][i][sp] * cc[i * 3 + col];
+        }
+}
+
+static void project2_c(const G* g, const cplx* full, cplx* c)
+{
+    init_basis();
+    for (int j = 0; j < g->nbs / 2; ++j)
+        for (int l3 = 0; l3 < g->V3; ++l3) {
+            int s = face2_site(g, j, l3);
+            cplx* cc = c + ((size_t)j * g->V3 + l3) * 6;
+            for (int i = 0; i < 2; ++i)
+                for (int col = 0; col < 3; ++col) {
+                    cplx v = 0;
+                    for (int sp = 0; sp < 4; ++sp) v += BASIS[0][i][sp] * full[(size_t)s * 12 + sp * 3 + col];
+                    cc[i * 3 + col] = v;
+                }
+        }
+}
+
+void lqo_embed_boundary2(const lqo_geom* gi, const double* coords, double* full)
+{
+    G g = mkg(gi);
+    embed2_c(&g, (const cplx*)coords, (cplx*)full);
+}
+
+void lqo_project_boundary2(const lqo_geom* gi, const double* full, double* coords)
+{
+    G g = mkg(gi);
+    project2_c(&g, (const cplx*)full, (cplx*)coords);
+}
+
+static void schur2_R_c(rctx* r, const cplx* in, cplx* out, int dagger)
+{
+    const G* g = r->g;
+    size_t n = (size_t)g->V * 12;
+    int nb2 = (g->nbs / 2) * g->V3 * 6;
+    cplx* e = malloc(sizeof(cplx) * n);
+    cplx* y = malloc(sizeof(cplx) * n);
+    cplx* z = malloc(sizeof(cplx) * n);
+    embed2_c(g, in, e);
+    if (!dagger) {
+        /* y = D2^-1 e; z = B2 y; y = A2^-1 z; z = C2 y */
+        r->status |= block_solve2_c(g, r->U, r->kappa, y, e, 1, 0, r->tol, r->maxit, NULL);
+        hop_c(g, r->U, y, z, LQO_HOP_CROSS2, 0);
+        for (size_t i = 0; i < n; ++i) z[i] *= -r->kappa;
+        r->status |= block_solve2_c(g, r->U, r->kappa, y, z, 0, 0, r->tol, r->maxit, NULL);
+        hop_c(g, r->U, y, z, LQO_HOP_CROSS2, 0);
+        for (size_t i = 0; i < n; ++i) z[i] *= -r->kappa;
+    } else {
+        hop_c(g, r->U, e, z, LQO_HOP_CROSS2, 1);
+        for (size_t i = 0; i < n; ++i) z[i] *= -r->kappa;
+        r->status |= block_solve2_c(g, r->U, r->kappa, y, z, 0, 1, r->tol, r->maxit, NULL);
+        hop_c(g, r->U, y, z, LQO_HOP_CROSS2, 1);
+        for (size_t i = 0; i < n; ++i) z[i] *= -r->kappa;
+        r->status |= block_solve2_c(g, r->U, r->kappa, y, z, 1, 1, r->tol, r->maxit, NULL);
+        memcpy(z, y, sizeof(cplx) * n);
+    }
+    cplx* pz = malloc(sizeof(cplx) * nb2);
+    project2_c(g, z, pz);
+    for (int i = 0; i < nb2; ++i) out[i] = in[i] - pz[i];
+    free(pz); free(e); free(y); free(z);
+}
+
+static void op_R2_adj(void* c, const cplx* in, cplx* out, int dagger)
+{
+    rctx_adj* ra = (rctx_adj*)c;
+    schur2_R_c(ra->r, in, out, dagger ^ ra->adj);
+}
+
+static int schur2_c(const G* g, const cplx* U, double kappa, cplx* out, const cplx* in, int op, int route,
+                    double tol, int maxit)
+{
+    size_t n = (size_t)g->V * 12;
+    int nb2 = (g->nbs / 2) * g->V3 * 6;
+    rctx r = {g, U, kappa, tol * 1e-3 > 1e-14 ? tol * 1e-3 : 1e-14, maxit, 0};
+    if (op == LQO_R || op == LQO_RDAG) {
+        schur2_R_c(&r, in, out, op == LQO_RDAG);
+        return r.status;
+    }
+    int dagger = (op == LQO_RINVDAG);
+    if (route == 0) {
+        rctx_adj ra = {&r, dagger};
+        int st = cgnr(op_R2_adj, &ra, nb2, out, in, tol, maxit, NULL);
+        return st | r.status;
+    }
+    /* (1 - C2 A2^-1 B2 D2^-1)^-1 = D2 (W1^-1)_bb on the black sub-slabs */
+    cplx* e = malloc(sizeof(cplx) * n);
+    cplx* psi = malloc(sizeof(cplx) * n);
+    cplx* w = malloc(sizeof(cplx) * n);
+    double it = tol * 1e-2 > 1e-14 ? tol * 1e-2 : 1e-14;
+    int st;
+    embed2_c(g, in, e);
+    if (!dagger) {
+        st = block_solve_c(g, U, kappa, psi, e, -1, 0, it, maxit, NULL);
+        keep_colour2(g, psi, 1);
+        apply_1mkH(g, U, kappa, psi, w, LQO_HOP_INTRA2, 0);
+        keep_colour2(g, w, 1);
+    } else {
+        apply_1mkH(g, U, kappa, e, w, LQO_HOP_INTRA2, 1);
+        keep_colour2(g, w, 1);
+        st = block_solve_c(g, U, kappa, psi, w, -1, 1, it, maxit, NULL);
+        memcpy(w, psi, sizeof(cplx) * n);
+        keep_colour2(g, w, 1);
+    }
+    project2_c(g, w, out);
+    free(e); free(psi); free(w);
+    return st;
+}
+
+int lqo_schur2(const lqo_geom* gi, const double* U, double kappa, double* out, const double* in, int op,
+               int route, double tol, int maxit)
+{
+    G g = mkg(gi);
+    if (!g.l0s) return -2;
+    return schur2_c(&g, (const cplx*)U, kappa, (cplx*)out, (const cplx*)in, op, route, tol, maxit);
+}
+
+/* S_W2 = |W2^-1 phi|^2: dS = -2 Re <xi, dW2 eta>, dW2 = -kappa dH (intra sub-slab) */
+int lqo_pf_w2(const lqo_geom* gi, const double* Ud, double kappa, const double* phi, double* F, double* S,
+              double tol, int maxit)
+{
+    G g = mkg(gi);
+    const cplx* U = (const cplx*)Ud;
+    size_t n = (size_t)g.V * 12;
+    if (!g.l0s) return -2;
+    cplx* eta = malloc(sizeof(cplx) * n);
+    cplx* xi = malloc(sizeof(cplx) * n);
+    int st = block_solve2_c(&g, U, kappa, eta, (const cplx*)phi, -1, 0, tol, maxit, NULL);
+    if (S) *S = nrm2(eta, n);
+    if (F) {
+        st |= block_solve2_c(&g, U, kappa, xi, eta, -1, 1, tol, maxit, NULL);
+        bilinear_c(&g, U, xi, eta, LQO_HOP_INTRA2, kappa, F);
+    }
+    free(eta); free(xi);
+    return st;
+}
+
+/* S_R2 = |R2^-1 phi|^2: the four block-LU terms of the first level with
+ * (M, W1) replaced by (W1, W2): C2, B2 on the hops between the two
+ * sub-slabs of a slab, A2, D2 on the hops inside sub-slabs */
+int lqo_pf_schur2(const lqo_geom* gi, const double* Ud, double kappa, const double* phi, double* F,
+                  double* S, int route, double tol, int maxit)
+{
+    G g = mkg(gi);
+    const cplx* U = (const cplx*)Ud;
+    size_t n = (size_t)g.V * 12;
+    if (!g.l0s) return -2;
+    int nb2 = (g.nbs / 2) * g.V3 * 6;
+    cplx* eta = malloc(sizeof(cplx) * nb2);
+    cplx* xi = malloc(sizeof(cplx) * nb2);
+    int st = schur2_c(&g, U, kappa, eta, (const cplx*)phi, LQO_RINV, route, tol, maxit);
+    if (S) *S = nrm2(eta, nb2);
+    if (F) {
+        double it = tol * 1e-2 > 1e-14 ? tol * 1e-2 : 1e-14;
+        st |= schur2_c(&g, U, kappa, xi, eta, LQO_RINVDAG, route, tol, maxit);
+        cplx* et = malloc(sizeof(cplx) * n);
+        cplx* xt = malloc(sizeof(cplx) * n);
+        cplx* y1 = malloc(sizeof(cplx) * n);
+        cplx* y2 = malloc(sizeof(cplx) * n);
+        cplx* z1 = malloc(sizeof(cplx) * n);
+        cplx* z2 = malloc(sizeof(cplx) * n);
+        cplx* w = malloc(sizeof(cplx) * n);
+        embed2_c(&g, eta, et);
+        embed2_c(&g, xi, xt);
+        st |= block_solve2_c(&g, U, kappa, y1, et, 1, 0, it, maxit, NULL);
+        hop_c(&g, U, y1, w, LQO_HOP_CROSS2, 0);
+        for (size_t i = 0; i < n; ++i) w[i] *= -kappa;
+        st |= block_solve2_c(&g, U, kappa, y2, w, 0, 0, it, maxit, NULL);
+        hop_c(&g, U, xt, w, LQO_HOP_CROSS2, 1);
+        for (size_t i = 0; i < n; ++i) w[i] *= -kappa;
+        st |= block_solve2_c(&g, U, kappa, z1, w, 0, 1, it, maxit, NULL);
+        hop_c(&g, U, z1, w, LQO_HOP_CROSS2, 1);
+        for (size_t i = 0; i < n; ++i) w[i] *= -kappa;
+        st |= block_solve2_c(&g, U, kappa, z2, w, 1, 1, it, maxit, NULL);
+        bilinear_c(&g, U, xt, y2, LQO_HOP_CROSS2, -kappa, F);
+        bilinear_c(&g, U, z1, y2, LQO_HOP_INTRA2, +kappa, F);
+        bilinear_c(&g, U, z1, y1, LQO_HOP_CROSS2, -kappa, F);
+        bilinear_c(&g, U, z2, y1, LQO_HOP_INTRA2, +kappa, F);
+        free(et); free(xt); free(y1); free(y2); free(z1); free(z2); free(w);
+    }
+    free(eta); free(xi);
+    return st;
+}
+
+/* ------------------------------------------------------------------ */
 /* gauge action S_G = -beta/3 sum_x sum_{mu>nu} Re tr(plaquette)        */
 /* ------------------------------------------------------------------ */
 static double plaq_re(const G* g, const cplx* U, int s, int mu, int nu)
@@ -1120,6 +1403,8 @@ typedef struct {
     double* P;
     const double* phi1;
     const double* phi2;
+    const double* phi3; /* |W2^-1 phi3|^2 (iterated decomposition) */
+    const double* phi4; /* |R2^-1 phi4|^2 */
     double* F;
     int status;
 } md_t;
@@ -1139,6 +1424,15 @@ static void T_P(md_t* m, int j, double dt)
     if (p->level_schur == j) {
         m->status |= lqo_pf_schur(m->gi, m->U, p->kappa, m->phi2, m->F, NULL, p->schur_route,
                                   p->tol, p->maxit);
+        any = 1;
+    }
+    if (p->level_w2 == j) {
+        m->status |= lqo_pf_w2(m->gi, m->U, p->kappa, m->phi3, m->F, NULL, p->tol, p->maxit);
+        any = 1;
+    }
+    if (p->level_schur2 == j) {
+        m->status |= lqo_pf_schur2(m->gi, m->U, p->kappa, m->phi4, m->F, NULL, p->schur_route, p->tol,
+                                   p->maxit);
         any = 1;
     }
     if (!any) return;
@@ -1179,11 +1473,11 @@ static void step(md_t* m, int j, double dt)
 /* the molecular-dynamics part of a trajectory, T_LF/SW,top(dt_top)^n_top,
  * on (U, P) in place for fixed pseudo-fermion fields */
 int lqo_md(const lqo_geom* gi, double* U, double* P, const double* phi1, const double* phi2,
-           const lqo_hmc_params* p)
+           const double* phi3, const double* phi4, const lqo_hmc_params* p)
 {
     G g = mkg(gi);
     double* F = malloc(sizeof(double) * (size_t)4 * g.V * 8);
-    md_t m = {&g, gi, p, U, P, phi1, phi2, F, 0};
+    md_t m = {&g, gi, p, U, P, phi1, phi2, phi3, phi4, F, 0};
     int top = p->nlevels - 1;
     double dt = p->tau / p->nsteps[top];
     for (int i = 0; i < p->nsteps[top]; ++i) step(&m, top, dt);
@@ -1205,11 +1499,16 @@ int lqo_hmc_trajectory(const lqo_geom* gi, double* U, const lqo_hmc_params* p, u
     G g = mkg(gi);
     size_t nl = (size_t)4 * g.V * 8, n = (size_t)g.V * 12, nu = (size_t)4 * g.V * 9;
     int nbnd = (g.nb / 2) * 2 * g.V3 * 6;
+    int nb2 = (g.nbs / 2) * g.V3 * 6;
     double* P = malloc(sizeof(double) * nl);
     double* e1 = malloc(sizeof(cplx) * n);
     double* e2 = malloc(sizeof(cplx) * nbnd);
     double* phi1 = malloc(sizeof(cplx) * n);
     double* phi2 = malloc(sizeof(cplx) * nbnd);
+    double* e3 = malloc(sizeof(cplx) * n);
+    double* phi3 = malloc(sizeof(cplx) * n);
+    double* e4 = malloc(sizeof(cplx) * (nb2 + 1));
+    double* phi4 = malloc(sizeof(cplx) * (nb2 + 1));
     double* U0 = malloc(sizeof(cplx) * nu);
     memcpy(U0, U, sizeof(cplx) * nu);
     int st = 0;
@@ -1250,8 +1549,31 @@ int lqo_hmc_trajectory(const lqo_geom* gi, double* U, const lqo_hmc_params* p, u
             H0 += S;
         }
     }
-    st |= lqo_md(gi, U, P, phi1, phi2, p);
+    /* iterated decomposition: phi3 = W2 eta3 (stream 5), phi4 = R2 eta4 (stream 6) */
+    if (p->level_w2 >= 0) {
+        lqo_normals(seed, 5, traj, (int64_t)n * 2, e3);
+        for (size_t i = 0; i < n * 2; ++i) e3[i] *= sqrt(0.5);
+        lqo_apply_W2(gi, U, p->kappa, e3, phi3, 0);
+        H0 += nrm2((const cplx*)e3, n);
+    }
+    if (p->level_schur2 >= 0) {
+        lqo_normals(seed, 6, traj, (int64_t)nb2 * 2, e4);
+        for (int i = 0; i < nb2 * 2; ++i) e4[i] *= sqrt(0.5);
+        st |= lqo_schur2(gi, U, p->kappa, phi4, e4, LQO_R, p->schur_route, p->tol, p->maxit);
+        H0 += nrm2((const cplx*)e4, nb2);
+    }
+    st |= lqo_md(gi, U, P, phi1, phi2, phi3, phi4, p);
     double H1 = kinetic(P, nl);
+    if (p->level_w2 >= 0) {
+        double S;
+        st |= lqo_pf_w2(gi, U, p->kappa, phi3, NULL, &S, p->tol, p->maxit);
+        H1 += S;
+    }
+    if (p->level_schur2 >= 0) {
+        double S;
+        st |= lqo_pf_schur2(gi, U, p->kappa, phi4, NULL, &S, p->schur_route, p->tol, p->maxit);
+        H1 += S;
+    }
     if (p->level_gauge >= 0) H1 += lqo_gauge_action(gi, U, p->beta);
     if (p->level_w1 >= 0) {
         double S;
@@ -1278,5 +1600,6 @@ int lqo_hmc_trajectory(const lqo_geom* gi, double* U, const lqo_hmc_params* p, u
         res->plaq = lqo_plaquette(gi, U);
     }
     free(P); free(e1); free(e2); free(phi1); free(phi2); free(U0);
+    free(e3); free(phi3); free(e4); free(phi4);
     return st;
 }

@@ -31,9 +31,11 @@ typedef struct {
     int L[4];  /* L0 (time, slab direction), L1, L2, L3 */
     int l0;    /* slab thickness; L0 % (2*l0) == 0 */
     int bc_t;  /* +1 periodic / -1 antiperiodic fermion wrap in x0 */
+    int l0s;   /* iterated decomposition (Sec. 1): sub-slabs of thickness
+                  l0s = l0/2 (W2); 0 = none */
 } lqo_geom;
 
-enum { LQO_HOP_ALL = 0, LQO_HOP_INTRA = 1, LQO_HOP_CROSS = 2 };
+enum { LQO_HOP_ALL = 0, LQO_HOP_INTRA = 1, LQO_HOP_CROSS = 2, LQO_HOP_INTRA2 = 3, LQO_HOP_CROSS2 = 4 };
 enum { LQO_R = 0, LQO_RDAG = 1, LQO_RINV = 2, LQO_RINVDAG = 3 };
 enum { LQO_LF = 0, LQO_SW = 1 };
 
@@ -50,6 +52,7 @@ typedef struct {
     double tol;       /* relative residual of every linear solve */
     int maxit;
     const double* step_scale; /* NULL, or [2][L0] s(x0) for space-like / time-like links */
+    int level_w2, level_schur2; /* iterated decomposition terms, -1: left out */
 } lqo_hmc_params;
 
 typedef struct {
@@ -107,7 +110,21 @@ void lqo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 void lqo_normals(uint64_t seed, uint32_t stream, uint32_t traj, int64_t n, double* out);
 void lqo_uniforms_metropolis(uint64_t seed, uint32_t traj, int L0, double* u, int* shift);
 int  lqo_md(const lqo_geom* g, double* U, double* P, const double* phi1,
-            const double* phi2, const lqo_hmc_params* prm);
+            const double* phi2, const double* phi3, const double* phi4,
+            const lqo_hmc_params* prm);
+int  lqo_block_solve2(const lqo_geom* g, const double* U, double kappa, double* x,
+                      const double* b, int colour, int dagger, double tol, int maxit, int* iters);
+void lqo_apply_W2(const lqo_geom* g, const double* U, double kappa, const double* in,
+                  double* out, int dagger);
+int  lqo_nbnd2(const lqo_geom* g);
+void lqo_embed_boundary2(const lqo_geom* g, const double* coords, double* full);
+void lqo_project_boundary2(const lqo_geom* g, const double* full, double* coords);
+int  lqo_schur2(const lqo_geom* g, const double* U, double kappa, double* out,
+                const double* in, int op, int route, double tol, int maxit);
+int  lqo_pf_w2(const lqo_geom* g, const double* U, double kappa, const double* phi,
+               double* F, double* S, double tol, int maxit);
+int  lqo_pf_schur2(const lqo_geom* g, const double* U, double kappa, const double* phi,
+                   double* F, double* S, int route, double tol, int maxit);
 int  lqo_hmc_trajectory(const lqo_geom* g, double* U, const lqo_hmc_params* prm,
                         uint64_t seed, uint32_t traj, const double* P0,
                         const double* eta1, const double* eta2,

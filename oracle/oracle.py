@@ -11,7 +11,7 @@ import numpy as np
 
 from . import build as _build
 
-HOP_ALL, HOP_INTRA, HOP_CROSS = 0, 1, 2
+HOP_ALL, HOP_INTRA, HOP_CROSS, HOP_INTRA2, HOP_CROSS2 = 0, 1, 2, 3, 4
 R, RDAG, RINV, RINVDAG = 0, 1, 2, 3
 LF, SW = 0, 1
 
@@ -19,7 +19,7 @@ _lib = None
 
 
 class Geom(C.Structure):
-    _fields_ = [("L", C.c_int * 4), ("l0", C.c_int), ("bc_t", C.c_int)]
+    _fields_ = [("L", C.c_int * 4), ("l0", C.c_int), ("bc_t", C.c_int), ("l0s", C.c_int)]
 
 
 class HmcParams(C.Structure):
@@ -29,7 +29,7 @@ class HmcParams(C.Structure):
         ("level_gauge", C.c_int), ("level_w1", C.c_int), ("level_schur", C.c_int),
         ("pf_init", C.c_int), ("roll", C.c_int), ("schur_route", C.c_int),
         ("metropolis", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
-        ("step_scale", C.c_void_p),
+        ("step_scale", C.c_void_p), ("level_w2", C.c_int), ("level_schur2", C.c_int),
     ]
 
 
@@ -54,18 +54,22 @@ def _p(a):
 
 
 class Lattice:
-    """Geometry L = (L0, L1, L2, L3) with x0-slabs of thickness l0."""
+    """Geometry L = (L0, L1, L2, L3) with x0-slabs of thickness l0 and,
+    for the iterated decomposition, sub-slabs of thickness l0s = l0/2."""
 
-    def __init__(self, L, l0, bc_t=-1):
+    def __init__(self, L, l0, bc_t=-1, l0s=0):
         self.L = tuple(int(v) for v in L)
         self.l0 = int(l0)
         self.bc_t = int(bc_t)
-        self.g = Geom((C.c_int * 4)(*self.L), self.l0, self.bc_t)
+        self.l0s = int(l0s)
+        self.g = Geom((C.c_int * 4)(*self.L), self.l0, self.bc_t, self.l0s)
         self.V3 = self.L[1] * self.L[2] * self.L[3]
         self.V = self.L[0] * self.V3
         self.Vh = self.V // 2
         self.nb = self.L[0] // self.l0
         self.nbnd = (self.nb // 2) * 2 * self.V3 * 6
+        self.nbs = self.L[0] // self.l0s if self.l0s else 0
+        self.nbnd2 = (self.nbs // 2) * self.V3 * 6
         st = lib().lqo_geom_check(C.byref(self.g))
         if st != 0:
             raise ValueError("invalid geometry L=%s l0=%d (status %d)" % (self.L, self.l0, st))
@@ -192,6 +196,63 @@ class Lattice:
             raise RuntimeError("oracle Schur force: a solve did not converge")
         return S.value, F
 
+    # ---- iterated decomposition (second level) -------------------------
+    def bnd2_shape(self):
+        return (self.nbs // 2, self.V3, 2, 3)
+
+    def W2(self, U, kappa, x, dagger=0):
+        out = np.zeros(self.spinor_shape(), np.complex128)
+        lib().lqo_apply_W2(C.byref(self.g), _p(U), C.c_double(kappa), _p(np.ascontiguousarray(x)),
+                           _p(out), dagger)
+        return out
+
+    def block_solve2(self, U, kappa, b, colour=-1, dagger=0, tol=1e-13, maxit=20000):
+        x = np.zeros(self.spinor_shape(), np.complex128)
+        it = C.c_int(0)
+        st = lib().lqo_block_solve2(C.byref(self.g), _p(U), C.c_double(kappa), _p(x),
+                                    _p(np.ascontiguousarray(b)), colour, dagger, C.c_double(tol),
+                                    maxit, C.byref(it))
+        if st:
+            raise RuntimeError("oracle sub-slab solve did not converge")
+        return x
+
+    def embed2(self, c):
+        out = np.zeros(self.spinor_shape(), np.complex128)
+        lib().lqo_embed_boundary2(C.byref(self.g), _p(np.ascontiguousarray(c)), _p(out))
+        return out
+
+    def project2(self, full):
+        out = np.zeros(self.bnd2_shape(), np.complex128)
+        lib().lqo_project_boundary2(C.byref(self.g), _p(np.ascontiguousarray(full)), _p(out))
+        return out
+
+    def schur2(self, U, kappa, c, op=R, route=1, tol=1e-12, maxit=50000):
+        out = np.zeros(self.bnd2_shape(), np.complex128)
+        st = lib().lqo_schur2(C.byref(self.g), _p(U), C.c_double(kappa), _p(out),
+                              _p(np.ascontiguousarray(c)), op, route, C.c_double(tol), maxit)
+        if st:
+            raise RuntimeError("oracle second-level Schur operator: a solve did not converge")
+        return out
+
+    def pf_w2(self, U, kappa, phi, force=True, tol=1e-13, maxit=20000):
+        F = np.zeros((4, self.V, 8)) if force else None
+        S = C.c_double(0)
+        st = lib().lqo_pf_w2(C.byref(self.g), _p(U), C.c_double(kappa), _p(np.ascontiguousarray(phi)),
+                             _p(F) if force else None, C.byref(S), C.c_double(tol), maxit)
+        if st:
+            raise RuntimeError("oracle W2 force: a solve did not converge")
+        return S.value, F
+
+    def pf_schur2(self, U, kappa, phi, force=True, route=1, tol=1e-12, maxit=50000):
+        F = np.zeros((4, self.V, 8)) if force else None
+        S = C.c_double(0)
+        st = lib().lqo_pf_schur2(C.byref(self.g), _p(U), C.c_double(kappa),
+                                 _p(np.ascontiguousarray(phi)), _p(F) if force else None,
+                                 C.byref(S), route, C.c_double(tol), maxit)
+        if st:
+            raise RuntimeError("oracle second-level Schur force: a solve did not converge")
+        return S.value, F
+
     def force_profile(self, F):
         out = np.zeros((2, self.L[0]))
         lib().lqo_force_profile(C.byref(self.g), _p(np.ascontiguousarray(F)), _p(out))
@@ -257,14 +318,14 @@ def metropolis_uniforms(seed, traj, L0):
 
 def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w1=0,
                level_schur=0, lam=1.0 / 6.0, pf_init=0, roll=0, schur_route=1, metropolis=1,
-               tol=1e-12, maxit=50000, step_scale=None):
+               tol=1e-12, maxit=50000, step_scale=None, level_w2=-1, level_schur2=-1):
     """step_scale: None, or a float64 array (2, L0) of s(x0) for space-like /
     time-like links (see step_scheme)"""
     sc = list(scheme) + [0] * (4 - len(scheme))
     ns = list(nsteps) + [1] * (4 - len(nsteps))
     p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * 4)(*sc), (C.c_int * 4)(*ns),
                   level_gauge, level_w1, level_schur, pf_init, roll, schur_route, metropolis,
-                  tol, maxit, None)
+                  tol, maxit, None, level_w2, level_schur2)
     if step_scale is not None:
         p._scale = np.ascontiguousarray(step_scale, dtype=np.float64)
         p.step_scale = p._scale.ctypes.data
@@ -279,11 +340,13 @@ def step_scheme(scheme, L0):
     return out
 
 
-def md(lat, U, P, phi1, phi2, prm):
-    """molecular dynamics only: integrates (U, P) for fixed phi1, phi2"""
+def md(lat, U, P, phi1, phi2, prm, phi3=None, phi4=None):
+    """molecular dynamics only: integrates (U, P) for fixed pseudofermions"""
     U2 = np.array(U, dtype=np.complex128, copy=True)
     P2 = np.array(P, dtype=np.float64, copy=True)
     a1 = np.ascontiguousarray(phi1) if phi1 is not None else np.zeros(lat.spinor_shape(), np.complex128)
     a2 = np.ascontiguousarray(phi2) if phi2 is not None else np.zeros(lat.bnd_shape(), np.complex128)
-    st = lib().lqo_md(C.byref(lat.g), _p(U2), _p(P2), _p(a1), _p(a2), C.byref(prm))
+    a3 = np.ascontiguousarray(phi3) if phi3 is not None else np.zeros(lat.spinor_shape(), np.complex128)
+    a4 = np.ascontiguousarray(phi4) if phi4 is not None else np.zeros(lat.bnd2_shape(), np.complex128)
+    st = lib().lqo_md(C.byref(lat.g), _p(U2), _p(P2), _p(a1), _p(a2), _p(a3), _p(a4), C.byref(prm))
     return U2, P2, st
