@@ -35,6 +35,11 @@
  *                           with basis (e_i + e_{i+2})/sqrt2 of range
  *                           (1-gamma_0)/2, i = 0,1; V3 spatial sites in
  *                           lexicographic (x1,x2,x3) order.
+ *   second-level boundary   double[L0/(2 l0s)][V3][2][3][2] (iterated
+ *   field (R2)              decomposition, lqcd_set_subslabs): black
+ *                           sub-slab 2j+1 (sub-slab k = x0 / l0s) has
+ *                           ordinal j; its first time slice with the face-0
+ *                           spin basis above.
  * Gamma matrices: chiral basis, gamma_0 = [[0,-1],[-1,0]],
  *   gamma_k = [[0,-i sigma_k],[i sigma_k,0]], gamma_5 = diag(1,1,-1,-1).
  * Fermion phase bc_t (+1 / -1) on every x0 hop that wraps L0-1 <-> 0.
@@ -67,8 +72,9 @@ enum {
 
 enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2 };
 enum { LQCD_OP_HOP = 0, LQCD_OP_MHAT = 1 };
-enum { LQCD_SCHUR_R = 0, LQCD_SCHUR_RDAG = 1, LQCD_SCHUR_RINV = 2, LQCD_SCHUR_RINVDAG = 3 };
-enum { LQCD_TERM_W1 = 0, LQCD_TERM_SCHUR = 1 };
+enum { LQCD_SCHUR_R = 0, LQCD_SCHUR_RDAG = 1, LQCD_SCHUR_RINV = 2, LQCD_SCHUR_RINVDAG = 3,
+       LQCD_SCHUR2_R = 4, LQCD_SCHUR2_RDAG = 5, LQCD_SCHUR2_RINV = 6, LQCD_SCHUR2_RINVDAG = 7 };
+enum { LQCD_TERM_W1 = 0, LQCD_TERM_SCHUR = 1, LQCD_TERM_W2 = 2, LQCD_TERM_SCHUR2 = 3 };
 enum { LQCD_LF = 0, LQCD_SW = 1 };
 
 /* Create a handle for the lattice L[4] with x0-slabs of thickness l0 and
@@ -81,6 +87,21 @@ int lqcd_create(lqcd_t* h, const int L[4], int l0, int bc_t, void* stream);
 int lqcd_destroy(lqcd_t h);
 const char* lqcd_last_error(lqcd_t h);
 int lqcd_set_stream(lqcd_t h, void* stream);
+
+/* Iterated decomposition (Sec. 1: the one-dimensional slabs can be
+ * decomposed again, second step l0^(2) = l0^(1)/2): split
+ * every slab once more into two sub-slabs of thickness l0s = l0 / 2,
+ * sub-slab k = x0 / l0s with colour k mod 2.  W2 is eq. (2) with every hop
+ * between different sub-slabs removed.  With the sites of W1 ordered
+ * red|black by sub-slab colour, W1 = [[A2,B2],[C2,D2]], W2 = diag(A2,D2)
+ * and det W1 = det W2 det R2 with R2 = E2 (1 - C2 A2^-1 B2 D2^-1) E2^dag on
+ * the second-level boundary field (layout above): the range of C2 is the
+ * first slice of each black sub-slab (its last slice borders the next slab,
+ * which W1 does not reach).  Together det M = det R det R2 det W2.
+ * Enables lqcd_subblock_*, LQCD_SCHUR2_*, LQCD_TERM_W2 / _SCHUR2 and the
+ * level_w2 / level_schur2 trajectory terms.  l0s = 0 switches it off.
+ * Errors: LQCD_ERR_GEOM (l0 odd or l0s != l0/2). */
+int lqcd_set_subslabs(lqcd_t h, int l0s);
 
 /* Load the gauge field U (device, gauge layout above, SU(3) links) into the
  * handle; builds the double, single (12-real, two rows) and half (12-real)
@@ -130,6 +151,17 @@ int lqcd_block_solve_batched(lqcd_t h, double* x, const double* b, double kappa,
                              int dagger, int precision, double tol, int max_iter,
                              int* iters_out, double* resid_out);
 
+/* W2 (iterated decomposition, see lqcd_set_subslabs): the same as
+ * lqcd_block_dslash / lqcd_block_solve_batched with the sub-slabs in place
+ * of the slabs; colour is the sub-slab colour, iters_out / resid_out are
+ * indexed by sub-slab (host arrays of L0/l0s entries).
+ * Errors as there, and LQCD_ERR_STATE without sub-slabs. */
+int lqcd_subblock_dslash(lqcd_t h, double* out, const double* in, double kappa, int colour,
+                         int dagger, int precision);
+int lqcd_subblock_solve_batched(lqcd_t h, double* x, const double* b, double kappa, int colour,
+                                int dagger, int precision, double tol, int max_iter,
+                                int* iters_out, double* resid_out);
+
 /* Solve M x = b (dagger: M^dag x = b) on the full lattice: even-odd reduced
  * BiCGstab, inner iterations in `precision`, double precision defect
  * correction to |b - M x| <= tol |b|.  iters_out / resid_out: host scalars
@@ -145,13 +177,21 @@ int lqcd_solve_wilson(lqcd_t h, double* x, const double* b, double kappa, int da
  *   R = E (1 - C A^-1 B D^-1) E^dag
  * on the boundary space (E: orthonormal spin-projected black-face
  * coordinates, layout above).  op: R, R^dag, R^-1 = E D (M^-1)_bb E^dag,
- * R^-dag.  in/out: boundary fields.  Synchronous. */
+ * R^-dag.  in/out: boundary fields.
+ * op LQCD_SCHUR2_*: the same four operators one level down (lqcd_set_subslabs):
+ * R2 = E2 (1 - C2 A2^-1 B2 D2^-1) E2^dag with B2 = C2 = -kappa H between the
+ * two sub-slabs of a slab, R2^-1 = E2 D2 (W1^-1)_bb E2^dag; in/out are
+ * second-level boundary fields (LQCD_ERR_STATE without sub-slabs).
+ * Synchronous. */
 int lqcd_schur_apply(lqcd_t h, double* out, const double* in, double kappa, int op,
                      int precision, double tol, int max_iter);
 
 /* Pseudo-fermion action and force (Sec. 1 eq. (3), Sec. 2 eq. (4)):
  * term W1:    S = |W1^-1 phi|^2, phi a full-lattice spinor;
- * term SCHUR: S = |R^-1 phi|^2, phi a boundary field.
+ * term SCHUR: S = |R^-1 phi|^2, phi a boundary field;
+ * term W2:    S = |W2^-1 phi|^2, phi a full-lattice spinor;
+ * term SCHUR2: S = |R2^-1 phi|^2, phi a second-level boundary field
+ * (W2 / SCHUR2: iterated decomposition, LQCD_ERR_STATE without sub-slabs).
  * F (device double[4][V][8]) += dS/dw^a for U_mu(x) -> exp(i w^a T^a) U_mu(x)
  * (not zeroed).  S_out (host, may be NULL) receives S.  F may be NULL to
  * compute S only.  Solutions are recomputed, never stored.  Synchronous. */
@@ -204,6 +244,13 @@ typedef struct {
      * step_scheme.  s = 0 freezes a link. */
     int step_scheme;
     const double* step_scale;
+    /* iterated decomposition (lqcd_set_subslabs): levels of |W2^-1 phi3|^2
+     * and |R2^-1 phi4|^2, or -1 (must be -1 without sub-slabs).  The action
+     * S_G + |R^-1 phi2|^2 + |R2^-1 phi4|^2 + |W2^-1 phi3|^2 takes
+     * level_w1 = -1.  phi3 = W2 eta3, phi4 = R2 eta4 are always drawn by the
+     * heatbath (Philox streams 5 and 6; pf_init applies to phi1, phi2). */
+    int level_w2;
+    int level_schur2;
 } lqcd_hmc_params;
 
 typedef struct {
@@ -221,7 +268,8 @@ typedef struct {
 } lqcd_hmc_result;
 
 /* One HMC trajectory (Sec. 2): heatbath (momenta p^a ~ N(0,1), eta ~
- * exp(-|eta|^2)), phi1 = W1 eta1, phi2 = R eta2, molecular dynamics
+ * exp(-|eta|^2)), phi1 = W1 eta1, phi2 = R eta2 (and phi3, phi4 of the
+ * iterated decomposition), molecular dynamics
  * T_{X,top}(dt_top)^{n_top} with the recursive LF / SW levels of eqs.
  * (5)-(7), Metropolis on dH, then the x0 shift of the configuration.
  * U: device gauge field, overwritten with the field after the trajectory.
@@ -233,10 +281,11 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
                         const double* eta2, lqcd_hmc_result* res);
 
 /* Molecular dynamics only: integrates (U, P) in place (device buffers, gauge
- * and momenta layouts) for fixed phi1 (full spinor) / phi2 (boundary
- * field); either may be NULL when its term is left out.  Synchronous. */
+ * and momenta layouts) for fixed phi1 (full spinor), phi2 (boundary field),
+ * phi3 (full spinor, W2 term) and phi4 (second-level boundary field); each
+ * may be NULL when its term is left out.  Synchronous. */
 int lqcd_md(lqcd_t h, double* U, double* P, const double* phi1, const double* phi2,
-            const lqcd_hmc_params* prm);
+            const double* phi3, const double* phi4, const lqcd_hmc_params* prm);
 
 /* Kernel timing with CUDA events on the handle's stream.  kernel ids:
  * 0 hopping sweep, 1 persistent solver, 2 force, 3 gauge force / update,

@@ -10,6 +10,11 @@
 //   dS_R   = 2 Re <eta~, dD psi> - 2 Re <chi, dM psi> with psi = M^-1 E^dag phi,
 //            eta~ = E^dag E D psi_b (so S_R = |eta~|^2), chi = M^-dag D^dag eta~
 //   dS_W1  = -2 Re <xi, dW1 eta>, eta = W1^-1 phi, xi = W1^-dag eta
+// Second level of the iterated decomposition (Sec. 1), the same formulas one
+// level down: (M, W1, H_cross, H_intra) -> (W1, W2, H_cross2, H_intra2), the
+// sub-slab operators run on the sub-slab geometry (GeoScope), the boundary
+// is the first slice of every black sub-slab.
+//   R2^-1 = E2 D2 (W1^-1)_bb E2^dag,  S_R2 = |R2^-1 phi|^2, S_W2 = |W2^-1 phi|^2
 #include <math.h>
 #include <string.h>
 
@@ -23,11 +28,13 @@ int bnd_sub(lqcd_ctx* h, double* out, const double* in, int n);
 
 namespace {
 
-enum { F_T1 = 0, F_T2, F_A, F_B, F_C, F_D, F_E, F_G, F_PHI1, F_ETA1, NFIELD };
+enum { F_T1 = 0, F_T2, F_A, F_B, F_C, F_D, F_E, F_G, F_PHI1, F_ETA1, F_PHI3, NFIELD };
 
 inline double2* fld(lqcd_ctx* h, int k) { return h->f64[k]; }
 
 int nbnd_of(const Geo& g) { return (g.nb / 2) * 2 * g.V3 * 6; }
+// complex entries of a second-level boundary field (first slices only)
+int nbnd2_of(const Geo& g1) { return g1.l0s ? (g1.L[0] / g1.l0s / 2) * g1.V3 * 6 : 0; }
 
 bool prec_ok(int p) { return p == LQCD_PREC_F64 || p == LQCD_PREC_F32 || p == LQCD_PREC_F16; }
 
@@ -149,6 +156,94 @@ int pf_schur(lqcd_ctx* h, double* F, const double* phi, double kappa, double coe
 }
 
 // ---------------------------------------------------------------------------
+// second level (iterated decomposition); all called with h->g the level-1
+// geometry and h->g1.l0s > 0
+// ---------------------------------------------------------------------------
+// x = W2^-1 b on the sub-slabs of `colour` (-1: all)
+int sub_solve(lqcd_ctx* h, int colour, int dagger, const SolveCfg& c, double kappa, double2* x, const double2* b)
+{
+    GeoScope sc(h, sub_geo(h->g1));
+    return solve_full(h, MODE_INTRA, colour, dagger, c.prec, kappa, x, b, c.tol, c.max_iter, nullptr, nullptr);
+}
+
+// out = a x + c H_intra2 in (dag: H^dag) on the sub-slabs of `colour`
+int sub_hop(lqcd_ctx* h, int dag, int colour, double2* out, const double2* in, double a, const double2* x, double c)
+{
+    GeoScope sc(h, sub_geo(h->g1));
+    return hop_full(h, MODE_INTRA, dag, colour, out, in, a, x, c);
+}
+
+int embed2(lqcd_ctx* h, double2* full, const double* coords)
+{
+    GeoScope sc(h, sub_geo(h->g1));
+    return embed_boundary(h, full, coords, 1);
+}
+
+int project2(lqcd_ctx* h, double* coords, const double2* full)
+{
+    GeoScope sc(h, sub_geo(h->g1));
+    return project_boundary(h, coords, full, 1);
+}
+
+// R2, R2^dag, R2^-1, R2^-dag (op 0..3) on second-level boundary fields
+int schur2_op(lqcd_ctx* h, double* out, const double* in, double kappa, int op, const SolveCfg& c)
+{
+    double2 *A = fld(h, F_A), *B = fld(h, F_B), *C = fld(h, F_C), *D = fld(h, F_D), *E = fld(h, F_E);
+    LQ_TRY(embed2(h, A, in));
+    if (op == LQCD_SCHUR_R) {
+        // (1 - C2 A2^-1 B2 D2^-1), B2 = C2 = -kappa H_cross2
+        LQ_TRY(sub_solve(h, 1, 0, c, kappa, B, A));
+        LQ_TRY(hop_full(h, MODE_CROSS2, 0, -1, C, B, 0.0, nullptr, -kappa));
+        LQ_TRY(sub_solve(h, 0, 0, c, kappa, D, C));
+        LQ_TRY(hop_full(h, MODE_CROSS2, 0, -1, E, D, 0.0, nullptr, -kappa));
+        LQ_TRY(project2(h, out, E));
+    } else if (op == LQCD_SCHUR_RDAG) {
+        LQ_TRY(hop_full(h, MODE_CROSS2, 1, -1, C, A, 0.0, nullptr, -kappa));
+        LQ_TRY(sub_solve(h, 0, 1, c, kappa, D, C));
+        LQ_TRY(hop_full(h, MODE_CROSS2, 1, -1, E, D, 0.0, nullptr, -kappa));
+        LQ_TRY(sub_solve(h, 1, 1, c, kappa, B, E));
+        LQ_TRY(project2(h, out, B));
+    } else if (op == LQCD_SCHUR_RINV) {
+        LQ_TRY(solve_full(h, MODE_INTRA, -1, 0, c.prec, kappa, B, A, c.tol, c.max_iter, nullptr, nullptr));
+        LQ_TRY(sub_hop(h, 0, 1, C, B, 1.0, B, -kappa));
+        return project2(h, out, C);
+    } else {
+        LQ_TRY(sub_hop(h, 1, 1, C, A, 1.0, A, -kappa));
+        LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, B, C, c.tol, c.max_iter, nullptr, nullptr));
+        return project2(h, out, B);
+    }
+    return bnd_sub(h, out, in, 2 * nbnd2_of(h->g1));
+}
+
+// F += coef * dS/dw for S = |W2^-1 phi|^2
+int pf_w2(lqcd_ctx* h, double* F, const double2* phi, double kappa, double coef, const SolveCfg& c,
+          double* S_dev, const double* ss = nullptr)
+{
+    GeoScope sc(h, sub_geo(h->g1));
+    return pf_w1(h, F, phi, kappa, coef, c, S_dev, ss);
+}
+
+// F += coef * dS/dw for S = |R2^-1 phi|^2 (phi: device second-level boundary field)
+int pf_schur2(lqcd_ctx* h, double* F, const double* phi, double kappa, double coef, const SolveCfg& c,
+              double* S_dev, const double* ss = nullptr)
+{
+    double2 *A = fld(h, F_A), *psi = fld(h, F_B), *C = fld(h, F_C), *et = fld(h, F_D), *E = fld(h, F_E),
+            *chi = fld(h, F_G);
+    double* eta = h->bnd[1];
+    LQ_TRY(embed2(h, A, phi));
+    LQ_TRY(solve_full(h, MODE_INTRA, -1, 0, c.prec, kappa, psi, A, c.tol, c.max_iter, nullptr, nullptr));
+    LQ_TRY(sub_hop(h, 0, 1, C, psi, 1.0, psi, -kappa));
+    LQ_TRY(project2(h, eta, C));
+    if (S_dev) LQ_TRY(norm2_dev(h, eta, 2 * nbnd2_of(h->g1), S_dev));
+    if (!F) return LQCD_OK;
+    LQ_TRY(embed2(h, et, eta));
+    LQ_TRY(sub_hop(h, 1, 1, E, et, 1.0, et, -kappa));
+    LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, chi, E, c.tol, c.max_iter, nullptr, nullptr));
+    return force_bilinear(h, F, et, psi, MODE_INTRA2, -kappa * coef, chi, psi, MODE_INTRA, kappa * coef, c.prec,
+                          ss);
+}
+
+// ---------------------------------------------------------------------------
 // integrator schedule (Sec. 2, eqs. (5)-(7)); consecutive kicks of one level
 // act on the same field and are merged
 // ---------------------------------------------------------------------------
@@ -215,12 +310,16 @@ int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
             return LQCD_ERR_ARG;
         }
     }
-    const int lv[3] = {p->level_gauge, p->level_w1, p->level_schur};
-    for (int k = 0; k < 3; ++k)
+    const int lv[5] = {p->level_gauge, p->level_w1, p->level_schur, p->level_w2, p->level_schur2};
+    for (int k = 0; k < 5; ++k)
         if (lv[k] < -1 || lv[k] >= p->nlevels) {
             h->err = "hmc params: term level out of range";
             return LQCD_ERR_ARG;
         }
+    if ((p->level_w2 >= 0 || p->level_schur2 >= 0) && !h->g1.l0s) {
+        h->err = "hmc params: the W2 / R2 terms need sub-slabs (lqcd_set_subslabs)";
+        return LQCD_ERR_STATE;
+    }
     if (!p->step_scale && p->step_scheme) {
         const int per[4] = {0, 6, 8, 16};
         if (p->step_scheme < 0 || p->step_scheme > 3 || h->g.L[0] % per[p->step_scheme]) {
@@ -264,7 +363,15 @@ int md_scale_table(lqcd_ctx* h, const lqcd_hmc_params& p, const double** out)
     return LQCD_OK;
 }
 
-int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const double2* phi1, const double* phi2, int* nforce)
+// pseudo-fermion fields of the MD: phi1 (W1), phi2 (R), phi3 (W2), phi4 (R2)
+struct PfFields {
+    const double2* phi1;
+    const double* phi2;
+    const double2* phi3;
+    const double* phi4;
+};
+
+int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, int* nforce)
 {
     std::vector<Op> ops;
     const int top = p.nlevels - 1;
@@ -280,11 +387,19 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const double2* phi1,
         }
         if (p.level_gauge == o.level) LQ_TRY(gauge_force_kick(h, P, -o.dt * p.beta / 6.0, p.precision, ss));
         if (p.level_w1 == o.level) {
-            LQ_TRY(pf_w1(h, P, phi1, p.kappa, -o.dt, c, nullptr, ss));
+            LQ_TRY(pf_w1(h, P, pf.phi1, p.kappa, -o.dt, c, nullptr, ss));
             ++*nforce;
         }
         if (p.level_schur == o.level) {
-            LQ_TRY(pf_schur(h, P, phi2, p.kappa, -o.dt, c, nullptr, ss));
+            LQ_TRY(pf_schur(h, P, pf.phi2, p.kappa, -o.dt, c, nullptr, ss));
+            ++*nforce;
+        }
+        if (p.level_w2 == o.level) {
+            LQ_TRY(pf_w2(h, P, pf.phi3, p.kappa, -o.dt, c, nullptr, ss));
+            ++*nforce;
+        }
+        if (p.level_schur2 == o.level) {
+            LQ_TRY(pf_schur2(h, P, pf.phi4, p.kappa, -o.dt, c, nullptr, ss));
             ++*nforce;
         }
     }
@@ -306,14 +421,20 @@ void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1)
     }
 }
 
-// the (up to) four energy terms: kinetic, gauge, W1, Schur -> red_out[base..base+3]
-int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const double2* phi1, const double* phi2, int base)
+// the (up to) six energy terms: kinetic, gauge, W1, Schur, W2, Schur2 ->
+// red_out[base..base+5]
+constexpr int NTERM = 6;
+
+int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, int base)
 {
     SolveCfg c{p.precision, p.tol, p.max_iter};
-    LQ_TRY(kinetic_sum(h, h->P, h->red_out + base));
-    if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, h->red_out + base + 1));
-    if (p.level_w1 >= 0) LQ_TRY(pf_w1(h, nullptr, phi1, p.kappa, 0.0, c, h->red_out + base + 2));
-    if (p.level_schur >= 0) LQ_TRY(pf_schur(h, nullptr, phi2, p.kappa, 0.0, c, h->red_out + base + 3));
+    double* e = h->red_out + base;
+    LQ_TRY(kinetic_sum(h, h->P, e));
+    if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, e + 1));
+    if (p.level_w1 >= 0) LQ_TRY(pf_w1(h, nullptr, pf.phi1, p.kappa, 0.0, c, e + 2));
+    if (p.level_schur >= 0) LQ_TRY(pf_schur(h, nullptr, pf.phi2, p.kappa, 0.0, c, e + 3));
+    if (p.level_w2 >= 0) LQ_TRY(pf_w2(h, nullptr, pf.phi3, p.kappa, 0.0, c, e + 4));
+    if (p.level_schur2 >= 0) LQ_TRY(pf_schur2(h, nullptr, pf.phi4, p.kappa, 0.0, c, e + 5));
     return LQCD_OK;
 }
 
@@ -323,6 +444,8 @@ double combine(const lqcd_hmc_params& p, const double* e)
     if (p.level_gauge >= 0) H += -p.beta / 3.0 * e[1];
     if (p.level_w1 >= 0) H += e[2];
     if (p.level_schur >= 0) H += e[3];
+    if (p.level_w2 >= 0) H += e[4];
+    if (p.level_schur2 >= 0) H += e[5];
     return H;
 }
 
@@ -447,6 +570,8 @@ int lqcd_create(lqcd_t* out, const int L[4], int l0, int bc_t, void* stream)
     g.nb = L[0] / l0;
     g.bc_t = bc_t;
     g.Sh = l0 * g.V3 / 2;
+    g.l0s = 0;
+    h->g1 = g;
     h->stream = (cudaStream_t)stream;
     *out = h;
     if (cudaGetDevice(&h->device) != cudaSuccess ||
@@ -507,6 +632,18 @@ int lqcd_set_stream(lqcd_t h, void* stream)
 {
     CHECK_H(h);
     h->stream = (cudaStream_t)stream;
+    return LQCD_OK;
+}
+
+int lqcd_set_subslabs(lqcd_t h, int l0s)
+{
+    CHECK_H(h);
+    if (l0s != 0 && (h->g1.l0 % 2 || l0s * 2 != h->g1.l0)) {
+        h->err = "sub-slab thickness must be l0 / 2 (l0 even), or 0";
+        return LQCD_ERR_GEOM;
+    }
+    h->g1.l0s = l0s;
+    h->g = h->g1;
     return LQCD_OK;
 }
 
@@ -577,13 +714,12 @@ int lqcd_dslash_eo(lqcd_t h, double* out, const double* in, double kappa, int pa
     return unpack_spinor(h, out, B, parity, 1);
 }
 
-int lqcd_block_dslash(lqcd_t h, double* out, const double* in, double kappa, int colour, int dagger, int precision)
+}  // extern "C"
+
+// W1 (level-1 geometry) or W2 (inside a GeoScope on the sub-slab geometry)
+static int block_dslash_impl(lqcd_t h, double* out, const double* in, double kappa, int colour, int dagger,
+                             int precision)
 {
-    CHECK_H(h);
-    NEED_GAUGE(h);
-    NEED(out && in, "null field pointer");
-    NEED(colour >= -1 && colour <= 1, "colour must be -1, 0 or 1");
-    NEED(prec_ok(precision), "bad precision");
     const int Vh = h->g.Vh;
     double2 *A = fld(h, F_A), *B = fld(h, F_B);
     LQ_TRY(pack_spinor(h, A, in, 0, 2));
@@ -608,14 +744,9 @@ int lqcd_block_dslash(lqcd_t h, double* out, const double* in, double kappa, int
     return unpack_spinor(h, out, B, 0, 2);
 }
 
-int lqcd_block_solve_batched(lqcd_t h, double* x, const double* b, double kappa, int colour, int dagger,
-                             int precision, double tol, int max_iter, int* iters_out, double* resid_out)
+static int block_solve_impl(lqcd_t h, double* x, const double* b, double kappa, int colour, int dagger,
+                            int precision, double tol, int max_iter, int* iters_out, double* resid_out)
 {
-    CHECK_H(h);
-    NEED_GAUGE(h);
-    NEED(x && b, "null field pointer");
-    NEED(colour >= -1 && colour <= 1, "colour must be -1, 0 or 1");
-    NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
     double2 *A = fld(h, F_A), *B = fld(h, F_B);
     LQ_TRY(pack_spinor(h, A, b, 0, 2));
     const int nsys = colour < 0 ? h->g.nb : h->g.nb / 2;
@@ -636,6 +767,61 @@ int lqcd_block_solve_batched(lqcd_t h, double* x, const double* b, double kappa,
     LQ_TRY(unpack_spinor(h, x, B, 0, 2));
     LQ_CUDA(h, cudaStreamSynchronize(h->stream));
     return LQCD_OK;
+}
+
+extern "C" {
+
+int lqcd_block_dslash(lqcd_t h, double* out, const double* in, double kappa, int colour, int dagger, int precision)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(out && in, "null field pointer");
+    NEED(colour >= -1 && colour <= 1, "colour must be -1, 0 or 1");
+    NEED(prec_ok(precision), "bad precision");
+    return block_dslash_impl(h, out, in, kappa, colour, dagger, precision);
+}
+
+int lqcd_subblock_dslash(lqcd_t h, double* out, const double* in, double kappa, int colour, int dagger,
+                         int precision)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(out && in, "null field pointer");
+    NEED(colour >= -1 && colour <= 1, "colour must be -1, 0 or 1");
+    NEED(prec_ok(precision), "bad precision");
+    if (!h->g1.l0s) {
+        h->err = "no sub-slabs (lqcd_set_subslabs)";
+        return LQCD_ERR_STATE;
+    }
+    GeoScope sc(h, sub_geo(h->g1));
+    return block_dslash_impl(h, out, in, kappa, colour, dagger, precision);
+}
+
+int lqcd_block_solve_batched(lqcd_t h, double* x, const double* b, double kappa, int colour, int dagger,
+                             int precision, double tol, int max_iter, int* iters_out, double* resid_out)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(x && b, "null field pointer");
+    NEED(colour >= -1 && colour <= 1, "colour must be -1, 0 or 1");
+    NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
+    return block_solve_impl(h, x, b, kappa, colour, dagger, precision, tol, max_iter, iters_out, resid_out);
+}
+
+int lqcd_subblock_solve_batched(lqcd_t h, double* x, const double* b, double kappa, int colour, int dagger,
+                                int precision, double tol, int max_iter, int* iters_out, double* resid_out)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(x && b, "null field pointer");
+    NEED(colour >= -1 && colour <= 1, "colour must be -1, 0 or 1");
+    NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
+    if (!h->g1.l0s) {
+        h->err = "no sub-slabs (lqcd_set_subslabs)";
+        return LQCD_ERR_STATE;
+    }
+    GeoScope sc(h, sub_geo(h->g1));
+    return block_solve_impl(h, x, b, kappa, colour, dagger, precision, tol, max_iter, iters_out, resid_out);
 }
 
 int lqcd_solve_wilson(lqcd_t h, double* x, const double* b, double kappa, int dagger, int precision, double tol,
@@ -663,10 +849,18 @@ int lqcd_schur_apply(lqcd_t h, double* out, const double* in, double kappa, int 
     CHECK_H(h);
     NEED_GAUGE(h);
     NEED(out && in && out != in, "null or aliased boundary pointer");
-    NEED(op >= LQCD_SCHUR_R && op <= LQCD_SCHUR_RINVDAG, "bad Schur op");
+    NEED(op >= LQCD_SCHUR_R && op <= LQCD_SCHUR2_RINVDAG, "bad Schur op");
     NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
     SolveCfg c{precision, tol, max_iter};
-    LQ_TRY(schur_op(h, out, in, kappa, op, c));
+    if (op >= LQCD_SCHUR2_R) {
+        if (!h->g1.l0s) {
+            h->err = "no sub-slabs (lqcd_set_subslabs)";
+            return LQCD_ERR_STATE;
+        }
+        LQ_TRY(schur2_op(h, out, in, kappa, op - LQCD_SCHUR2_R, c));
+    } else {
+        LQ_TRY(schur_op(h, out, in, kappa, op, c));
+    }
     LQ_CUDA(h, cudaStreamSynchronize(h->stream));
     return LQCD_OK;
 }
@@ -677,14 +871,23 @@ int lqcd_pf_force(lqcd_t h, double* F, const double* phi, double kappa, int term
     CHECK_H(h);
     NEED_GAUGE(h);
     NEED(phi, "null phi");
-    NEED(term == LQCD_TERM_W1 || term == LQCD_TERM_SCHUR, "bad term");
+    NEED(term >= LQCD_TERM_W1 && term <= LQCD_TERM_SCHUR2, "bad term");
     NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
+    if (term >= LQCD_TERM_W2 && !h->g1.l0s) {
+        h->err = "no sub-slabs (lqcd_set_subslabs)";
+        return LQCD_ERR_STATE;
+    }
     SolveCfg c{precision, tol, max_iter};
     if (term == LQCD_TERM_W1) {
         LQ_TRY(pack_spinor(h, fld(h, F_PHI1), phi, 0, 2));
         LQ_TRY(pf_w1(h, F, fld(h, F_PHI1), kappa, 1.0, c, h->red_out));
-    } else {
+    } else if (term == LQCD_TERM_SCHUR) {
         LQ_TRY(pf_schur(h, F, phi, kappa, 1.0, c, h->red_out));
+    } else if (term == LQCD_TERM_W2) {
+        LQ_TRY(pack_spinor(h, fld(h, F_PHI3), phi, 0, 2));
+        LQ_TRY(pf_w2(h, F, fld(h, F_PHI3), kappa, 1.0, c, h->red_out));
+    } else {
+        LQ_TRY(pf_schur2(h, F, phi, kappa, 1.0, c, h->red_out));
     }
     double S;
     LQ_TRY(read_scalars(h, 1, &S));
@@ -713,21 +916,29 @@ int lqcd_rng_normals(lqcd_t h, double* out, int64_t n, uint64_t seed, uint32_t s
     return rng_normals(h, out, n, seed, stream, traj, 1.0);
 }
 
-int lqcd_md(lqcd_t h, double* U, double* P, const double* phi1, const double* phi2, const lqcd_hmc_params* prm)
+int lqcd_md(lqcd_t h, double* U, double* P, const double* phi1, const double* phi2, const double* phi3,
+            const double* phi4, const lqcd_hmc_params* prm)
 {
     CHECK_H(h);
     NEED(U && P, "null U / P");
     LQ_TRY(check_params(h, prm));
     NEED(prm->level_w1 < 0 || phi1, "phi1 needed for the W1 term");
     NEED(prm->level_schur < 0 || phi2, "phi2 needed for the Schur term");
+    NEED(prm->level_w2 < 0 || phi3, "phi3 needed for the W2 term");
+    NEED(prm->level_schur2 < 0 || phi4, "phi4 needed for the second-level Schur term");
     LQ_TRY(pack_gauge(h, U));
     h->have_gauge = true;
     if (prm->level_w1 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI1), phi1, 0, 2));
     if (prm->level_schur >= 0)
         LQ_CUDA(h, cudaMemcpyAsync(h->bnd[0], phi2, sizeof(double) * 2 * nbnd_of(h->g), cudaMemcpyDeviceToDevice,
                                    h->stream));
+    if (prm->level_w2 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI3), phi3, 0, 2));
+    if (prm->level_schur2 >= 0)
+        LQ_CUDA(h, cudaMemcpyAsync(h->bnd[3], phi4, sizeof(double) * 2 * nbnd2_of(h->g1),
+                                   cudaMemcpyDeviceToDevice, h->stream));
     int nf = 0;
-    LQ_TRY(do_md(h, *prm, P, fld(h, F_PHI1), h->bnd[0], &nf));
+    const PfFields pf{fld(h, F_PHI1), h->bnd[0], fld(h, F_PHI3), h->bnd[3]};
+    LQ_TRY(do_md(h, *prm, P, pf, &nf));
     LQ_TRY(unpack_gauge(h, U));
     LQ_CUDA(h, cudaStreamSynchronize(h->stream));
     return LQCD_OK;
@@ -755,7 +966,7 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
     else
         LQ_TRY(rng_normals(h, h->P, (int64_t)32 * g.V, seed, 1, traj, 1.0));
     SolveCfg c{p.precision, p.tol, p.max_iter};
-    double* e0 = h->red_out;  // [0..3] H0 terms, [4..7] H1 terms
+    double* e0 = h->red_out;  // [0..5] H0 terms, [6..11] H1 terms, [12] plaquette
     LQ_CUDA(h, cudaMemsetAsync(h->red_out, 0, sizeof(double) * 16, h->stream));
     LQ_TRY(kinetic_sum(h, h->P, e0));
     if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, e0 + 1));
@@ -784,12 +995,28 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
             LQ_TRY(pf_schur(h, nullptr, h->bnd[0], p.kappa, 0.0, c, e0 + 3));
         }
     }
+    // second level (iterated decomposition): phi3 = W2 eta3, phi4 = R2 eta4
+    // (Philox streams 5 and 6)
+    if (p.level_w2 >= 0) {
+        double2* et = fld(h, F_ETA1);
+        LQ_TRY(rng_spinor(h, et, seed, 5, traj));
+        LQ_TRY(sub_hop(h, 0, -1, fld(h, F_PHI3), et, 1.0, et, -p.kappa));
+        LQ_TRY(norm2_dev(h, (const double*)et, (int64_t)48 * g.Vh, e0 + 4));
+    }
+    if (p.level_schur2 >= 0) {
+        const int nbd2 = 2 * nbnd2_of(h->g1);
+        double* e4 = h->bnd[2];
+        LQ_TRY(rng_normals(h, e4, nbd2, seed, 6, traj, sqrt(0.5)));
+        LQ_TRY(schur2_op(h, h->bnd[3], e4, p.kappa, LQCD_SCHUR_R, c));
+        LQ_TRY(norm2_dev(h, e4, nbd2, e0 + 5));
+    }
     int nforce = 0;
-    LQ_TRY(do_md(h, p, h->P, fld(h, F_PHI1), h->bnd[0], &nforce));
-    LQ_TRY(energy(h, p, fld(h, F_PHI1), h->bnd[0], 4));
-    double e[8];
-    LQ_TRY(read_scalars(h, 8, e));
-    const double H0 = combine(p, e), H1 = combine(p, e + 4);
+    const PfFields pf{fld(h, F_PHI1), h->bnd[0], fld(h, F_PHI3), h->bnd[3]};
+    LQ_TRY(do_md(h, p, h->P, pf, &nforce));
+    LQ_TRY(energy(h, p, pf, NTERM));
+    double e[2 * NTERM];
+    LQ_TRY(read_scalars(h, 2 * NTERM, e));
+    const double H0 = combine(p, e), H1 = combine(p, e + NTERM);
     const double dH = H1 - H0;
     if (!isfinite(dH)) {
         h->err = "non-finite energy";
@@ -812,10 +1039,11 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
                                    h->stream));
         LQ_TRY(roll_links(h, shift));
     }
-    LQ_TRY(plaquette_sum(h, h->red_out + 8));
+    LQ_TRY(plaquette_sum(h, h->red_out + 2 * NTERM));
     LQ_TRY(unpack_gauge(h, U));
     double pl;
-    LQ_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out + 8, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LQ_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out + 2 * NTERM, sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
     LQ_CUDA(h, cudaStreamSynchronize(h->stream));
     pl = h->red_host[0];
     res->dH = dH;

@@ -30,8 +30,22 @@ struct Geo {
     int L[4];
     int V, Vh, V3;
     int l0, nb, bc_t;
-    int Sh;  // sites of one parity in one slab = l0 * V3 / 2
+    int Sh;   // sites of one parity in one slab = l0 * V3 / 2
+    int l0s;  // iterated decomposition: sub-slab thickness l0 / 2, or 0
 };
+
+// Geometry of the second level of the iterated decomposition (Sec. 1): the
+// sub-slabs of thickness l0s play the part of the slabs, so every block
+// kernel run on it works on W2 instead of W1.
+inline Geo sub_geo(const Geo& g)
+{
+    Geo s = g;
+    s.l0 = g.l0s;
+    s.nb = g.L[0] / g.l0s;
+    s.Sh = g.l0s * g.V3 / 2;
+    s.l0s = 0;
+    return s;
+}
 
 // coordinates of eo index i of parity p
 LQ_HD void eo_coords(const Geo& g, int p, int i, int x[4])
@@ -365,9 +379,24 @@ __device__ __forceinline__ void load_link<PREC16>(const GaugeF& g, int mu, int p
 //   mode 0: all hops (x0 wrap carries bc_t)
 //   mode 1: hops inside one slab only (W1)
 //   mode 2: hops between different slabs only (blocks B, C of M)
+//   mode 3: hops inside one sub-slab only (W2; needs g.l0s)
+//   mode 4: hops between the two sub-slabs of one slab (blocks B2, C2 of W1)
 // dag = 1 gives H^dag (projectors swapped).  acc is overwritten.
 // ---------------------------------------------------------------------------
-enum { MODE_ALL = 0, MODE_INTRA = 1, MODE_CROSS = 2 };
+enum { MODE_ALL = 0, MODE_INTRA = 1, MODE_CROSS = 2, MODE_INTRA2 = 3, MODE_CROSS2 = 4 };
+
+// is a time-like hop across the face between slices xf-1 and xf (mod L0)
+// kept in `mode`?  (space-like hops: kept unless mode is 2 or 4)
+LQ_HD bool t_hop_kept(const Geo& g, int mode, int xf)
+{
+    if (mode == MODE_ALL) return true;
+    const bool slab_face = (xf % g.l0) == 0;
+    if (mode == MODE_INTRA) return !slab_face;
+    if (mode == MODE_CROSS) return slab_face;
+    const bool sub_face = g.l0s > 0 && (xf % g.l0s) == 0;
+    if (mode == MODE_INTRA2) return !sub_face;
+    return sub_face && !slab_face;
+}
 
 // ld(j, spinor) provides the input spinor at eo index j of parity 1-pout
 template <int P, class Loader>
@@ -405,12 +434,8 @@ __device__ __forceinline__ void hop_site_ld(const Geo& g, int mode, int dag, int
             bool wrap = (x[mu] == g.L[mu] - 1);
             if (wrap) nl -= g.L[mu] * stride;
             bool use = true;
-            if (mu == 0 && mode != MODE_ALL) {
-                bool cross = ((x[0] + 1) % g.l0) == 0;
-                use = (mode == MODE_INTRA) ? !cross : cross;
-            } else if (mu != 0 && mode == MODE_CROSS) {
-                use = false;
-            }
+            if (mu == 0) use = t_hop_kept(g, mode, x[0] + 1);
+            else if (mode == MODE_CROSS || mode == MODE_CROSS2) use = false;
             if (use) {
                 Spinor<T> ps;
                 ld(nl >> 1, ps);
@@ -435,12 +460,8 @@ __device__ __forceinline__ void hop_site_ld(const Geo& g, int mode, int dag, int
             bool wrap = (x[mu] == 0);
             if (wrap) nl += g.L[mu] * stride;
             bool use = true;
-            if (mu == 0 && mode != MODE_ALL) {
-                bool cross = (x[0] % g.l0) == 0;
-                use = (mode == MODE_INTRA) ? !cross : cross;
-            } else if (mu != 0 && mode == MODE_CROSS) {
-                use = false;
-            }
+            if (mu == 0) use = t_hop_kept(g, mode, x[0]);
+            else if (mode == MODE_CROSS || mode == MODE_CROSS2) use = false;
             if (use) {
                 Spinor<T> ps;
                 ld(nl >> 1, ps);
@@ -483,7 +504,8 @@ struct Profiler {
 struct Work;  // solver workspace (lqcd_solver.cu)
 
 struct lqcd_ctx {
-    Geo g;
+    Geo g;   // active geometry (level 1, or level 2 inside a GeoScope)
+    Geo g1;  // level 1: slabs of thickness l0 (g1.l0s: sub-slabs, or 0)
     cudaStream_t stream;
     int device;
     int num_sms;
@@ -513,6 +535,14 @@ struct lqcd_ctx {
     int64_t iter_count = 0;  // inner iterations since reset (trajectory stats)
     int64_t site_iters = 0;  // inner iterations x even sites of the system
     int solve_count = 0;
+};
+
+// switches the handle to another geometry for the lifetime of the scope
+struct GeoScope {
+    lqcd_ctx* h;
+    Geo saved;
+    GeoScope(lqcd_ctx* hh, const Geo& g) : h(hh), saved(hh->g) { h->g = g; }
+    ~GeoScope() { h->g = saved; }
 };
 
 // error helpers
@@ -556,8 +586,10 @@ int pack_gauge(lqcd_ctx* h, const double* abi);
 int unpack_gauge(lqcd_ctx* h, double* abi);
 int convert_spinor(lqcd_ctx* h, SpinorF dst, int dprec, SpinorF src, int sprec, int n);
 int index_maps(lqcd_ctx* h, int32_t* maps);
-int embed_boundary(lqcd_ctx* h, double2* full, const double* coords);
-int project_boundary(lqcd_ctx* h, double* coords, const double2* full);
+// boundary space of the active geometry; nface = 2: both faces of every
+// black slab (level 1), nface = 1: first slice only (level 2)
+int embed_boundary(lqcd_ctx* h, double2* full, const double* coords, int nface = 2);
+int project_boundary(lqcd_ctx* h, double* coords, const double2* full, int nface = 2);
 int axpby_full(lqcd_ctx* h, double2* y, double a, const double2* x, double b, int colour);
 int gamma5_full(lqcd_ctx* h, double2* y, const double2* x);
 int keep_colour(lqcd_ctx* h, double2* y, int colour);

@@ -163,8 +163,9 @@ __device__ void face_site(const Geo& g, int j, int f, int lex3, int& par, int& i
     i = lex_of(g, x) >> 1;
 }
 
-// one thread per (j, lex3); both faces (they coincide for l0 = 1)
-__global__ void k_embed(double2* full, const double2* coords, Geo g)
+// one thread per (j, lex3); both faces (they coincide for l0 = 1), or only
+// face 0 when nface = 1 (second level: coords [nb/2][V3][2][3])
+__global__ void k_embed(double2* full, const double2* coords, Geo g, int nface)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nj = g.nb / 2;
@@ -173,9 +174,9 @@ __global__ void k_embed(double2* full, const double2* coords, Geo g)
     const double r = 0.70710678118654752440;
     double2 out[2][12];
     int par[2], idx[2];
-    for (int f = 0; f < 2; ++f) {
+    for (int f = 0; f < nface; ++f) {
         face_site(g, j, f, l3, par[f], idx[f]);
-        const double2* c = coords + ((size_t)(j * 2 + f) * g.V3 + l3) * 6;
+        const double2* c = coords + ((size_t)(j * nface + f) * g.V3 + l3) * 6;
         const double sgn = f ? 1.0 : -1.0;
         for (int s = 0; s < 2; ++s)
             for (int col = 0; col < 3; ++col) {
@@ -184,25 +185,25 @@ __global__ void k_embed(double2* full, const double2* coords, Geo g)
                 out[f][(s + 2) * 3 + col] = make_double2(sgn * r * v.x, sgn * r * v.y);
             }
     }
-    if (g.l0 == 1) {
+    if (g.l0 == 1 && nface == 2) {
         double2* d = full + (size_t)par[0] * 12 * g.Vh;
         for (int c = 0; c < 12; ++c)
             d[(size_t)c * g.Vh + idx[0]] = make_double2(out[0][c].x + out[1][c].x, out[0][c].y + out[1][c].y);
     } else {
-        for (int f = 0; f < 2; ++f) {
+        for (int f = 0; f < nface; ++f) {
             double2* d = full + (size_t)par[f] * 12 * g.Vh;
             for (int c = 0; c < 12; ++c) d[(size_t)c * g.Vh + idx[f]] = out[f][c];
         }
     }
 }
 
-__global__ void k_project(double2* coords, const double2* full, Geo g)
+__global__ void k_project(double2* coords, const double2* full, Geo g, int nface)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nj = g.nb / 2;
-    if (t >= nj * 2 * g.V3) return;
+    if (t >= nj * nface * g.V3) return;
     const int jf = t / g.V3, l3 = t % g.V3;
-    const int j = jf / 2, f = jf % 2;
+    const int j = jf / nface, f = jf % nface;
     int par, i;
     face_site(g, j, f, l3, par, i);
     const double2* s = full + (size_t)par * 12 * g.Vh;
@@ -428,17 +429,17 @@ int index_maps(lqcd_ctx* h, int32_t* maps)
     return LQCD_OK;
 }
 
-int embed_boundary(lqcd_ctx* h, double2* full, const double* coords)
+int embed_boundary(lqcd_ctx* h, double2* full, const double* coords, int nface)
 {
     LQ_CUDA(h, cudaMemsetAsync(full, 0, sizeof(double2) * 24 * (size_t)h->g.Vh, h->stream));
-    k_embed<<<nblk((h->g.nb / 2) * h->g.V3), BS, 0, h->stream>>>(full, (const double2*)coords, h->g);
+    k_embed<<<nblk((h->g.nb / 2) * h->g.V3), BS, 0, h->stream>>>(full, (const double2*)coords, h->g, nface);
     LAUNCH_CHECK(h);
     return LQCD_OK;
 }
 
-int project_boundary(lqcd_ctx* h, double* coords, const double2* full)
+int project_boundary(lqcd_ctx* h, double* coords, const double2* full, int nface)
 {
-    k_project<<<nblk((h->g.nb / 2) * 2 * h->g.V3), BS, 0, h->stream>>>((double2*)coords, full, h->g);
+    k_project<<<nblk((h->g.nb / 2) * nface * h->g.V3), BS, 0, h->stream>>>((double2*)coords, full, h->g, nface);
     LAUNCH_CHECK(h);
     return LQCD_OK;
 }

@@ -100,7 +100,7 @@ __device__ __forceinline__ void bilinear_link(const Geo& g, const GaugeF& U, con
                                               int i, const int x[4], double f[8])
 {
     typedef typename Real<PL>::T R;
-    if (mu == 0 && T.mask == MODE_INTRA && ((x[0] + 1) % g.l0) == 0) return;
+    if (mu == 0 ? !t_hop_kept(g, T.mask, x[0] + 1) : (T.mask == MODE_CROSS || T.mask == MODE_CROSS2)) return;
     const bool wrap = (x[mu] == g.L[mu] - 1);
     int y[4], py, iy;
     shifted(g, x, mu, +1, y);

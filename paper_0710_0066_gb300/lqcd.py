@@ -22,7 +22,8 @@ OK, ERR_ARG, ERR_GEOM, ERR_NOCONVERGE, ERR_CUDA, ERR_NAN, ERR_TIMEOUT, ERR_STATE
 PREC_F64, PREC_F32, PREC_F16 = 0, 1, 2
 OP_HOP, OP_MHAT = 0, 1
 SCHUR_R, SCHUR_RDAG, SCHUR_RINV, SCHUR_RINVDAG = 0, 1, 2, 3
-TERM_W1, TERM_SCHUR = 0, 1
+SCHUR2_R, SCHUR2_RDAG, SCHUR2_RINV, SCHUR2_RINVDAG = 4, 5, 6, 7
+TERM_W1, TERM_SCHUR, TERM_W2, TERM_SCHUR2 = 0, 1, 2, 3
 LF, SW = 0, 1
 KERNEL_HOP, KERNEL_SOLVER, KERNEL_FORCE, KERNEL_GAUGE, KERNEL_BLAS = 0, 1, 2, 3, 4
 
@@ -32,7 +33,8 @@ EXPORTS = [
     "lqcd_block_solve_batched", "lqcd_solve_wilson", "lqcd_schur_apply", "lqcd_pf_force",
     "lqcd_gauge_force", "lqcd_rng_normals", "lqcd_hmc_trajectory", "lqcd_md",
     "lqcd_profile_enable", "lqcd_profile_reset", "lqcd_profile_read", "lqcd_launch_count",
-    "lqcd_gauge_action_static", "lqcd_force_profile",
+    "lqcd_gauge_action_static", "lqcd_force_profile", "lqcd_set_subslabs", "lqcd_subblock_dslash",
+    "lqcd_subblock_solve_batched",
 ]
 
 
@@ -43,6 +45,7 @@ class HmcParams(C.Structure):
         ("level_gauge", C.c_int), ("level_w1", C.c_int), ("level_schur", C.c_int),
         ("pf_init", C.c_int), ("roll", C.c_int), ("metropolis", C.c_int), ("precision", C.c_int),
         ("tol", C.c_double), ("max_iter", C.c_int), ("step_scheme", C.c_int), ("step_scale", C.c_void_p),
+        ("level_w2", C.c_int), ("level_schur2", C.c_int),
     ]
 
 
@@ -57,14 +60,14 @@ class HmcResult(C.Structure):
 
 def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w1=0, level_schur=0,
                lam=1.0 / 6.0, pf_init=0, roll=0, metropolis=1, precision=PREC_F64, tol=1e-10,
-               max_iter=20000, step_scheme=0, step_scale=None):
+               max_iter=20000, step_scheme=0, step_scale=None, level_w2=-1, level_schur2=-1):
     """step_scale: None or a host float64 array (2, L0) of s(x0) (space-like,
     time-like rows); it is kept alive on the returned object"""
     sc = list(scheme) + [0] * (4 - len(scheme))
     ns = list(nsteps) + [1] * (4 - len(nsteps))
     p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * 4)(*sc), (C.c_int * 4)(*ns),
                   level_gauge, level_w1, level_schur, pf_init, roll, metropolis, precision, tol,
-                  max_iter, step_scheme, None)
+                  max_iter, step_scheme, None, level_w2, level_schur2)
     if step_scale is not None:
         import numpy as np
 
@@ -102,7 +105,10 @@ def load():
         "lqcd_gauge_force": [vp, vp, d, vp, vp],
         "lqcd_rng_normals": [vp, vp, i64, u64, u32, u32],
         "lqcd_hmc_trajectory": [vp, vp, vp, u64, u32, vp, vp, vp, vp],
-        "lqcd_md": [vp, vp, vp, vp, vp, vp],
+        "lqcd_md": [vp, vp, vp, vp, vp, vp, vp, vp],
+        "lqcd_set_subslabs": [vp, i],
+        "lqcd_subblock_dslash": [vp, vp, vp, d, i, i, i],
+        "lqcd_subblock_solve_batched": [vp, vp, vp, d, i, i, i, d, i, vp, vp],
         "lqcd_profile_enable": [vp, i],
         "lqcd_profile_reset": [vp],
         "lqcd_profile_read": [vp, i, vp, vp, vp],
@@ -202,6 +208,26 @@ def lqcd_block_solve_batched(h, x, b, kappa, colour=-1, dagger=0, precision=PREC
     return list(it), list(rs)
 
 
+def lqcd_set_subslabs(h, l0s):
+    return _check(h, load().lqcd_set_subslabs(h, int(l0s)))
+
+
+def lqcd_subblock_dslash(h, out, inp, kappa, colour=-1, dagger=0, precision=PREC_F64):
+    return _check(h, load().lqcd_subblock_dslash(h, _ptr(out), _ptr(inp), float(kappa), int(colour),
+                                                 int(dagger), int(precision)))
+
+
+def lqcd_subblock_solve_batched(h, x, b, kappa, colour=-1, dagger=0, precision=PREC_F64, tol=1e-10,
+                                max_iter=10000, nbs=None):
+    n = nbs or 128
+    it = (C.c_int * n)()
+    rs = (C.c_double * n)()
+    _check(h, load().lqcd_subblock_solve_batched(h, _ptr(x), _ptr(b), float(kappa), int(colour),
+                                                 int(dagger), int(precision), float(tol), int(max_iter),
+                                                 it, rs))
+    return list(it), list(rs)
+
+
 def lqcd_solve_wilson(h, x, b, kappa, dagger=0, precision=PREC_F64, tol=1e-10, max_iter=20000):
     it = C.c_int(0)
     rs = C.c_double(0)
@@ -242,8 +268,9 @@ def lqcd_hmc_trajectory(h, U, prm, seed, traj, P0=None, eta1=None, eta2=None):
     return res
 
 
-def lqcd_md(h, U, P, phi1, phi2, prm):
-    return _check(h, load().lqcd_md(h, _ptr(U), _ptr(P), _ptr(phi1), _ptr(phi2), C.byref(prm)))
+def lqcd_md(h, U, P, phi1, phi2, prm, phi3=None, phi4=None):
+    return _check(h, load().lqcd_md(h, _ptr(U), _ptr(P), _ptr(phi1), _ptr(phi2), _ptr(phi3), _ptr(phi4),
+                                    C.byref(prm)))
 
 
 def lqcd_profile_enable(h, on):
@@ -284,17 +311,22 @@ def lqcd_profile_read(h, kernel_id):
 # convenience wrapper
 # ---------------------------------------------------------------------------
 class Lattice:
-    """A handle on one lattice: L = (L0, L1, L2, L3), x0-slabs of thickness l0."""
+    """A handle on one lattice: L = (L0, L1, L2, L3), x0-slabs of thickness l0
+    and, with l0s = l0/2, the sub-slabs of the iterated decomposition."""
 
-    def __init__(self, L, l0, bc_t=-1, stream=None):
+    def __init__(self, L, l0, bc_t=-1, stream=None, l0s=0):
         self.L = tuple(int(v) for v in L)
         self.l0 = int(l0)
+        self.l0s = int(l0s)
         self.V3 = self.L[1] * self.L[2] * self.L[3]
         self.V = self.L[0] * self.V3
         self.Vh = self.V // 2
         self.nb = self.L[0] // self.l0
+        self.nbs = self.L[0] // self.l0s if self.l0s else 0
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.h = lqcd_create(self.L, self.l0, bc_t, stream)
+        if self.l0s:
+            lqcd_set_subslabs(self.h, self.l0s)
 
     def close(self):
         if self.h is not None:
@@ -315,6 +347,9 @@ class Lattice:
 
     def boundary(self):
         return torch.zeros((self.nb // 2, 2, self.V3, 2, 3), dtype=torch.complex128, device=self.dev)
+
+    def boundary2(self):
+        return torch.zeros((self.nbs // 2, self.V3, 2, 3), dtype=torch.complex128, device=self.dev)
 
     def momenta(self):
         return torch.zeros((4, self.V, 8), dtype=torch.float64, device=self.dev)
@@ -348,13 +383,24 @@ class Lattice:
                                           tol, max_iter, nb=self.nb)
         return x, it, rs
 
+    def subblock_dslash(self, x, kappa, colour=-1, dagger=0, precision=PREC_F64):
+        out = self.spinor()
+        lqcd_subblock_dslash(self.h, out, x.contiguous(), kappa, colour, dagger, precision)
+        return out
+
+    def subblock_solve(self, b, kappa, colour=-1, dagger=0, precision=PREC_F64, tol=1e-10, max_iter=10000):
+        x = self.spinor()
+        it, rs = lqcd_subblock_solve_batched(self.h, x, b.contiguous(), kappa, colour, dagger, precision,
+                                             tol, max_iter, nbs=self.nbs)
+        return x, it, rs
+
     def solve(self, b, kappa, dagger=0, precision=PREC_F64, tol=1e-10, max_iter=20000):
         x = self.spinor()
         it, rs = lqcd_solve_wilson(self.h, x, b.contiguous(), kappa, dagger, precision, tol, max_iter)
         return x, it, rs
 
     def schur(self, c, kappa, op=SCHUR_R, precision=PREC_F64, tol=1e-10, max_iter=20000):
-        out = self.boundary()
+        out = self.boundary2() if op >= SCHUR2_R else self.boundary()
         lqcd_schur_apply(self.h, out, c.contiguous(), kappa, op, precision, tol, max_iter)
         return out
 
@@ -379,8 +425,8 @@ class Lattice:
         res = lqcd_hmc_trajectory(self.h, U2, prm, seed, traj, P0, eta1, eta2)
         return U2, res
 
-    def md(self, U, P, phi1, phi2, prm):
+    def md(self, U, P, phi1, phi2, prm, phi3=None, phi4=None):
         U2 = U.clone().contiguous()
         P2 = P.clone().contiguous()
-        lqcd_md(self.h, U2, P2, phi1, phi2, prm)
+        lqcd_md(self.h, U2, P2, phi1, phi2, prm, phi3, phi4)
         return U2, P2
