@@ -370,6 +370,100 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# the iterated decomposition at 32^3 x 64: slabs l0 = 8 split into sub-slabs
+# of thickness 4, action S_G + |R^-1 phi2|^2 + |R2^-1 phi4|^2 + |W2^-1 phi3|^2
+# on four time scales (gauge / W2 / R2 / R), Omelyan on every level
+WL_ITER = dict(L=(64, 32, 32, 32), l0=8, l0s=4, kappa=0.158, beta=5.6, eps=0.6, seed=2010, tau=1.0,
+               nlevels=4, scheme=(1, 1, 1, 1), nsteps=(2, 2, 2, 6), lam=0.1931833275037836,
+               level_gauge=0, level_w2=1, level_schur2=2, level_schur=3, tol=1e-10, max_iter=20000, therm=40)
+
+
+def run_iterated(args):
+    """--case iterated: K trajectories of the four-part action at 32^3 x 64
+    in the mixed-precision form, the first input again in the plain double
+    form; one JSON line"""
+    import torch
+
+    from paper_0710_0066_gb300 import lqcd, synthetic as syn
+
+    torch.cuda.set_device(0)
+    W = WL_ITER
+    L = W["L"]
+    lat = lqcd.Lattice(L, W["l0"], -1, l0s=W["l0s"])
+    U0 = syn.random_links_torch(L, W["eps"], W["seed"], "cuda").contiguous()
+    U0, rth = thermalise(lat, U0, W["beta"], W["therm"], W["seed"])
+
+    def params(prec):
+        return lqcd.hmc_params(W["beta"], W["kappa"], W["tau"], W["nlevels"], W["scheme"], W["nsteps"],
+                               W["level_gauge"], -1, W["level_schur"], lam=W["lam"], roll=1, metropolis=1,
+                               precision=prec, tol=W["tol"], max_iter=W["max_iter"], level_w2=W["level_w2"],
+                               level_schur2=W["level_schur2"])
+
+    prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
+    prm = params(prec)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    U = U0.clone()
+    traj = 0
+    for _ in range(args.warmup):
+        U, res = lat.hmc_trajectory(U, prm, W["seed"], traj)
+        traj += 1
+    lqcd.lqcd_profile_reset(lat.h)
+    lqcd.lqcd_profile_enable(lat.h, 1 << lqcd.KERNEL_SOLVER)
+    clocks = Clocks(0)
+    clocks.start()
+    step_ms, results, U_in = [], [], []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        U_in.append((U.clone(), traj))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        U, res = lat.hmc_trajectory(U, prm, W["seed"], traj)
+        b.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        results.append(res)
+        traj += 1
+    clk = clocks.stop()
+    n_sol, ms_sol, by_sol = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
+    lqcd.lqcd_profile_enable(lat.h, 0)
+    fp64 = None
+    if not args.no_fp64 and prec != lqcd.PREC_F64:
+        Uk, tk = U_in[0]
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, r64 = lat.hmc_trajectory(Uk, params(lqcd.PREC_F64), W["seed"], tk)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        fp64 = {"s_per_traj": t64, "dH": r64.dH, "dH_mixed": results[0].dH,
+                "abs_dH_diff": abs(r64.dH - results[0].dH), "speedup_mixed_vs_fp64": t64 / (step_ms[0] / 1e3),
+                "accepted": r64.accepted}
+    peak, peak_kind = hbm_peak()
+    achieved = by_sol / ms_sol / 1e6 if ms_sol > 0 else None
+    line = {
+        "case": "iterated", "metric": "s/HMC trajectory (32^3x64, iterated slab decomposition)",
+        "value": sum(step_ms) / 1e3 / args.steps, "unit": "s/trajectory", "steps": args.steps,
+        "warmup": args.warmup, "precision": args.precision,
+        "config": {"lattice": "x".join(map(str, L)), "l0": W["l0"], "l0s": W["l0s"], "kappa": W["kappa"],
+                   "beta": W["beta"], "nsteps": W["nsteps"], "levels": "gauge/W2/R2/R",
+                   "thermalisation": "%d pure-gauge trajectories from exp(i %.1f H)" % (W["therm"], W["eps"]),
+                   "l2": "flushed between timed trajectories"},
+        "solver": {"achieved_gbs": achieved, "peak": peak, "peak_kind": peak_kind,
+                   "frac": (achieved / peak) if achieved else None, "launches": n_sol,
+                   "share_of_step": ms_sol / sum(step_ms)},
+        "trajectory": {"dH": [r.dH for r in results], "accepted": [r.accepted for r in results],
+                       "plaq": results[-1].plaq, "solver_iters": [r.solver_iters for r in results],
+                       "n_solves": results[-1].n_solves, "n_force": results[-1].n_force, "step_ms": step_ms},
+        "acceptance": sum(r.accepted for r in results) / len(results),
+        "fp64_form": fp64, "thermalisation_plaq": rth.plaq if rth else None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    lat.close()
+
+
 def run_case(args):
     """small single-kernel cases for profiler captures (a few GB on the device)"""
     import torch
@@ -380,6 +474,8 @@ def run_case(args):
     g = torch.Generator(device="cuda")
     g.manual_seed(WL["seed"])
     prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
+    if args.case == "iterated":
+        return run_iterated(args)
     if args.case == "solver":
         # the batched slab solve (8 slabs) and the global solve of the workload
         L, l0 = WL["L"], WL["l0"]
@@ -423,7 +519,7 @@ def run_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default=None, choices=["solver", "dslash"],
+    ap.add_argument("--case", default=None, choices=["solver", "dslash", "iterated"],
                     help="run one small kernel case instead of the benchmark (profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)

@@ -131,8 +131,8 @@ int lqcd_index_maps(lqcd_t h, int32_t* maps);
 int lqcd_dslash_eo(lqcd_t h, double* out, const double* in, double kappa, int parity,
                    int dagger, int op, int precision);
 
-/* W1: eq. (2) with every hop between different x0-slabs removed (Sec. 1,
- * "eliminating the hopping terms in M that connect different blocks"),
+/* W1: eq. (2) with every hop between different x0-slabs removed (Sec. 1:
+ * the block operator keeps only the hops inside one block),
  * applied on the slabs of one colour (0 red, 1 black, -1 all); out is zero
  * on the other slabs.  Full-lattice fields.  Asynchronous. */
 int lqcd_block_dslash(lqcd_t h, double* out, const double* in, double kappa, int colour,
@@ -203,8 +203,8 @@ int lqcd_pf_force(lqcd_t h, double* F, const double* phi, double kappa, int term
  * receive S_G and the average Re tr P / 3.  Synchronous. */
 int lqcd_gauge_force(lqcd_t h, double* F, double beta, double* S_out, double* plaq_out);
 
-/* Average force per time slice, the diagnostic of Sec. 3 (Fig. 1: "average
- * force on spatial links as a function of x0"): out (device double[2][L0])
+/* Average force per time slice, the diagnostic of Sec. 3 (Fig. 1 plots the
+ * mean force on the space-like links against x0): out (device double[2][L0])
  * receives, for each x0, the mean over the slice's space-like links
  * (row 0) and time-like links (row 1) of |F| = (sum_a F_a^2)^(1/2).
  * F: device forces double[4][V][8] (e.g. from lqcd_pf_force).  Asynchronous. */
