@@ -1107,6 +1107,136 @@ int lqo_pf_schur2(const lqo_geom* gi, const double* Ud, double kappa, const doub
 }
 
 /* ------------------------------------------------------------------ */
+/* even-odd and mass preconditioning of W2 (Sec. 1).  On the even sites */
+/*   W2,eo = 1 - kappa^2 H_eo H_oe   (hops inside the sub-slabs),        */
+/*   W3,eo = W2,eo + rho,                                                 */
+/* det W2 = det W2,eo (Schur complement of the odd-odd identity block).  */
+/* The four-part action represents det^2 W2 by                           */
+/*   S2 = |W3,eo W2,eo^-1 phi|^2   (det^2 of W2,eo W3,eo^-1),            */
+/*   S1 = |W3,eo^-1 phi|^2         (det^2 of W3,eo),                     */
+/* phi an even-site field double[V/2][4][3] complex.                      */
+/* ------------------------------------------------------------------ */
+/* out_e = (1 + rho) in_e - kappa^2 (H_eo H_oe) in_e; dagger: the adjoint,
+ * (1 + rho) - kappa^2 (H^dag)_eo (H^dag)_oe */
+static void w3eo_c(const G* g, const cplx* U, double kappa, double rho, const cplx* in, cplx* out, int dagger)
+{
+    size_t n = (size_t)g->V * 12, nh = (size_t)g->Vh * 12;
+    cplx* f = calloc(n, sizeof(cplx));
+    cplx* t = malloc(sizeof(cplx) * n);
+    memcpy(f, in, sizeof(cplx) * nh);
+    hop_c(g, U, f, t, LQO_HOP_INTRA2, dagger); /* odd part: H_oe in */
+    memset(t, 0, sizeof(cplx) * nh);
+    hop_c(g, U, t, f, LQO_HOP_INTRA2, dagger); /* even part: H_eo H_oe in */
+    for (size_t i = 0; i < nh; ++i) out[i] = (1.0 + rho) * in[i] - kappa * kappa * f[i];
+    free(f);
+    free(t);
+}
+
+/* A = W3,eo (adj = 0) or its adjoint (adj = 1) */
+typedef struct { const G* g; const cplx* U; double kappa, rho; int adj; } eoctx;
+
+static void op_w3eo(void* c, const cplx* in, cplx* out, int dagger)
+{
+    eoctx* o = (eoctx*)c;
+    w3eo_c(o->g, o->U, o->kappa, o->rho, in, out, dagger ^ o->adj);
+}
+
+/* x = W3,eo^-1 b (dagger: W3,eo^-dag b); rho = 0 gives W2,eo */
+static int w3eo_solve(const G* g, const cplx* U, double kappa, double rho, cplx* x, const cplx* b, int dagger,
+                      double tol, int maxit, int* iters)
+{
+    eoctx o = {g, U, kappa, rho, dagger};
+    return cgnr(op_w3eo, &o, (size_t)g->Vh * 12, x, b, tol, maxit, iters);
+}
+
+void lqo_apply_w3eo(const lqo_geom* gi, const double* U, double kappa, double rho, const double* in,
+                    double* out, int dagger)
+{
+    G g = mkg(gi);
+    w3eo_c(&g, (const cplx*)U, kappa, rho, (const cplx*)in, (cplx*)out, dagger);
+}
+
+int lqo_solve_w3eo(const lqo_geom* gi, const double* U, double kappa, double rho, double* x, const double* b,
+                   int dagger, double tol, int maxit, int* iters)
+{
+    G g = mkg(gi);
+    if (!g.l0s) return -2;
+    return w3eo_solve(&g, (const cplx*)U, kappa, rho, (cplx*)x, (const cplx*)b, dagger, tol, maxit, iters);
+}
+
+/* full-lattice fields for the force of <a, d(H_eo H_oe) b> on the even
+ * sites: A = (a_e, (H^dag)_oe a_e), B = (b_e, H_oe b_e), so that
+ * <a, dH_eo H_oe b> + <a, H_eo dH_oe b> = <A, dH B> over sub-slab hops */
+static void eo_pair(const G* g, const cplx* U, const cplx* a_e, const cplx* b_e, cplx* A, cplx* B)
+{
+    size_t n = (size_t)g->V * 12, nh = (size_t)g->Vh * 12;
+    cplx* t = malloc(sizeof(cplx) * n);
+    memset(A, 0, sizeof(cplx) * n);
+    memcpy(A, a_e, sizeof(cplx) * nh);
+    hop_c(g, U, A, t, LQO_HOP_INTRA2, 1);
+    memcpy(A + nh, t + nh, sizeof(cplx) * nh);
+    memset(B, 0, sizeof(cplx) * n);
+    memcpy(B, b_e, sizeof(cplx) * nh);
+    hop_c(g, U, B, t, LQO_HOP_INTRA2, 0);
+    memcpy(B + nh, t + nh, sizeof(cplx) * nh);
+    free(t);
+}
+
+/* S1 = |W3,eo^-1 phi|^2: eta = W3^-1 phi, xi = W3^-dag eta,
+ * dS1 = -2 Re <xi, dW3 eta> = 2 kappa^2 Re <xi, d(H_eo H_oe) eta> */
+int lqo_pf_s1(const lqo_geom* gi, const double* Ud, double kappa, double rho, const double* phi, double* F,
+              double* S, double tol, int maxit)
+{
+    G g = mkg(gi);
+    const cplx* U = (const cplx*)Ud;
+    if (!g.l0s) return -2;
+    size_t n = (size_t)g.V * 12, nh = (size_t)g.Vh * 12;
+    cplx* eta = malloc(sizeof(cplx) * nh);
+    int st = w3eo_solve(&g, U, kappa, rho, eta, (const cplx*)phi, 0, tol, maxit, NULL);
+    if (S) *S = nrm2(eta, nh);
+    if (F) {
+        cplx* xi = malloc(sizeof(cplx) * nh);
+        cplx* A = malloc(sizeof(cplx) * n);
+        cplx* B = malloc(sizeof(cplx) * n);
+        st |= w3eo_solve(&g, U, kappa, rho, xi, eta, 1, tol, maxit, NULL);
+        eo_pair(&g, U, xi, eta, A, B);
+        bilinear_c(&g, U, A, B, LQO_HOP_INTRA2, kappa * kappa, F);
+        free(xi); free(A); free(B);
+    }
+    free(eta);
+    return st;
+}
+
+/* S2 = |W3,eo W2,eo^-1 phi|^2 = |chi|^2, zeta = W2^-1 phi, chi = phi + rho zeta;
+ * d chi = -rho W2^-1 dW2 zeta, so dS2 = -2 rho Re <W2^-dag chi, dW2 zeta>
+ *                                     = 2 rho kappa^2 Re <lambda, d(H_eo H_oe) zeta> */
+int lqo_pf_s2(const lqo_geom* gi, const double* Ud, double kappa, double rho, const double* phi, double* F,
+              double* S, double tol, int maxit)
+{
+    G g = mkg(gi);
+    const cplx* U = (const cplx*)Ud;
+    if (!g.l0s) return -2;
+    size_t n = (size_t)g.V * 12, nh = (size_t)g.Vh * 12;
+    const cplx* ph = (const cplx*)phi;
+    cplx* zeta = malloc(sizeof(cplx) * nh);
+    cplx* chi = malloc(sizeof(cplx) * nh);
+    int st = w3eo_solve(&g, U, kappa, 0.0, zeta, ph, 0, tol, maxit, NULL);
+    for (size_t i = 0; i < nh; ++i) chi[i] = ph[i] + rho * zeta[i];
+    if (S) *S = nrm2(chi, nh);
+    if (F) {
+        cplx* lam = malloc(sizeof(cplx) * nh);
+        cplx* A = malloc(sizeof(cplx) * n);
+        cplx* B = malloc(sizeof(cplx) * n);
+        st |= w3eo_solve(&g, U, kappa, 0.0, lam, chi, 1, tol, maxit, NULL);
+        eo_pair(&g, U, lam, zeta, A, B);
+        bilinear_c(&g, U, A, B, LQO_HOP_INTRA2, rho * kappa * kappa, F);
+        free(lam); free(A); free(B);
+    }
+    free(zeta); free(chi);
+    return st;
+}
+
+/* ------------------------------------------------------------------ */
 /* gauge action S_G = -beta/3 sum_x sum_{mu>nu} Re tr(plaquette)        */
 /* ------------------------------------------------------------------ */
 static double plaq_re(const G* g, const cplx* U, int s, int mu, int nu)
@@ -1401,10 +1531,7 @@ typedef struct {
     const lqo_hmc_params* prm;
     double* U;
     double* P;
-    const double* phi1;
-    const double* phi2;
-    const double* phi3; /* |W2^-1 phi3|^2 (iterated decomposition) */
-    const double* phi4; /* |R2^-1 phi4|^2 */
+    lqo_pf_fields pf;
     double* F;
     int status;
 } md_t;
@@ -1418,21 +1545,29 @@ static void T_P(md_t* m, int j, double dt)
     memset(m->F, 0, sizeof(double) * nl);
     if (p->level_gauge == j) { lqo_gauge_force(m->gi, m->U, p->beta, m->F); any = 1; }
     if (p->level_w1 == j) {
-        m->status |= lqo_pf_w1(m->gi, m->U, p->kappa, m->phi1, m->F, NULL, p->tol, p->maxit);
+        m->status |= lqo_pf_w1(m->gi, m->U, p->kappa, m->pf.w1, m->F, NULL, p->tol, p->maxit);
         any = 1;
     }
     if (p->level_schur == j) {
-        m->status |= lqo_pf_schur(m->gi, m->U, p->kappa, m->phi2, m->F, NULL, p->schur_route,
+        m->status |= lqo_pf_schur(m->gi, m->U, p->kappa, m->pf.schur, m->F, NULL, p->schur_route,
                                   p->tol, p->maxit);
         any = 1;
     }
     if (p->level_w2 == j) {
-        m->status |= lqo_pf_w2(m->gi, m->U, p->kappa, m->phi3, m->F, NULL, p->tol, p->maxit);
+        m->status |= lqo_pf_w2(m->gi, m->U, p->kappa, m->pf.w2, m->F, NULL, p->tol, p->maxit);
         any = 1;
     }
     if (p->level_schur2 == j) {
-        m->status |= lqo_pf_schur2(m->gi, m->U, p->kappa, m->phi4, m->F, NULL, p->schur_route, p->tol,
+        m->status |= lqo_pf_schur2(m->gi, m->U, p->kappa, m->pf.schur2, m->F, NULL, p->schur_route, p->tol,
                                    p->maxit);
+        any = 1;
+    }
+    if (p->level_s2 == j) {
+        m->status |= lqo_pf_s2(m->gi, m->U, p->kappa, p->rho, m->pf.s2, m->F, NULL, p->tol, p->maxit);
+        any = 1;
+    }
+    if (p->level_s1 == j) {
+        m->status |= lqo_pf_s1(m->gi, m->U, p->kappa, p->rho, m->pf.s1, m->F, NULL, p->tol, p->maxit);
         any = 1;
     }
     if (!any) return;
@@ -1472,12 +1607,11 @@ static void step(md_t* m, int j, double dt)
 
 /* the molecular-dynamics part of a trajectory, T_LF/SW,top(dt_top)^n_top,
  * on (U, P) in place for fixed pseudo-fermion fields */
-int lqo_md(const lqo_geom* gi, double* U, double* P, const double* phi1, const double* phi2,
-           const double* phi3, const double* phi4, const lqo_hmc_params* p)
+int lqo_md(const lqo_geom* gi, double* U, double* P, const lqo_pf_fields* pf, const lqo_hmc_params* p)
 {
     G g = mkg(gi);
     double* F = malloc(sizeof(double) * (size_t)4 * g.V * 8);
-    md_t m = {&g, gi, p, U, P, phi1, phi2, phi3, phi4, F, 0};
+    md_t m = {&g, gi, p, U, P, *pf, F, 0};
     int top = p->nlevels - 1;
     double dt = p->tau / p->nsteps[top];
     for (int i = 0; i < p->nsteps[top]; ++i) step(&m, top, dt);
@@ -1509,6 +1643,11 @@ int lqo_hmc_trajectory(const lqo_geom* gi, double* U, const lqo_hmc_params* p, u
     double* phi3 = malloc(sizeof(cplx) * n);
     double* e4 = malloc(sizeof(cplx) * (nb2 + 1));
     double* phi4 = malloc(sizeof(cplx) * (nb2 + 1));
+    size_t nh = (size_t)g.Vh * 12;
+    double* e5 = malloc(sizeof(cplx) * nh);
+    double* phi5 = malloc(sizeof(cplx) * nh);
+    double* e6 = malloc(sizeof(cplx) * nh);
+    double* phi6 = malloc(sizeof(cplx) * nh);
     double* U0 = malloc(sizeof(cplx) * nu);
     memcpy(U0, U, sizeof(cplx) * nu);
     int st = 0;
@@ -1562,8 +1701,37 @@ int lqo_hmc_trajectory(const lqo_geom* gi, double* U, const lqo_hmc_params* p, u
         st |= lqo_schur2(gi, U, p->kappa, phi4, e4, LQO_R, p->schur_route, p->tol, p->maxit);
         H0 += nrm2((const cplx*)e4, nb2);
     }
-    st |= lqo_md(gi, U, P, phi1, phi2, phi3, phi4, p);
+    /* mass preconditioning of W2: phi_S2 = W2,eo W3,eo^-1 eta (stream 7),
+     * phi_S1 = W3,eo eta (stream 8), even-site fields */
+    if (p->level_s2 >= 0) {
+        lqo_normals(seed, 7, traj, (int64_t)nh * 2, e5);
+        for (size_t i = 0; i < nh * 2; ++i) e5[i] *= sqrt(0.5);
+        double* t = malloc(sizeof(cplx) * nh);
+        st |= w3eo_solve(&g, (const cplx*)U, p->kappa, p->rho, (cplx*)t, (const cplx*)e5, 0, p->tol * 1e-2,
+                         p->maxit, NULL);
+        w3eo_c(&g, (const cplx*)U, p->kappa, 0.0, (const cplx*)t, (cplx*)phi5, 0);
+        free(t);
+        H0 += nrm2((const cplx*)e5, nh);
+    }
+    if (p->level_s1 >= 0) {
+        lqo_normals(seed, 8, traj, (int64_t)nh * 2, e6);
+        for (size_t i = 0; i < nh * 2; ++i) e6[i] *= sqrt(0.5);
+        w3eo_c(&g, (const cplx*)U, p->kappa, p->rho, (const cplx*)e6, (cplx*)phi6, 0);
+        H0 += nrm2((const cplx*)e6, nh);
+    }
+    lqo_pf_fields pf = {phi1, phi2, phi3, phi4, phi5, phi6};
+    st |= lqo_md(gi, U, P, &pf, p);
     double H1 = kinetic(P, nl);
+    if (p->level_s2 >= 0) {
+        double S;
+        st |= lqo_pf_s2(gi, U, p->kappa, p->rho, phi5, NULL, &S, p->tol, p->maxit);
+        H1 += S;
+    }
+    if (p->level_s1 >= 0) {
+        double S;
+        st |= lqo_pf_s1(gi, U, p->kappa, p->rho, phi6, NULL, &S, p->tol, p->maxit);
+        H1 += S;
+    }
     if (p->level_w2 >= 0) {
         double S;
         st |= lqo_pf_w2(gi, U, p->kappa, phi3, NULL, &S, p->tol, p->maxit);
@@ -1601,5 +1769,6 @@ int lqo_hmc_trajectory(const lqo_geom* gi, double* U, const lqo_hmc_params* p, u
     }
     free(P); free(e1); free(e2); free(phi1); free(phi2); free(U0);
     free(e3); free(phi3); free(e4); free(phi4);
+    free(e5); free(phi5); free(e6); free(phi6);
     return st;
 }

@@ -41,9 +41,9 @@ enum { LQO_LF = 0, LQO_SW = 1 };
 
 typedef struct {
     double beta, kappa, tau, lambda;
-    int nlevels;
-    int scheme[4];
-    int nsteps[4];
+    int nlevels;      /* 1..5 */
+    int scheme[5];
+    int nsteps[5];
     int level_gauge, level_w1, level_schur; /* -1: term left out */
     int pf_init;      /* 0: heatbath phi = W eta; 1: phi = eta directly */
     int roll;         /* 1: shift U along x0 after the trajectory */
@@ -53,7 +53,19 @@ typedef struct {
     int maxit;
     const double* step_scale; /* NULL, or [2][L0] s(x0) for space-like / time-like links */
     int level_w2, level_schur2; /* iterated decomposition terms, -1: left out */
+    double rho;                 /* mass preconditioning W3,eo = W2,eo + rho */
+    int level_s2, level_s1;     /* |W3,eo W2,eo^-1 phi|^2 and |W3,eo^-1 phi|^2, -1: left out */
 } lqo_hmc_params;
+
+/* pseudo-fermion fields of the MD (NULL where the term is left out) */
+typedef struct {
+    const double* w1;     /* full spinor, |W1^-1 phi|^2 */
+    const double* schur;  /* boundary field, |R^-1 phi|^2 */
+    const double* w2;     /* full spinor, |W2^-1 phi|^2 */
+    const double* schur2; /* second-level boundary field, |R2^-1 phi|^2 */
+    const double* s2;     /* even sites, |W3,eo W2,eo^-1 phi|^2 */
+    const double* s1;     /* even sites, |W3,eo^-1 phi|^2 */
+} lqo_pf_fields;
 
 typedef struct {
     double dH, H0, H1;
@@ -109,9 +121,16 @@ void lqo_roll_x0(const lqo_geom* g, double* U, int shift);
 void lqo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void lqo_normals(uint64_t seed, uint32_t stream, uint32_t traj, int64_t n, double* out);
 void lqo_uniforms_metropolis(uint64_t seed, uint32_t traj, int L0, double* u, int* shift);
-int  lqo_md(const lqo_geom* g, double* U, double* P, const double* phi1,
-            const double* phi2, const double* phi3, const double* phi4,
+int  lqo_md(const lqo_geom* g, double* U, double* P, const lqo_pf_fields* pf,
             const lqo_hmc_params* prm);
+void lqo_apply_w3eo(const lqo_geom* g, const double* U, double kappa, double rho,
+                    const double* in_e, double* out_e, int dagger);
+int  lqo_solve_w3eo(const lqo_geom* g, const double* U, double kappa, double rho, double* x_e,
+                    const double* b_e, int dagger, double tol, int maxit, int* iters);
+int  lqo_pf_s1(const lqo_geom* g, const double* U, double kappa, double rho, const double* phi_e,
+               double* F, double* S, double tol, int maxit);
+int  lqo_pf_s2(const lqo_geom* g, const double* U, double kappa, double rho, const double* phi_e,
+               double* F, double* S, double tol, int maxit);
 int  lqo_block_solve2(const lqo_geom* g, const double* U, double kappa, double* x,
                       const double* b, int colour, int dagger, double tol, int maxit, int* iters);
 void lqo_apply_W2(const lqo_geom* g, const double* U, double kappa, const double* in,

@@ -25,12 +25,17 @@ class Geom(C.Structure):
 class HmcParams(C.Structure):
     _fields_ = [
         ("beta", C.c_double), ("kappa", C.c_double), ("tau", C.c_double), ("lam", C.c_double),
-        ("nlevels", C.c_int), ("scheme", C.c_int * 4), ("nsteps", C.c_int * 4),
+        ("nlevels", C.c_int), ("scheme", C.c_int * 5), ("nsteps", C.c_int * 5),
         ("level_gauge", C.c_int), ("level_w1", C.c_int), ("level_schur", C.c_int),
         ("pf_init", C.c_int), ("roll", C.c_int), ("schur_route", C.c_int),
         ("metropolis", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
         ("step_scale", C.c_void_p), ("level_w2", C.c_int), ("level_schur2", C.c_int),
+        ("rho", C.c_double), ("level_s2", C.c_int), ("level_s1", C.c_int),
     ]
+
+
+class PfFields(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("w1", "schur", "w2", "schur2", "s2", "s1")]
 
 
 class HmcResult(C.Structure):
@@ -253,6 +258,37 @@ class Lattice:
             raise RuntimeError("oracle second-level Schur force: a solve did not converge")
         return S.value, F
 
+    # ---- even-odd + mass preconditioning of W2 (even-site fields) ---------
+    def w3eo(self, U, kappa, rho, x_e, dagger=0):
+        out = np.zeros(self.half_shape(), np.complex128)
+        lib().lqo_apply_w3eo(C.byref(self.g), _p(U), C.c_double(kappa), C.c_double(rho),
+                             _p(np.ascontiguousarray(x_e)), _p(out), dagger)
+        return out
+
+    def solve_w3eo(self, U, kappa, rho, b_e, dagger=0, tol=1e-13, maxit=20000):
+        x = np.zeros(self.half_shape(), np.complex128)
+        it = C.c_int(0)
+        st = lib().lqo_solve_w3eo(C.byref(self.g), _p(U), C.c_double(kappa), C.c_double(rho), _p(x),
+                                  _p(np.ascontiguousarray(b_e)), dagger, C.c_double(tol), maxit, C.byref(it))
+        if st:
+            raise RuntimeError("oracle W3,eo solve did not converge")
+        return x
+
+    def _pf_eo(self, fn, U, kappa, rho, phi, force, tol, maxit):
+        F = np.zeros((4, self.V, 8)) if force else None
+        S = C.c_double(0)
+        st = fn(C.byref(self.g), _p(U), C.c_double(kappa), C.c_double(rho), _p(np.ascontiguousarray(phi)),
+                _p(F) if force else None, C.byref(S), C.c_double(tol), maxit)
+        if st:
+            raise RuntimeError("oracle mass-preconditioned force: a solve did not converge")
+        return S.value, F
+
+    def pf_s1(self, U, kappa, rho, phi, force=True, tol=1e-13, maxit=20000):
+        return self._pf_eo(lib().lqo_pf_s1, U, kappa, rho, phi, force, tol, maxit)
+
+    def pf_s2(self, U, kappa, rho, phi, force=True, tol=1e-13, maxit=20000):
+        return self._pf_eo(lib().lqo_pf_s2, U, kappa, rho, phi, force, tol, maxit)
+
     def force_profile(self, F):
         out = np.zeros((2, self.L[0]))
         lib().lqo_force_profile(C.byref(self.g), _p(np.ascontiguousarray(F)), _p(out))
@@ -318,14 +354,15 @@ def metropolis_uniforms(seed, traj, L0):
 
 def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w1=0,
                level_schur=0, lam=1.0 / 6.0, pf_init=0, roll=0, schur_route=1, metropolis=1,
-               tol=1e-12, maxit=50000, step_scale=None, level_w2=-1, level_schur2=-1):
+               tol=1e-12, maxit=50000, step_scale=None, level_w2=-1, level_schur2=-1, rho=0.0,
+               level_s2=-1, level_s1=-1):
     """step_scale: None, or a float64 array (2, L0) of s(x0) for space-like /
     time-like links (see step_scheme)"""
-    sc = list(scheme) + [0] * (4 - len(scheme))
-    ns = list(nsteps) + [1] * (4 - len(nsteps))
-    p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * 4)(*sc), (C.c_int * 4)(*ns),
+    sc = list(scheme) + [0] * (5 - len(scheme))
+    ns = list(nsteps) + [1] * (5 - len(nsteps))
+    p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * 5)(*sc), (C.c_int * 5)(*ns),
                   level_gauge, level_w1, level_schur, pf_init, roll, schur_route, metropolis,
-                  tol, maxit, None, level_w2, level_schur2)
+                  tol, maxit, None, level_w2, level_schur2, rho, level_s2, level_s1)
     if step_scale is not None:
         p._scale = np.ascontiguousarray(step_scale, dtype=np.float64)
         p.step_scale = p._scale.ctypes.data
@@ -340,13 +377,14 @@ def step_scheme(scheme, L0):
     return out
 
 
-def md(lat, U, P, phi1, phi2, prm, phi3=None, phi4=None):
-    """molecular dynamics only: integrates (U, P) for fixed pseudofermions"""
+def md(lat, U, P, phi1, phi2, prm, phi3=None, phi4=None, phi_s2=None, phi_s1=None):
+    """molecular dynamics only: integrates (U, P) for fixed pseudofermions
+    (phi1 W1, phi2 R, phi3 W2, phi4 R2, phi_s2 / phi_s1 the even-site fields
+    of the mass-preconditioned W2 terms)"""
     U2 = np.array(U, dtype=np.complex128, copy=True)
     P2 = np.array(P, dtype=np.float64, copy=True)
-    a1 = np.ascontiguousarray(phi1) if phi1 is not None else np.zeros(lat.spinor_shape(), np.complex128)
-    a2 = np.ascontiguousarray(phi2) if phi2 is not None else np.zeros(lat.bnd_shape(), np.complex128)
-    a3 = np.ascontiguousarray(phi3) if phi3 is not None else np.zeros(lat.spinor_shape(), np.complex128)
-    a4 = np.ascontiguousarray(phi4) if phi4 is not None else np.zeros(lat.bnd2_shape(), np.complex128)
-    st = lib().lqo_md(C.byref(lat.g), _p(U2), _p(P2), _p(a1), _p(a2), _p(a3), _p(a4), C.byref(prm))
+    keep = [np.ascontiguousarray(a) if a is not None else None
+            for a in (phi1, phi2, phi3, phi4, phi_s2, phi_s1)]
+    pf = PfFields(*[(a.ctypes.data if a is not None else None) for a in keep])
+    st = lib().lqo_md(C.byref(lat.g), _p(U2), _p(P2), C.byref(pf), C.byref(prm))
     return U2, P2, st
