@@ -375,19 +375,31 @@ def run_ours(args):
 # on four time scales (gauge / W2 / R2 / R), Omelyan on every level
 WL_ITER = dict(L=(64, 32, 32, 32), l0=8, l0s=4, kappa=0.158, beta=5.6, eps=0.6, seed=2010, tau=1.0,
                nlevels=4, scheme=(1, 1, 1, 1), nsteps=(2, 2, 2, 6), lam=0.1931833275037836,
-               level_gauge=0, level_w2=1, level_schur2=2, level_schur=3, tol=1e-10, max_iter=20000, therm=40)
+               level_gauge=0, level_w2=1, level_schur2=2, level_schur=3, tol=1e-10, max_iter=20000, therm=40,
+               name="iterated", metric="s/HMC trajectory (32^3x64, iterated slab decomposition)",
+               levels="gauge/W2/R2/R")
+# the paper's production form at 32 x 16^3 (Sec. 1-3, Table 1 row L0 = 32,
+# L = 16, kappa = 0.1575): l0 = L0/2, l0s = L0/4, the four-part action
+# S4 (R) + S3 (R2) + S2 + S1 with W3,eo = W2,eo + rho, rho = 0.20, five levels
+# n = (n0..n4) = (4, 2, 3, 1, 4), SW on levels 0, 1 and LF on 2, 3, 4,
+# lambda = 1/6, step-size scheme B
+WL_PROD = dict(L=(32, 16, 16, 16), l0=16, l0s=8, kappa=0.1575, beta=5.6, eps=0.6, seed=2011, tau=1.0,
+               nlevels=5, scheme=(1, 1, 0, 0, 0), nsteps=(4, 2, 3, 1, 4), lam=1.0 / 6.0,
+               level_gauge=0, level_w2=-1, level_schur2=3, level_schur=4, rho=0.20, level_s2=2, level_s1=1,
+               step_scheme=2, tol=1e-10, max_iter=20000, therm=40, name="production",
+               metric="s/HMC trajectory (32x16^3, four-part action, Table 1 schedule)",
+               levels="gauge/S1/S2/S3(R2)/S4(R)")
 
 
-def run_iterated(args):
-    """--case iterated: K trajectories of the four-part action at 32^3 x 64
-    in the mixed-precision form, the first input again in the plain double
+def run_iterated(args, W=WL_ITER):
+    """--case iterated / production: K trajectories of a four-part action in
+    the mixed-precision form, the first input again in the plain double
     form; one JSON line"""
     import torch
 
     from paper_0710_0066_gb300 import lqcd, synthetic as syn
 
     torch.cuda.set_device(0)
-    W = WL_ITER
     L = W["L"]
     lat = lqcd.Lattice(L, W["l0"], -1, l0s=W["l0s"])
     U0 = syn.random_links_torch(L, W["eps"], W["seed"], "cuda").contiguous()
@@ -397,7 +409,9 @@ def run_iterated(args):
         return lqcd.hmc_params(W["beta"], W["kappa"], W["tau"], W["nlevels"], W["scheme"], W["nsteps"],
                                W["level_gauge"], -1, W["level_schur"], lam=W["lam"], roll=1, metropolis=1,
                                precision=prec, tol=W["tol"], max_iter=W["max_iter"], level_w2=W["level_w2"],
-                               level_schur2=W["level_schur2"])
+                               level_schur2=W["level_schur2"], rho=W.get("rho", 0.0),
+                               level_s2=W.get("level_s2", -1), level_s1=W.get("level_s1", -1),
+                               step_scheme=W.get("step_scheme", 0))
 
     prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     prm = params(prec)
@@ -444,11 +458,12 @@ def run_iterated(args):
     peak, peak_kind = hbm_peak()
     achieved = by_sol / ms_sol / 1e6 if ms_sol > 0 else None
     line = {
-        "case": "iterated", "metric": "s/HMC trajectory (32^3x64, iterated slab decomposition)",
+        "case": W["name"], "metric": W["metric"],
         "value": sum(step_ms) / 1e3 / args.steps, "unit": "s/trajectory", "steps": args.steps,
         "warmup": args.warmup, "precision": args.precision,
         "config": {"lattice": "x".join(map(str, L)), "l0": W["l0"], "l0s": W["l0s"], "kappa": W["kappa"],
-                   "beta": W["beta"], "nsteps": W["nsteps"], "levels": "gauge/W2/R2/R",
+                   "beta": W["beta"], "nsteps": W["nsteps"], "levels": W["levels"], "rho": W.get("rho"),
+                   "step_scheme": W.get("step_scheme", 0), "scheme": W["scheme"],
                    "thermalisation": "%d pure-gauge trajectories from exp(i %.1f H)" % (W["therm"], W["eps"]),
                    "l2": "flushed between timed trajectories"},
         "solver": {"achieved_gbs": achieved, "peak": peak, "peak_kind": peak_kind,
@@ -475,7 +490,9 @@ def run_case(args):
     g.manual_seed(WL["seed"])
     prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     if args.case == "iterated":
-        return run_iterated(args)
+        return run_iterated(args, WL_ITER)
+    if args.case == "production":
+        return run_iterated(args, WL_PROD)
     if args.case == "solver":
         # the batched slab solve (8 slabs) and the global solve of the workload
         L, l0 = WL["L"], WL["l0"]
@@ -519,7 +536,7 @@ def run_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default=None, choices=["solver", "dslash", "iterated"],
+    ap.add_argument("--case", default=None, choices=["solver", "dslash", "iterated", "production"],
                     help="run one small kernel case instead of the benchmark (profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)

@@ -74,7 +74,10 @@ enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2 };
 enum { LQCD_OP_HOP = 0, LQCD_OP_MHAT = 1 };
 enum { LQCD_SCHUR_R = 0, LQCD_SCHUR_RDAG = 1, LQCD_SCHUR_RINV = 2, LQCD_SCHUR_RINVDAG = 3,
        LQCD_SCHUR2_R = 4, LQCD_SCHUR2_RDAG = 5, LQCD_SCHUR2_RINV = 6, LQCD_SCHUR2_RINVDAG = 7 };
-enum { LQCD_TERM_W1 = 0, LQCD_TERM_SCHUR = 1, LQCD_TERM_W2 = 2, LQCD_TERM_SCHUR2 = 3 };
+enum { LQCD_TERM_W1 = 0, LQCD_TERM_SCHUR = 1, LQCD_TERM_W2 = 2, LQCD_TERM_SCHUR2 = 3,
+       LQCD_TERM_S2 = 4, LQCD_TERM_S1 = 5 };
+enum { LQCD_EO_APPLY = 0, LQCD_EO_SOLVE = 1 };
+enum { LQCD_MAX_LEVELS = 5 };
 enum { LQCD_LF = 0, LQCD_SW = 1 };
 
 /* Create a handle for the lattice L[4] with x0-slabs of thickness l0 and
@@ -162,6 +165,20 @@ int lqcd_subblock_solve_batched(lqcd_t h, double* x, const double* b, double kap
                                 int dagger, int precision, double tol, int max_iter,
                                 int* iters_out, double* resid_out);
 
+/* Even-odd and mass preconditioning of W2 (Sec. 1): on the even sites of
+ * the sub-slabs, W2,eo = 1 - kappa^2 H_eo H_oe (the Schur complement of
+ * W2's odd-odd block, det W2 = det W2,eo) and W3,eo = W2,eo + rho.
+ * op LQCD_EO_APPLY: out = W3,eo in (dagger: W3,eo^dag in);
+ * op LQCD_EO_SOLVE: out = W3,eo^-1 in (dagger: W3,eo^-dag in), every
+ * sub-slab in one batched launch, relative residual <= tol; iters_out
+ * (host int[L0/l0s], may be NULL) the inner iterations per sub-slab.
+ * rho = 0 gives W2,eo.  in/out: even-site fields, the one-parity layout
+ * above (double[V/2][4][3][2]).  Synchronous.  LQCD_ERR_STATE without
+ * sub-slabs. */
+int lqcd_subblock_eo(lqcd_t h, double* out, const double* in, double kappa, double rho,
+                     int dagger, int op, int precision, double tol, int max_iter,
+                     int* iters_out);
+
 /* Solve M x = b (dagger: M^dag x = b) on the full lattice: even-odd reduced
  * BiCGstab, inner iterations in `precision`, double precision defect
  * correction to |b - M x| <= tol |b|.  iters_out / resid_out: host scalars
@@ -198,6 +215,14 @@ int lqcd_schur_apply(lqcd_t h, double* out, const double* in, double kappa, int 
 int lqcd_pf_force(lqcd_t h, double* F, const double* phi, double kappa, int term,
                   int precision, double tol, int max_iter, double* S_out);
 
+/* The two mass-preconditioned parts of det^2 W2 in the four-part action
+ * (Sec. 1, S2 and S1), phi an even-site field:
+ * term LQCD_TERM_S2: S = |W3,eo W2,eo^-1 phi|^2  (det^2 of W2,eo W3,eo^-1);
+ * term LQCD_TERM_S1: S = |W3,eo^-1 phi|^2        (det^2 of W3,eo);
+ * W3,eo = W2,eo + rho.  F, S_out as in lqcd_pf_force.  Synchronous. */
+int lqcd_pf_force_eo(lqcd_t h, double* F, const double* phi, double kappa, double rho, int term,
+                     int precision, double tol, int max_iter, double* S_out);
+
 /* Wilson gauge action (Sec. 1): S_G = -beta/3 sum_x sum_{mu>nu} Re tr P_{mu nu}(x).
  * F (device, may be NULL) += dS_G/dw^a; S_out / plaq_out (host, may be NULL)
  * receive S_G and the average Re tr P / 3.  Synchronous. */
@@ -221,9 +246,9 @@ typedef struct {
     double beta, kappa;
     double tau;         /* trajectory length */
     double lambda;      /* SW / Omelyan parameter, the paper uses 1/6 */
-    int nlevels;        /* 1..4 integration levels */
-    int scheme[4];      /* LQCD_LF or LQCD_SW per level */
-    int nsteps[4];      /* n_j: steps of level j per step of level j+1;
+    int nlevels;        /* 1..LQCD_MAX_LEVELS integration levels */
+    int scheme[LQCD_MAX_LEVELS];  /* LQCD_LF or LQCD_SW per level */
+    int nsteps[LQCD_MAX_LEVELS];  /* n_j: steps of level j per step of level j+1;
                            nsteps[nlevels-1] = steps per trajectory */
     int level_gauge;    /* level of S_G, -1 to leave the term out */
     int level_w1;       /* level of |W1^-1 phi1|^2, or -1 */
@@ -251,7 +276,29 @@ typedef struct {
      * heatbath (Philox streams 5 and 6; pf_init applies to phi1, phi2). */
     int level_w2;
     int level_schur2;
+    /* mass preconditioning of W2 (Sec. 1, W3,eo = W2,eo + rho): levels of
+     * S2 = |W3,eo W2,eo^-1 phi5|^2 and S1 = |W3,eo^-1 phi6|^2, or -1 (must be
+     * -1 without sub-slabs).  The paper's four-part action is level_schur
+     * (S4), level_schur2 (S3), level_s2 (S2), level_s1 (S1) with
+     * level_w1 = level_w2 = -1.  phi5 = W2,eo W3,eo^-1 eta5 and
+     * phi6 = W3,eo eta6 are drawn on Philox streams 7 and 8 (the even-site
+     * half of a full-lattice draw). */
+    double rho;
+    int level_s2;
+    int level_s1;
 } lqcd_hmc_params;
+
+/* Pseudo-fermion fields of lqcd_md (device pointers, NULL where the term
+ * is left out): w1, w2 full spinors; schur, schur2 first- / second-level
+ * boundary fields; s2, s1 even-site fields. */
+typedef struct {
+    const double* w1;
+    const double* schur;
+    const double* w2;
+    const double* schur2;
+    const double* s2;
+    const double* s1;
+} lqcd_pf_fields;
 
 typedef struct {
     double dH, H0, H1;
@@ -281,11 +328,9 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
                         const double* eta2, lqcd_hmc_result* res);
 
 /* Molecular dynamics only: integrates (U, P) in place (device buffers, gauge
- * and momenta layouts) for fixed phi1 (full spinor), phi2 (boundary field),
- * phi3 (full spinor, W2 term) and phi4 (second-level boundary field); each
- * may be NULL when its term is left out.  Synchronous. */
-int lqcd_md(lqcd_t h, double* U, double* P, const double* phi1, const double* phi2,
-            const double* phi3, const double* phi4, const lqcd_hmc_params* prm);
+ * and momenta layouts) for the fixed pseudo-fermion fields f (host struct
+ * of device pointers).  Synchronous. */
+int lqcd_md(lqcd_t h, double* U, double* P, const lqcd_pf_fields* f, const lqcd_hmc_params* prm);
 
 /* Kernel timing with CUDA events on the handle's stream.  kernel ids:
  * 0 hopping sweep, 1 persistent solver, 2 force, 3 gauge force / update,

@@ -28,7 +28,7 @@ int bnd_sub(lqcd_ctx* h, double* out, const double* in, int n);
 
 namespace {
 
-enum { F_T1 = 0, F_T2, F_A, F_B, F_C, F_D, F_E, F_G, F_PHI1, F_ETA1, F_PHI3, NFIELD };
+enum { F_T1 = 0, F_T2, F_A, F_B, F_C, F_D, F_E, F_G, F_PHI1, F_ETA1, F_PHI3, F_PHI5, F_PHI6, NFIELD };
 
 inline double2* fld(lqcd_ctx* h, int k) { return h->f64[k]; }
 
@@ -244,6 +244,78 @@ int pf_schur2(lqcd_ctx* h, double* F, const double* phi, double kappa, double co
 }
 
 // ---------------------------------------------------------------------------
+// even-odd + mass preconditioning of W2 (Sec. 1): W2,eo = 1 - kappa^2 H_eo H_oe
+// on the even sites of the sub-slabs, W3,eo = W2,eo + rho.  Even-site fields
+// live in the parity-0 half of full double fields.
+//   S1 = |W3,eo^-1 phi|^2:  dS1 = 2 kappa^2 Re <xi, d(H_eo H_oe) eta>,
+//        eta = W3^-1 phi, xi = W3^-dag eta
+//   S2 = |W3,eo W2,eo^-1 phi|^2 = |phi + rho zeta|^2, zeta = W2^-1 phi:
+//        dS2 = 2 rho kappa^2 Re <W2^-dag chi, d(H_eo H_oe) zeta>
+// ---------------------------------------------------------------------------
+// out_e = (1 + rho) in_e - kappa^2 H_eo H_oe in_e (dag: the adjoint); out != in
+int w3eo_apply(lqcd_ctx* h, double2* out, const double2* in, double kappa, double rho, int dag)
+{
+    GeoScope sc(h, sub_geo(h->g1));
+    const int Vh = h->g.Vh;
+    double2* t = fld(h, F_T1);
+    LQ_TRY(hop_sweep(h, PREC64, MODE_INTRA, dag, 1, -1, sp64(t, 1, Vh), sp64((double2*)in, 0, Vh), 0.0, none(),
+                     1.0));
+    return hop_sweep(h, PREC64, MODE_INTRA, dag, 0, -1, sp64(out, 0, Vh), sp64(t, 1, Vh), 1.0 + rho,
+                     sp64((double2*)in, 0, Vh), -kappa * kappa);
+}
+
+// x_e = W3,eo^-1 b_e, all sub-slabs in one batched launch (dag: W3,eo^-dag =
+// g5 W3,eo^-1 g5); x must not alias b
+int w3eo_solve(lqcd_ctx* h, double2* x, const double2* b, double kappa, double rho, int dag, const SolveCfg& c,
+               int* iters = nullptr, double* resid = nullptr)
+{
+    GeoScope sc(h, sub_geo(h->g1));
+    const double2* bb = b;
+    if (dag) {
+        LQ_TRY(gamma5_full(h, fld(h, F_T2), b));
+        bb = fld(h, F_T2);
+    }
+    LQ_TRY(eo_solve(h, MODE_INTRA, -1, c.prec, kappa, x, bb, c.tol, c.max_iter, iters, resid, 1.0 + rho));
+    if (dag) LQ_TRY(gamma5_full(h, x, x));
+    return LQCD_OK;
+}
+
+// F += coef * d/dw 2 Re <a, d(H_eo H_oe) b> for even-site a, b (parity-0
+// halves); their odd halves are overwritten with (H^dag)_oe a and H_oe b
+int eo_force(lqcd_ctx* h, double* F, double2* a, double2* b, double coef, int prec, const double* ss)
+{
+    GeoScope sc(h, sub_geo(h->g1));
+    const int Vh = h->g.Vh;
+    LQ_TRY(hop_sweep(h, PREC64, MODE_INTRA, 1, 1, -1, sp64(a, 1, Vh), sp64(a, 0, Vh), 0.0, none(), 1.0));
+    LQ_TRY(hop_sweep(h, PREC64, MODE_INTRA, 0, 1, -1, sp64(b, 1, Vh), sp64(b, 0, Vh), 0.0, none(), 1.0));
+    return force_bilinear(h, F, a, b, MODE_INTRA, coef, nullptr, nullptr, 0, 0.0, prec, ss);
+}
+
+int pf_s1(lqcd_ctx* h, double* F, const double2* phi, double kappa, double rho, double coef, const SolveCfg& c,
+          double* S_dev, const double* ss = nullptr)
+{
+    double2 *eta = fld(h, F_A), *xi = fld(h, F_B);
+    LQ_TRY(w3eo_solve(h, eta, phi, kappa, rho, 0, c));
+    if (S_dev) LQ_TRY(norm2_dev(h, (const double*)eta, (int64_t)24 * h->g.Vh, S_dev));
+    if (!F) return LQCD_OK;
+    LQ_TRY(w3eo_solve(h, xi, eta, kappa, rho, 1, c));
+    return eo_force(h, F, xi, eta, kappa * kappa * coef, c.prec, ss);
+}
+
+int pf_s2(lqcd_ctx* h, double* F, const double2* phi, double kappa, double rho, double coef, const SolveCfg& c,
+          double* S_dev, const double* ss = nullptr)
+{
+    double2 *zeta = fld(h, F_A), *lam = fld(h, F_B), *chi = fld(h, F_C);
+    LQ_TRY(w3eo_solve(h, zeta, phi, kappa, 0.0, 0, c));
+    LQ_TRY(axpby_full(h, chi, 1.0, phi, 0.0, -1));
+    LQ_TRY(axpby_full(h, chi, rho, zeta, 1.0, -1));
+    if (S_dev) LQ_TRY(norm2_dev(h, (const double*)chi, (int64_t)24 * h->g.Vh, S_dev));
+    if (!F) return LQCD_OK;
+    LQ_TRY(w3eo_solve(h, lam, chi, kappa, 0.0, 1, c));
+    return eo_force(h, F, lam, zeta, rho * kappa * kappa * coef, c.prec, ss);
+}
+
+// ---------------------------------------------------------------------------
 // integrator schedule (Sec. 2, eqs. (5)-(7)); consecutive kicks of one level
 // act on the same field and are merged
 // ---------------------------------------------------------------------------
@@ -296,7 +368,7 @@ void build_step(const lqcd_hmc_params& p, int j, double dt, std::vector<Op>& v)
 
 int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
 {
-    if (!p || p->nlevels < 1 || p->nlevels > 4 || !(p->tau > 0) || !prec_ok(p->precision) || !(p->tol > 0)) {
+    if (!p || p->nlevels < 1 || p->nlevels > LQCD_MAX_LEVELS || !(p->tau > 0) || !prec_ok(p->precision) || !(p->tol > 0)) {
         h->err = "hmc params: bad nlevels / tau / precision / tol";
         return LQCD_ERR_ARG;
     }
@@ -310,14 +382,15 @@ int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
             return LQCD_ERR_ARG;
         }
     }
-    const int lv[5] = {p->level_gauge, p->level_w1, p->level_schur, p->level_w2, p->level_schur2};
-    for (int k = 0; k < 5; ++k)
+    const int lv[7] = {p->level_gauge, p->level_w1, p->level_schur, p->level_w2, p->level_schur2,
+                       p->level_s2, p->level_s1};
+    for (int k = 0; k < 7; ++k)
         if (lv[k] < -1 || lv[k] >= p->nlevels) {
             h->err = "hmc params: term level out of range";
             return LQCD_ERR_ARG;
         }
-    if ((p->level_w2 >= 0 || p->level_schur2 >= 0) && !h->g1.l0s) {
-        h->err = "hmc params: the W2 / R2 terms need sub-slabs (lqcd_set_subslabs)";
+    if ((p->level_w2 >= 0 || p->level_schur2 >= 0 || p->level_s2 >= 0 || p->level_s1 >= 0) && !h->g1.l0s) {
+        h->err = "hmc params: the W2 / R2 / S2 / S1 terms need sub-slabs (lqcd_set_subslabs)";
         return LQCD_ERR_STATE;
     }
     if (!p->step_scale && p->step_scheme) {
@@ -363,12 +436,15 @@ int md_scale_table(lqcd_ctx* h, const lqcd_hmc_params& p, const double** out)
     return LQCD_OK;
 }
 
-// pseudo-fermion fields of the MD: phi1 (W1), phi2 (R), phi3 (W2), phi4 (R2)
+// pseudo-fermion fields of the MD: phi1 (W1), phi2 (R), phi3 (W2), phi4 (R2),
+// phi5 (S2, even sites), phi6 (S1, even sites)
 struct PfFields {
     const double2* phi1;
     const double* phi2;
     const double2* phi3;
     const double* phi4;
+    const double2* phi5;
+    const double2* phi6;
 };
 
 int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, int* nforce)
@@ -402,6 +478,14 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
             LQ_TRY(pf_schur2(h, P, pf.phi4, p.kappa, -o.dt, c, nullptr, ss));
             ++*nforce;
         }
+        if (p.level_s2 == o.level) {
+            LQ_TRY(pf_s2(h, P, pf.phi5, p.kappa, p.rho, -o.dt, c, nullptr, ss));
+            ++*nforce;
+        }
+        if (p.level_s1 == o.level) {
+            LQ_TRY(pf_s1(h, P, pf.phi6, p.kappa, p.rho, -o.dt, c, nullptr, ss));
+            ++*nforce;
+        }
     }
     return LQCD_OK;
 }
@@ -421,9 +505,9 @@ void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1)
     }
 }
 
-// the (up to) six energy terms: kinetic, gauge, W1, Schur, W2, Schur2 ->
-// red_out[base..base+5]
-constexpr int NTERM = 6;
+// the (up to) eight energy terms: kinetic, gauge, W1, Schur, W2, Schur2, S2, S1
+// -> red_out[base..base+7]
+constexpr int NTERM = 8;
 
 int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, int base)
 {
@@ -435,6 +519,8 @@ int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, int base)
     if (p.level_schur >= 0) LQ_TRY(pf_schur(h, nullptr, pf.phi2, p.kappa, 0.0, c, e + 3));
     if (p.level_w2 >= 0) LQ_TRY(pf_w2(h, nullptr, pf.phi3, p.kappa, 0.0, c, e + 4));
     if (p.level_schur2 >= 0) LQ_TRY(pf_schur2(h, nullptr, pf.phi4, p.kappa, 0.0, c, e + 5));
+    if (p.level_s2 >= 0) LQ_TRY(pf_s2(h, nullptr, pf.phi5, p.kappa, p.rho, 0.0, c, e + 6));
+    if (p.level_s1 >= 0) LQ_TRY(pf_s1(h, nullptr, pf.phi6, p.kappa, p.rho, 0.0, c, e + 7));
     return LQCD_OK;
 }
 
@@ -446,6 +532,8 @@ double combine(const lqcd_hmc_params& p, const double* e)
     if (p.level_schur >= 0) H += e[3];
     if (p.level_w2 >= 0) H += e[4];
     if (p.level_schur2 >= 0) H += e[5];
+    if (p.level_s2 >= 0) H += e[6];
+    if (p.level_s1 >= 0) H += e[7];
     return H;
 }
 
@@ -593,9 +681,9 @@ int lqcd_create(lqcd_t* out, const int L[4], int l0, int bc_t, void* stream)
     for (int k = 0; k < 4; ++k) LQ_CUDA(h, cudaMalloc(&h->bnd[k], sizeof(double) * std::max<size_t>(nb2, 2)));
     h->red_blocks = reduction_blocks();
     LQ_CUDA(h, cudaMalloc(&h->red_part, sizeof(double) * h->red_blocks));
-    LQ_CUDA(h, cudaMalloc(&h->red_out, sizeof(double) * 16));
-    LQ_CUDA(h, cudaMallocHost(&h->red_host, sizeof(double) * 16));
-    LQ_CUDA(h, cudaMemsetAsync(h->red_out, 0, sizeof(double) * 16, h->stream));
+    LQ_CUDA(h, cudaMalloc(&h->red_out, sizeof(double) * 32));
+    LQ_CUDA(h, cudaMallocHost(&h->red_host, sizeof(double) * 32));
+    LQ_CUDA(h, cudaMemsetAsync(h->red_out, 0, sizeof(double) * 32, h->stream));
     return solver_init(h);
 }
 
@@ -916,31 +1004,86 @@ int lqcd_rng_normals(lqcd_t h, double* out, int64_t n, uint64_t seed, uint32_t s
     return rng_normals(h, out, n, seed, stream, traj, 1.0);
 }
 
-int lqcd_md(lqcd_t h, double* U, double* P, const double* phi1, const double* phi2, const double* phi3,
-            const double* phi4, const lqcd_hmc_params* prm)
+int lqcd_md(lqcd_t h, double* U, double* P, const lqcd_pf_fields* f, const lqcd_hmc_params* prm)
 {
     CHECK_H(h);
-    NEED(U && P, "null U / P");
+    NEED(U && P && f, "null U / P / fields");
     LQ_TRY(check_params(h, prm));
-    NEED(prm->level_w1 < 0 || phi1, "phi1 needed for the W1 term");
-    NEED(prm->level_schur < 0 || phi2, "phi2 needed for the Schur term");
-    NEED(prm->level_w2 < 0 || phi3, "phi3 needed for the W2 term");
-    NEED(prm->level_schur2 < 0 || phi4, "phi4 needed for the second-level Schur term");
+    NEED(prm->level_w1 < 0 || f->w1, "the W1 field is needed");
+    NEED(prm->level_schur < 0 || f->schur, "the boundary field is needed");
+    NEED(prm->level_w2 < 0 || f->w2, "the W2 field is needed");
+    NEED(prm->level_schur2 < 0 || f->schur2, "the second-level boundary field is needed");
+    NEED(prm->level_s2 < 0 || f->s2, "the S2 field is needed");
+    NEED(prm->level_s1 < 0 || f->s1, "the S1 field is needed");
     LQ_TRY(pack_gauge(h, U));
     h->have_gauge = true;
-    if (prm->level_w1 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI1), phi1, 0, 2));
+    if (prm->level_w1 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI1), f->w1, 0, 2));
     if (prm->level_schur >= 0)
-        LQ_CUDA(h, cudaMemcpyAsync(h->bnd[0], phi2, sizeof(double) * 2 * nbnd_of(h->g), cudaMemcpyDeviceToDevice,
+        LQ_CUDA(h, cudaMemcpyAsync(h->bnd[0], f->schur, sizeof(double) * 2 * nbnd_of(h->g), cudaMemcpyDeviceToDevice,
                                    h->stream));
-    if (prm->level_w2 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI3), phi3, 0, 2));
+    if (prm->level_w2 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI3), f->w2, 0, 2));
     if (prm->level_schur2 >= 0)
-        LQ_CUDA(h, cudaMemcpyAsync(h->bnd[3], phi4, sizeof(double) * 2 * nbnd2_of(h->g1),
+        LQ_CUDA(h, cudaMemcpyAsync(h->bnd[3], f->schur2, sizeof(double) * 2 * nbnd2_of(h->g1),
                                    cudaMemcpyDeviceToDevice, h->stream));
+    if (prm->level_s2 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI5), f->s2, 0, 1));
+    if (prm->level_s1 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI6), f->s1, 0, 1));
     int nf = 0;
-    const PfFields pf{fld(h, F_PHI1), h->bnd[0], fld(h, F_PHI3), h->bnd[3]};
+    const PfFields pf{fld(h, F_PHI1), h->bnd[0], fld(h, F_PHI3), h->bnd[3], fld(h, F_PHI5), fld(h, F_PHI6)};
     LQ_TRY(do_md(h, *prm, P, pf, &nf));
     LQ_TRY(unpack_gauge(h, U));
     LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LQCD_OK;
+}
+
+int lqcd_subblock_eo(lqcd_t h, double* out, const double* in, double kappa, double rho, int dagger, int op,
+                     int precision, double tol, int max_iter, int* iters_out)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(out && in, "null field pointer");
+    NEED(op == LQCD_EO_APPLY || op == LQCD_EO_SOLVE, "bad op");
+    NEED(prec_ok(precision) && (op == LQCD_EO_APPLY || (tol > 0 && max_iter > 0)), "bad precision / tol / max_iter");
+    if (!h->g1.l0s) {
+        h->err = "no sub-slabs (lqcd_set_subslabs)";
+        return LQCD_ERR_STATE;
+    }
+    double2 *A = fld(h, F_D), *B = fld(h, F_E);
+    LQ_TRY(pack_spinor(h, A, in, 0, 1));
+    if (op == LQCD_EO_APPLY) {
+        LQ_TRY(w3eo_apply(h, B, A, kappa, rho, dagger));
+    } else {
+        const int nbs = h->g1.L[0] / h->g1.l0s;
+        std::vector<int> it(nbs, 0);
+        SolveCfg c{precision, tol, max_iter};
+        LQ_TRY(w3eo_solve(h, B, A, kappa, rho, dagger, c, it.data(), nullptr));
+        if (iters_out)
+            for (int k = 0; k < nbs; ++k) iters_out[k] = it[k];
+    }
+    LQ_TRY(unpack_spinor(h, out, B, 0, 1));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LQCD_OK;
+}
+
+int lqcd_pf_force_eo(lqcd_t h, double* F, const double* phi, double kappa, double rho, int term, int precision,
+                     double tol, int max_iter, double* S_out)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(phi, "null phi");
+    NEED(term == LQCD_TERM_S2 || term == LQCD_TERM_S1, "bad term");
+    NEED(prec_ok(precision) && tol > 0 && max_iter > 0, "bad precision / tol / max_iter");
+    if (!h->g1.l0s) {
+        h->err = "no sub-slabs (lqcd_set_subslabs)";
+        return LQCD_ERR_STATE;
+    }
+    SolveCfg c{precision, tol, max_iter};
+    double2* ph = fld(h, term == LQCD_TERM_S2 ? F_PHI5 : F_PHI6);
+    LQ_TRY(pack_spinor(h, ph, phi, 0, 1));
+    if (term == LQCD_TERM_S2) LQ_TRY(pf_s2(h, F, ph, kappa, rho, 1.0, c, h->red_out));
+    else LQ_TRY(pf_s1(h, F, ph, kappa, rho, 1.0, c, h->red_out));
+    double S;
+    LQ_TRY(read_scalars(h, 1, &S));
+    if (S_out) *S_out = S;
     return LQCD_OK;
 }
 
@@ -966,8 +1109,8 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
     else
         LQ_TRY(rng_normals(h, h->P, (int64_t)32 * g.V, seed, 1, traj, 1.0));
     SolveCfg c{p.precision, p.tol, p.max_iter};
-    double* e0 = h->red_out;  // [0..5] H0 terms, [6..11] H1 terms, [12] plaquette
-    LQ_CUDA(h, cudaMemsetAsync(h->red_out, 0, sizeof(double) * 16, h->stream));
+    double* e0 = h->red_out;  // [0..7] H0 terms, [8..15] H1 terms, [16] plaquette
+    LQ_CUDA(h, cudaMemsetAsync(h->red_out, 0, sizeof(double) * 32, h->stream));
     LQ_TRY(kinetic_sum(h, h->P, e0));
     if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, e0 + 1));
     if (p.level_w1 >= 0) {
@@ -1010,8 +1153,23 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
         LQ_TRY(schur2_op(h, h->bnd[3], e4, p.kappa, LQCD_SCHUR_R, c));
         LQ_TRY(norm2_dev(h, e4, nbd2, e0 + 5));
     }
+    // mass-preconditioned W2 (even sites): phi5 = W2,eo W3,eo^-1 eta5,
+    // phi6 = W3,eo eta6 (Philox streams 7 and 8; the even half of a full draw)
+    if (p.level_s2 >= 0) {
+        double2* et = fld(h, F_ETA1);
+        LQ_TRY(rng_spinor(h, et, seed, 7, traj));
+        LQ_TRY(w3eo_solve(h, fld(h, F_G), et, p.kappa, p.rho, 0, c));
+        LQ_TRY(w3eo_apply(h, fld(h, F_PHI5), fld(h, F_G), p.kappa, 0.0, 0));
+        LQ_TRY(norm2_dev(h, (const double*)et, (int64_t)24 * g.Vh, e0 + 6));
+    }
+    if (p.level_s1 >= 0) {
+        double2* et = fld(h, F_ETA1);
+        LQ_TRY(rng_spinor(h, et, seed, 8, traj));
+        LQ_TRY(w3eo_apply(h, fld(h, F_PHI6), et, p.kappa, p.rho, 0));
+        LQ_TRY(norm2_dev(h, (const double*)et, (int64_t)24 * g.Vh, e0 + 7));
+    }
     int nforce = 0;
-    const PfFields pf{fld(h, F_PHI1), h->bnd[0], fld(h, F_PHI3), h->bnd[3]};
+    const PfFields pf{fld(h, F_PHI1), h->bnd[0], fld(h, F_PHI3), h->bnd[3], fld(h, F_PHI5), fld(h, F_PHI6)};
     LQ_TRY(do_md(h, p, h->P, pf, &nforce));
     LQ_TRY(energy(h, p, pf, NTERM));
     double e[2 * NTERM];
@@ -1039,7 +1197,7 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
                                    h->stream));
         LQ_TRY(roll_links(h, shift));
     }
-    LQ_TRY(plaquette_sum(h, h->red_out + 2 * NTERM));
+    LQ_TRY(plaquette_sum(h, h->red_out + 2 * NTERM));  // [16] of 32
     LQ_TRY(unpack_gauge(h, U));
     double pl;
     LQ_CUDA(h, cudaMemcpyAsync(h->red_host, h->red_out + 2 * NTERM, sizeof(double), cudaMemcpyDeviceToHost,

@@ -37,6 +37,7 @@ struct SolveArgs {
     Geo g;
     int mode;  // MODE_INTRA: slabs, MODE_ALL: whole lattice
     double k2;
+    double diag;  // the system is diag - k2 H_eo H_oe (1, or 1 + rho for W3,eo)
     int nsys, cps;
     int slab0, slabstep;
     int nsite;
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             {
                 double qr = 0.0, qi = 0.0;
                 if (act) {
-                    const T k2 = (T)A.k2;
+                    const T k2 = (T)A.k2, dg = (T)A.diag;
                     FOR_SITES
                     {
                         const int i = base + j_;
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 #pragma unroll
                         for (int s = 0; s < 4; ++s)
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) a.c[s][c] = pp.c[s][c] - k2 * a.c[s][c];
+                            for (int c = 0; c < 3; ++c) a.c[s][c] = dg * pp.c[s][c] - k2 * a.c[s][c];
                         store_spinor<P>(A.v, i, a);
                         if (P == PREC16) load_spinor<P, false>(A.v, i, a);
                         load_spinor<P, false>(A.rh, i, rh);
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             {
                 double qr = 0.0, qi = 0.0, qt = 0.0;
                 if (act2) {
-                    const T k2 = (T)A.k2;
+                    const T k2 = (T)A.k2, dg = (T)A.diag;
                     FOR_SITES
                     {
                         const int i = base + j_;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 #pragma unroll
                         for (int s = 0; s < 4; ++s)
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) a.c[s][c] = ss.c[s][c] - k2 * a.c[s][c];
+                            for (int c = 0; c < 3; ++c) a.c[s][c] = dg * ss.c[s][c] - k2 * a.c[s][c];
                         store_spinor<P>(A.t, i, a);
                         if (P == PREC16) load_spinor<P, false>(A.t, i, a);
                         cdot_acc(a, ss, qr, qi);
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 #pragma unroll
                     for (int s = 0; s < 4; ++s)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) a.c[s][c] = bb.c[s][c] - xx.c[s][c] + A.k2 * a.c[s][c];
+                        for (int c = 0; c < 3; ++c) a.c[s][c] = bb.c[s][c] - A.diag * xx.c[s][c] + A.k2 * a.c[s][c];
                     store_spinor<PREC64>(A.r64, i, a);
                     q += nrm_acc(a);
                 }
@@ -734,7 +735,7 @@ static void solver_site_bytes(int prec, double* inner, double* outer)
 }
 
 int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e, const double2* b_e,
-             double tol, int max_iter, int* iters_sys, double* resid_sys)
+             double tol, int max_iter, int* iters_sys, double* resid_sys, double diag)
 {
     Work* w = h->work;
     const Geo& g = h->g;
@@ -742,6 +743,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.g = g;
     A.mode = mode;
     A.k2 = kappa * kappa;
+    A.diag = diag;
     if (mode == MODE_INTRA) {
         A.nsys = colour < 0 ? g.nb : g.nb / 2;
         A.slab0 = colour < 0 ? 0 : colour;

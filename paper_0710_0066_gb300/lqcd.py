@@ -23,7 +23,9 @@ PREC_F64, PREC_F32, PREC_F16 = 0, 1, 2
 OP_HOP, OP_MHAT = 0, 1
 SCHUR_R, SCHUR_RDAG, SCHUR_RINV, SCHUR_RINVDAG = 0, 1, 2, 3
 SCHUR2_R, SCHUR2_RDAG, SCHUR2_RINV, SCHUR2_RINVDAG = 4, 5, 6, 7
-TERM_W1, TERM_SCHUR, TERM_W2, TERM_SCHUR2 = 0, 1, 2, 3
+TERM_W1, TERM_SCHUR, TERM_W2, TERM_SCHUR2, TERM_S2, TERM_S1 = 0, 1, 2, 3, 4, 5
+EO_APPLY, EO_SOLVE = 0, 1
+MAX_LEVELS = 5
 LF, SW = 0, 1
 KERNEL_HOP, KERNEL_SOLVER, KERNEL_FORCE, KERNEL_GAUGE, KERNEL_BLAS = 0, 1, 2, 3, 4
 
@@ -34,19 +36,24 @@ EXPORTS = [
     "lqcd_gauge_force", "lqcd_rng_normals", "lqcd_hmc_trajectory", "lqcd_md",
     "lqcd_profile_enable", "lqcd_profile_reset", "lqcd_profile_read", "lqcd_launch_count",
     "lqcd_gauge_action_static", "lqcd_force_profile", "lqcd_set_subslabs", "lqcd_subblock_dslash",
-    "lqcd_subblock_solve_batched",
+    "lqcd_subblock_solve_batched", "lqcd_subblock_eo", "lqcd_pf_force_eo",
 ]
 
 
 class HmcParams(C.Structure):
     _fields_ = [
         ("beta", C.c_double), ("kappa", C.c_double), ("tau", C.c_double), ("lam", C.c_double),
-        ("nlevels", C.c_int), ("scheme", C.c_int * 4), ("nsteps", C.c_int * 4),
+        ("nlevels", C.c_int), ("scheme", C.c_int * MAX_LEVELS), ("nsteps", C.c_int * MAX_LEVELS),
         ("level_gauge", C.c_int), ("level_w1", C.c_int), ("level_schur", C.c_int),
         ("pf_init", C.c_int), ("roll", C.c_int), ("metropolis", C.c_int), ("precision", C.c_int),
         ("tol", C.c_double), ("max_iter", C.c_int), ("step_scheme", C.c_int), ("step_scale", C.c_void_p),
         ("level_w2", C.c_int), ("level_schur2", C.c_int),
+        ("rho", C.c_double), ("level_s2", C.c_int), ("level_s1", C.c_int),
     ]
+
+
+class PfFields(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("w1", "schur", "w2", "schur2", "s2", "s1")]
 
 
 class HmcResult(C.Structure):
@@ -60,14 +67,15 @@ class HmcResult(C.Structure):
 
 def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w1=0, level_schur=0,
                lam=1.0 / 6.0, pf_init=0, roll=0, metropolis=1, precision=PREC_F64, tol=1e-10,
-               max_iter=20000, step_scheme=0, step_scale=None, level_w2=-1, level_schur2=-1):
+               max_iter=20000, step_scheme=0, step_scale=None, level_w2=-1, level_schur2=-1, rho=0.0,
+               level_s2=-1, level_s1=-1):
     """step_scale: None or a host float64 array (2, L0) of s(x0) (space-like,
     time-like rows); it is kept alive on the returned object"""
-    sc = list(scheme) + [0] * (4 - len(scheme))
-    ns = list(nsteps) + [1] * (4 - len(nsteps))
-    p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * 4)(*sc), (C.c_int * 4)(*ns),
+    sc = list(scheme) + [0] * (MAX_LEVELS - len(scheme))
+    ns = list(nsteps) + [1] * (MAX_LEVELS - len(nsteps))
+    p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * MAX_LEVELS)(*sc), (C.c_int * MAX_LEVELS)(*ns),
                   level_gauge, level_w1, level_schur, pf_init, roll, metropolis, precision, tol,
-                  max_iter, step_scheme, None, level_w2, level_schur2)
+                  max_iter, step_scheme, None, level_w2, level_schur2, rho, level_s2, level_s1)
     if step_scale is not None:
         import numpy as np
 
@@ -105,7 +113,9 @@ def load():
         "lqcd_gauge_force": [vp, vp, d, vp, vp],
         "lqcd_rng_normals": [vp, vp, i64, u64, u32, u32],
         "lqcd_hmc_trajectory": [vp, vp, vp, u64, u32, vp, vp, vp, vp],
-        "lqcd_md": [vp, vp, vp, vp, vp, vp, vp, vp],
+        "lqcd_md": [vp, vp, vp, vp, vp],
+        "lqcd_subblock_eo": [vp, vp, vp, d, d, i, i, i, d, i, vp],
+        "lqcd_pf_force_eo": [vp, vp, vp, d, d, i, i, d, i, vp],
         "lqcd_set_subslabs": [vp, i],
         "lqcd_subblock_dslash": [vp, vp, vp, d, i, i, i],
         "lqcd_subblock_solve_batched": [vp, vp, vp, d, i, i, i, d, i, vp, vp],
@@ -268,9 +278,24 @@ def lqcd_hmc_trajectory(h, U, prm, seed, traj, P0=None, eta1=None, eta2=None):
     return res
 
 
-def lqcd_md(h, U, P, phi1, phi2, prm, phi3=None, phi4=None):
-    return _check(h, load().lqcd_md(h, _ptr(U), _ptr(P), _ptr(phi1), _ptr(phi2), _ptr(phi3), _ptr(phi4),
-                                    C.byref(prm)))
+def lqcd_md(h, U, P, prm, w1=None, schur=None, w2=None, schur2=None, s2=None, s1=None):
+    f = PfFields(*[_ptr(t) for t in (w1, schur, w2, schur2, s2, s1)])
+    return _check(h, load().lqcd_md(h, _ptr(U), _ptr(P), C.byref(f), C.byref(prm)))
+
+
+def lqcd_subblock_eo(h, out, inp, kappa, rho, dagger=0, op=EO_APPLY, precision=PREC_F64, tol=1e-10,
+                     max_iter=10000, nbs=128):
+    it = (C.c_int * nbs)()
+    _check(h, load().lqcd_subblock_eo(h, _ptr(out), _ptr(inp), float(kappa), float(rho), int(dagger), int(op),
+                                      int(precision), float(tol), int(max_iter), it))
+    return list(it)
+
+
+def lqcd_pf_force_eo(h, F, phi, kappa, rho, term, precision=PREC_F64, tol=1e-10, max_iter=20000):
+    S = C.c_double(0)
+    _check(h, load().lqcd_pf_force_eo(h, _ptr(F), _ptr(phi), float(kappa), float(rho), int(term), int(precision),
+                                      float(tol), int(max_iter), C.byref(S)))
+    return S.value
 
 
 def lqcd_profile_enable(h, on):
@@ -394,6 +419,22 @@ class Lattice:
                                              tol, max_iter, nbs=self.nbs)
         return x, it, rs
 
+    def w3eo(self, x_e, kappa, rho, dagger=0):
+        out = self.half()
+        lqcd_subblock_eo(self.h, out, x_e.contiguous(), kappa, rho, dagger, EO_APPLY, nbs=self.nbs)
+        return out
+
+    def solve_w3eo(self, b_e, kappa, rho, dagger=0, precision=PREC_F64, tol=1e-10, max_iter=10000):
+        x = self.half()
+        it = lqcd_subblock_eo(self.h, x, b_e.contiguous(), kappa, rho, dagger, EO_SOLVE, precision, tol, max_iter,
+                              nbs=self.nbs)
+        return x, it
+
+    def pf_force_eo(self, phi_e, kappa, rho, term, precision=PREC_F64, tol=1e-10, max_iter=20000, force=True):
+        F = self.momenta() if force else None
+        S = lqcd_pf_force_eo(self.h, F, phi_e.contiguous(), kappa, rho, term, precision, tol, max_iter)
+        return S, F
+
     def solve(self, b, kappa, dagger=0, precision=PREC_F64, tol=1e-10, max_iter=20000):
         x = self.spinor()
         it, rs = lqcd_solve_wilson(self.h, x, b.contiguous(), kappa, dagger, precision, tol, max_iter)
@@ -425,8 +466,8 @@ class Lattice:
         res = lqcd_hmc_trajectory(self.h, U2, prm, seed, traj, P0, eta1, eta2)
         return U2, res
 
-    def md(self, U, P, phi1, phi2, prm, phi3=None, phi4=None):
+    def md(self, U, P, phi1, phi2, prm, phi3=None, phi4=None, phi_s2=None, phi_s1=None):
         U2 = U.clone().contiguous()
         P2 = P.clone().contiguous()
-        lqcd_md(self.h, U2, P2, phi1, phi2, prm, phi3, phi4)
+        lqcd_md(self.h, U2, P2, prm, phi1, phi2, phi3, phi4, phi_s2, phi_s1)
         return U2, P2
