@@ -411,7 +411,8 @@ def run_iterated(args, W=WL_ITER):
                                precision=prec, tol=W["tol"], max_iter=W["max_iter"], level_w2=W["level_w2"],
                                level_schur2=W["level_schur2"], rho=W.get("rho", 0.0),
                                level_s2=W.get("level_s2", -1), level_s1=W.get("level_s1", -1),
-                               step_scheme=W.get("step_scheme", 0))
+                               step_scheme=W.get("step_scheme", 0),
+                               eo_solver=lqcd.SOLVER_SERIES if args.eo_solver == "series" else lqcd.SOLVER_BICGSTAB)
 
     prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     prm = params(prec)
@@ -463,7 +464,7 @@ def run_iterated(args, W=WL_ITER):
         "warmup": args.warmup, "precision": args.precision,
         "config": {"lattice": "x".join(map(str, L)), "l0": W["l0"], "l0s": W["l0s"], "kappa": W["kappa"],
                    "beta": W["beta"], "nsteps": W["nsteps"], "levels": W["levels"], "rho": W.get("rho"),
-                   "step_scheme": W.get("step_scheme", 0), "scheme": W["scheme"],
+                   "step_scheme": W.get("step_scheme", 0), "scheme": W["scheme"], "eo_solver": args.eo_solver,
                    "thermalisation": "%d pure-gauge trajectories from exp(i %.1f H)" % (W["therm"], W["eps"]),
                    "l2": "flushed between timed trajectories"},
         "solver": {"achieved_gbs": achieved, "peak": peak, "peak_kind": peak_kind,
@@ -545,6 +546,8 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f16", "f32", "f64"],
                     help="storage of the inner Krylov iterations (outer residuals stay double)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--eo-solver", default="bicgstab", choices=["bicgstab", "series"],
+                    help="inner iteration of the S2 / S1 solves (--case production)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

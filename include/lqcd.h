@@ -77,6 +77,7 @@ enum { LQCD_SCHUR_R = 0, LQCD_SCHUR_RDAG = 1, LQCD_SCHUR_RINV = 2, LQCD_SCHUR_RI
 enum { LQCD_TERM_W1 = 0, LQCD_TERM_SCHUR = 1, LQCD_TERM_W2 = 2, LQCD_TERM_SCHUR2 = 3,
        LQCD_TERM_S2 = 4, LQCD_TERM_S1 = 5 };
 enum { LQCD_EO_APPLY = 0, LQCD_EO_SOLVE = 1 };
+enum { LQCD_SOLVER_BICGSTAB = 0, LQCD_SOLVER_SERIES = 1 };
 enum { LQCD_MAX_LEVELS = 5 };
 enum { LQCD_LF = 0, LQCD_SW = 1 };
 
@@ -170,13 +171,17 @@ int lqcd_subblock_solve_batched(lqcd_t h, double* x, const double* b, double kap
  * W2's odd-odd block, det W2 = det W2,eo) and W3,eo = W2,eo + rho.
  * op LQCD_EO_APPLY: out = W3,eo in (dagger: W3,eo^dag in);
  * op LQCD_EO_SOLVE: out = W3,eo^-1 in (dagger: W3,eo^-dag in), every
- * sub-slab in one batched launch, relative residual <= tol; iters_out
+ * sub-slab in one batched launch, relative residual <= tol, inner
+ * iteration `method`: LQCD_SOLVER_BICGSTAB, or LQCD_SOLVER_SERIES, the
+ * geometric series sum_k (kappa^2 H_eo H_oe / (1+rho))^k / (1+rho) (Sec. 3,
+ * the solver of the block terms; it converges only when that operator's
+ * spectral radius is below one, else LQCD_ERR_NOCONVERGE); iters_out
  * (host int[L0/l0s], may be NULL) the inner iterations per sub-slab.
  * rho = 0 gives W2,eo.  in/out: even-site fields, the one-parity layout
  * above (double[V/2][4][3][2]).  Synchronous.  LQCD_ERR_STATE without
  * sub-slabs. */
 int lqcd_subblock_eo(lqcd_t h, double* out, const double* in, double kappa, double rho,
-                     int dagger, int op, int precision, double tol, int max_iter,
+                     int dagger, int op, int precision, int method, double tol, int max_iter,
                      int* iters_out);
 
 /* Solve M x = b (dagger: M^dag x = b) on the full lattice: even-odd reduced
@@ -286,6 +291,8 @@ typedef struct {
     double rho;
     int level_s2;
     int level_s1;
+    int eo_solver;      /* inner iteration of the S2 / S1 solves (W3,eo, W2,eo):
+                           LQCD_SOLVER_BICGSTAB or LQCD_SOLVER_SERIES */
 } lqcd_hmc_params;
 
 /* Pseudo-fermion fields of lqcd_md (device pointers, NULL where the term

@@ -88,6 +88,7 @@ struct SolveCfg {
     int prec;
     double tol;
     int max_iter;
+    int method = SOLVER_BICGSTAB;  // inner iteration of the W3,eo / W2,eo solves
 };
 
 // R, R^dag, R^-1, R^-dag on boundary coordinates (device doubles)
@@ -275,7 +276,7 @@ int w3eo_solve(lqcd_ctx* h, double2* x, const double2* b, double kappa, double r
         LQ_TRY(gamma5_full(h, fld(h, F_T2), b));
         bb = fld(h, F_T2);
     }
-    LQ_TRY(eo_solve(h, MODE_INTRA, -1, c.prec, kappa, x, bb, c.tol, c.max_iter, iters, resid, 1.0 + rho));
+    LQ_TRY(eo_solve(h, MODE_INTRA, -1, c.prec, kappa, x, bb, c.tol, c.max_iter, iters, resid, 1.0 + rho, c.method));
     if (dag) LQ_TRY(gamma5_full(h, x, x));
     return LQCD_OK;
 }
@@ -393,6 +394,10 @@ int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
         h->err = "hmc params: the W2 / R2 / S2 / S1 terms need sub-slabs (lqcd_set_subslabs)";
         return LQCD_ERR_STATE;
     }
+    if (p->eo_solver != LQCD_SOLVER_BICGSTAB && p->eo_solver != LQCD_SOLVER_SERIES) {
+        h->err = "hmc params: bad eo_solver";
+        return LQCD_ERR_ARG;
+    }
     if (!p->step_scale && p->step_scheme) {
         const int per[4] = {0, 6, 8, 16};
         if (p->step_scheme < 0 || p->step_scheme > 3 || h->g.L[0] % per[p->step_scheme]) {
@@ -454,6 +459,7 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
     const double dt = p.tau / p.nsteps[top];
     for (int i = 0; i < p.nsteps[top]; ++i) build_step(p, top, dt, ops);
     SolveCfg c{p.precision, p.tol, p.max_iter};
+    const SolveCfg ceo{p.precision, p.tol, p.max_iter, p.eo_solver};
     const double* ss = nullptr;
     LQ_TRY(md_scale_table(h, p, &ss));
     for (const Op& o : ops) {
@@ -479,11 +485,11 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
             ++*nforce;
         }
         if (p.level_s2 == o.level) {
-            LQ_TRY(pf_s2(h, P, pf.phi5, p.kappa, p.rho, -o.dt, c, nullptr, ss));
+            LQ_TRY(pf_s2(h, P, pf.phi5, p.kappa, p.rho, -o.dt, ceo, nullptr, ss));
             ++*nforce;
         }
         if (p.level_s1 == o.level) {
-            LQ_TRY(pf_s1(h, P, pf.phi6, p.kappa, p.rho, -o.dt, c, nullptr, ss));
+            LQ_TRY(pf_s1(h, P, pf.phi6, p.kappa, p.rho, -o.dt, ceo, nullptr, ss));
             ++*nforce;
         }
     }
@@ -519,8 +525,9 @@ int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, int base)
     if (p.level_schur >= 0) LQ_TRY(pf_schur(h, nullptr, pf.phi2, p.kappa, 0.0, c, e + 3));
     if (p.level_w2 >= 0) LQ_TRY(pf_w2(h, nullptr, pf.phi3, p.kappa, 0.0, c, e + 4));
     if (p.level_schur2 >= 0) LQ_TRY(pf_schur2(h, nullptr, pf.phi4, p.kappa, 0.0, c, e + 5));
-    if (p.level_s2 >= 0) LQ_TRY(pf_s2(h, nullptr, pf.phi5, p.kappa, p.rho, 0.0, c, e + 6));
-    if (p.level_s1 >= 0) LQ_TRY(pf_s1(h, nullptr, pf.phi6, p.kappa, p.rho, 0.0, c, e + 7));
+    const SolveCfg ceo{p.precision, p.tol, p.max_iter, p.eo_solver};
+    if (p.level_s2 >= 0) LQ_TRY(pf_s2(h, nullptr, pf.phi5, p.kappa, p.rho, 0.0, ceo, e + 6));
+    if (p.level_s1 >= 0) LQ_TRY(pf_s1(h, nullptr, pf.phi6, p.kappa, p.rho, 0.0, ceo, e + 7));
     return LQCD_OK;
 }
 
@@ -1036,7 +1043,7 @@ int lqcd_md(lqcd_t h, double* U, double* P, const lqcd_pf_fields* f, const lqcd_
 }
 
 int lqcd_subblock_eo(lqcd_t h, double* out, const double* in, double kappa, double rho, int dagger, int op,
-                     int precision, double tol, int max_iter, int* iters_out)
+                     int precision, int method, double tol, int max_iter, int* iters_out)
 {
     CHECK_H(h);
     NEED_GAUGE(h);
@@ -1054,7 +1061,8 @@ int lqcd_subblock_eo(lqcd_t h, double* out, const double* in, double kappa, doub
     } else {
         const int nbs = h->g1.L[0] / h->g1.l0s;
         std::vector<int> it(nbs, 0);
-        SolveCfg c{precision, tol, max_iter};
+        NEED(method == LQCD_SOLVER_BICGSTAB || method == LQCD_SOLVER_SERIES, "bad method");
+        SolveCfg c{precision, tol, max_iter, method};
         LQ_TRY(w3eo_solve(h, B, A, kappa, rho, dagger, c, it.data(), nullptr));
         if (iters_out)
             for (int k = 0; k < nbs; ++k) iters_out[k] = it[k];
@@ -1158,7 +1166,8 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
     if (p.level_s2 >= 0) {
         double2* et = fld(h, F_ETA1);
         LQ_TRY(rng_spinor(h, et, seed, 7, traj));
-        LQ_TRY(w3eo_solve(h, fld(h, F_G), et, p.kappa, p.rho, 0, c));
+        const SolveCfg ceo{p.precision, p.tol, p.max_iter, p.eo_solver};
+        LQ_TRY(w3eo_solve(h, fld(h, F_G), et, p.kappa, p.rho, 0, ceo));
         LQ_TRY(w3eo_apply(h, fld(h, F_PHI5), fld(h, F_G), p.kappa, 0.0, 0));
         LQ_TRY(norm2_dev(h, (const double*)et, (int64_t)24 * g.Vh, e0 + 6));
     }

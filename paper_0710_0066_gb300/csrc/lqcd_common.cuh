@@ -611,9 +611,12 @@ void solver_free(lqcd_ctx* h);
 // even-odd reduced solve (1 - kappa^2 H_eo H_oe) x_e = b_e on the slabs of
 // `colour` (block mode) or globally; x_e, b_e: double parity-0 views
 // `diag` replaces the 1 of the system: diag - kappa^2 H_eo H_oe (W3,eo = W2,eo + rho)
+// `method`: inner iteration, BiCGstab or the geometric series (which needs
+// the spectral radius of kappa^2 H_eo H_oe / diag below one)
+enum { SOLVER_BICGSTAB = 0, SOLVER_SERIES = 1 };
 int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e,
              const double2* b_e, double tol, int max_iter, int* iters_sys, double* resid_sys,
-             double diag = 1.0);
+             double diag = 1.0, int method = SOLVER_BICGSTAB);
 
 // force.cu
 // prec: PREC64 runs the link arithmetic in double, otherwise in single

@@ -38,6 +38,7 @@ struct SolveArgs {
     int mode;  // MODE_INTRA: slabs, MODE_ALL: whole lattice
     double k2;
     double diag;  // the system is diag - k2 H_eo H_oe (1, or 1 + rho for W3,eo)
+    int method;   // SOLVER_BICGSTAB or SOLVER_SERIES (inner iteration)
     int nsys, cps;
     int slab0, slabstep;
     int nsite;
@@ -345,6 +346,77 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             __syncthreads();
         }
 
+        if (A.method == SOLVER_SERIES) {
+            // ---- geometric series (Sec. 3, the solver of the block terms):
+            // p <- (r + k2 H_eo H_oe p) / diag from p = r; before an update
+            // the inner residual is r - A p = diag (p_new - p).  Two
+            // barriers per iteration.
+            const T k2 = (T)A.k2, dinv = (T)(1.0 / A.diag);
+            for (;;) {
+                const bool act = !S.idone;
+                if (act) FOR_SITES
+                    {
+                        const int i = base + j_;
+                        Spinor<T> a;
+                        hop_site<P, false>(A.g, A.mode, 0, 1, i, A.p, A.UP, a);
+                        store_spinor<P>(A.tmp, i, a);
+                    }
+                SYNC_OR_RETURN;
+                read_flags(A.iflag, A.nsys, &any_active, &worst);
+                if (!any_active) break;
+                double q = 0.0;
+                if (act) FOR_SITES
+                    {
+                        const int i = base + j_;
+                        Spinor<T> a, pp, rr;
+                        hop_site<P, false>(A.g, A.mode, 0, 0, i, A.tmp, A.UP, a);
+                        load_spinor<P, false>(A.p, i, pp);
+                        load_spinor<P, false>(A.r, i, rr);
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) a.c[s][c] = dinv * (rr.c[s][c] + k2 * a.c[s][c]);
+                        store_spinor<P>(A.p, i, a);
+                        if (P == PREC16) load_spinor<P, false>(A.p, i, a);
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) pp.c[s][c] = a.c[s][c] - pp.c[s][c];
+                        q += nrm_acc(pp);
+                    }
+                reduce_put(A, q, 0.0, 0.0, 1);
+                SYNC_OR_RETURN;
+                gather_own(A, sys, 1, red);
+                if (tid == 0 && act) {
+                    S.it += 1;
+                    S.itc += 1;
+                    const double res2 = A.diag * A.diag * red[0];
+                    if (!(res2 > S.itol2) || S.itc >= A.max_inner || S.it >= A.max_iter) S.idone = 1;
+                    // a series that grows (spectral radius above one) cannot
+                    // converge: report the system as not converged
+                    if (!isfinite(res2) || (S.itc >= 16 && res2 > 1e6)) {
+                        S.idone = 1;
+                        S.it = A.max_iter;
+                    }
+                }
+                if (leader) A.iflag[sys] = S.idone ? F_DONE : F_ACTIVE;
+                __syncthreads();
+            }
+            // e = p
+            if (S.active) FOR_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<T> pp;
+                    Spinor<TE> ee;
+                    load_spinor<P, false>(A.p, i, pp);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) ee.c[s][c] = mk((TE)pp.c[s][c].re, (TE)pp.c[s][c].im);
+                    store_spinor<PE>(A.e, i, ee);
+                }
+            SYNC_OR_RETURN;
+        } else
         // ---- BiCGstab: seven barriers per iteration
         for (;;) {
             const bool act = !S.idone;
@@ -725,17 +797,19 @@ void solver_free(lqcd_ctx* h)
 
 // algorithmic DRAM bytes per system site: one inner iteration and one outer
 // cycle (each vector and the eight links moved once per phase)
-static void solver_site_bytes(int prec, double* inner, double* outer)
+static void solver_site_bytes(int prec, int method, double* inner, double* outer)
 {
     const double sp = prec == PREC64 ? 192.0 : prec == PREC32 ? 96.0 : 52.0;
     const double lk = prec == PREC64 ? 1152.0 : prec == PREC32 ? 384.0 : 192.0;
     const double se = prec == PREC64 ? 192.0 : 96.0;
-    *inner = 24.0 * sp + 4.0 * lk + 2.0 * se;
+    // BiCGstab: 24 spinor passes, 4 half sweeps of links, solution r/w;
+    // series: p, tmp, tmp, r, p, p (6 passes), 2 half sweeps of links
+    *inner = method == SOLVER_SERIES ? 6.0 * sp + 2.0 * lk : 24.0 * sp + 4.0 * lk + 2.0 * se;
     *outer = (192.0 + 3.0 * sp + se) + (2.0 * 192.0 + se) + (2.0 * 192.0 + 1152.0) + (4.0 * 192.0 + 1152.0);
 }
 
 int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e, const double2* b_e,
-             double tol, int max_iter, int* iters_sys, double* resid_sys, double diag)
+             double tol, int max_iter, int* iters_sys, double* resid_sys, double diag, int method)
 {
     Work* w = h->work;
     const Geo& g = h->g;
@@ -744,6 +818,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.mode = mode;
     A.k2 = kappa * kappa;
     A.diag = diag;
+    A.method = method;
     if (mode == MODE_INTRA) {
         A.nsys = colour < 0 ? g.nb : g.nb / 2;
         A.slab0 = colour < 0 ? 0 : colour;
@@ -811,7 +886,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     const int st = w->h_status[0];
     const int nouter = w->h_status[1];
     double bi, bo;
-    solver_site_bytes(prec, &bi, &bo);
+    solver_site_bytes(prec, method, &bi, &bo);
     int64_t itsum = 0;
     for (int s = 0; s < A.nsys; ++s) {
         itsum += w->h_status[4 + s];

@@ -25,6 +25,7 @@ SCHUR_R, SCHUR_RDAG, SCHUR_RINV, SCHUR_RINVDAG = 0, 1, 2, 3
 SCHUR2_R, SCHUR2_RDAG, SCHUR2_RINV, SCHUR2_RINVDAG = 4, 5, 6, 7
 TERM_W1, TERM_SCHUR, TERM_W2, TERM_SCHUR2, TERM_S2, TERM_S1 = 0, 1, 2, 3, 4, 5
 EO_APPLY, EO_SOLVE = 0, 1
+SOLVER_BICGSTAB, SOLVER_SERIES = 0, 1
 MAX_LEVELS = 5
 LF, SW = 0, 1
 KERNEL_HOP, KERNEL_SOLVER, KERNEL_FORCE, KERNEL_GAUGE, KERNEL_BLAS = 0, 1, 2, 3, 4
@@ -48,7 +49,7 @@ class HmcParams(C.Structure):
         ("pf_init", C.c_int), ("roll", C.c_int), ("metropolis", C.c_int), ("precision", C.c_int),
         ("tol", C.c_double), ("max_iter", C.c_int), ("step_scheme", C.c_int), ("step_scale", C.c_void_p),
         ("level_w2", C.c_int), ("level_schur2", C.c_int),
-        ("rho", C.c_double), ("level_s2", C.c_int), ("level_s1", C.c_int),
+        ("rho", C.c_double), ("level_s2", C.c_int), ("level_s1", C.c_int), ("eo_solver", C.c_int),
     ]
 
 
@@ -68,14 +69,14 @@ class HmcResult(C.Structure):
 def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w1=0, level_schur=0,
                lam=1.0 / 6.0, pf_init=0, roll=0, metropolis=1, precision=PREC_F64, tol=1e-10,
                max_iter=20000, step_scheme=0, step_scale=None, level_w2=-1, level_schur2=-1, rho=0.0,
-               level_s2=-1, level_s1=-1):
+               level_s2=-1, level_s1=-1, eo_solver=SOLVER_BICGSTAB):
     """step_scale: None or a host float64 array (2, L0) of s(x0) (space-like,
     time-like rows); it is kept alive on the returned object"""
     sc = list(scheme) + [0] * (MAX_LEVELS - len(scheme))
     ns = list(nsteps) + [1] * (MAX_LEVELS - len(nsteps))
     p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * MAX_LEVELS)(*sc), (C.c_int * MAX_LEVELS)(*ns),
                   level_gauge, level_w1, level_schur, pf_init, roll, metropolis, precision, tol,
-                  max_iter, step_scheme, None, level_w2, level_schur2, rho, level_s2, level_s1)
+                  max_iter, step_scheme, None, level_w2, level_schur2, rho, level_s2, level_s1, eo_solver)
     if step_scale is not None:
         import numpy as np
 
@@ -114,7 +115,7 @@ def load():
         "lqcd_rng_normals": [vp, vp, i64, u64, u32, u32],
         "lqcd_hmc_trajectory": [vp, vp, vp, u64, u32, vp, vp, vp, vp],
         "lqcd_md": [vp, vp, vp, vp, vp],
-        "lqcd_subblock_eo": [vp, vp, vp, d, d, i, i, i, d, i, vp],
+        "lqcd_subblock_eo": [vp, vp, vp, d, d, i, i, i, i, d, i, vp],
         "lqcd_pf_force_eo": [vp, vp, vp, d, d, i, i, d, i, vp],
         "lqcd_set_subslabs": [vp, i],
         "lqcd_subblock_dslash": [vp, vp, vp, d, i, i, i],
@@ -284,10 +285,10 @@ def lqcd_md(h, U, P, prm, w1=None, schur=None, w2=None, schur2=None, s2=None, s1
 
 
 def lqcd_subblock_eo(h, out, inp, kappa, rho, dagger=0, op=EO_APPLY, precision=PREC_F64, tol=1e-10,
-                     max_iter=10000, nbs=128):
+                     max_iter=10000, nbs=128, method=SOLVER_BICGSTAB):
     it = (C.c_int * nbs)()
     _check(h, load().lqcd_subblock_eo(h, _ptr(out), _ptr(inp), float(kappa), float(rho), int(dagger), int(op),
-                                      int(precision), float(tol), int(max_iter), it))
+                                      int(precision), int(method), float(tol), int(max_iter), it))
     return list(it)
 
 
@@ -424,10 +425,11 @@ class Lattice:
         lqcd_subblock_eo(self.h, out, x_e.contiguous(), kappa, rho, dagger, EO_APPLY, nbs=self.nbs)
         return out
 
-    def solve_w3eo(self, b_e, kappa, rho, dagger=0, precision=PREC_F64, tol=1e-10, max_iter=10000):
+    def solve_w3eo(self, b_e, kappa, rho, dagger=0, precision=PREC_F64, tol=1e-10, max_iter=10000,
+                   method=SOLVER_BICGSTAB):
         x = self.half()
         it = lqcd_subblock_eo(self.h, x, b_e.contiguous(), kappa, rho, dagger, EO_SOLVE, precision, tol, max_iter,
-                              nbs=self.nbs)
+                              nbs=self.nbs, method=method)
         return x, it
 
     def pf_force_eo(self, phi_e, kappa, rho, term, precision=PREC_F64, tol=1e-10, max_iter=20000, force=True):

@@ -72,6 +72,39 @@ def test_w3eo_solve(setup, prec):
             assert rel(x, ref) < 1e-8
 
 
+@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16])
+def test_w3eo_geometric_series(setup, prec):
+    """the geometric series (Sec. 3) at kappa = 0.1, where the spectral
+    radius of kappa^2 H_eo H_oe / (1 + rho) is well below one"""
+    lat, olat, U, kappa, seed = setup
+    kappa = 0.1
+    b = syn.gaussian_spinor(olat.Vh, seed + 12)
+    for dagger in (0, 1):
+        x, it = lat.solve_w3eo(cuda(b), kappa, RHO, dagger, prec, tol=1e-10, method=lqcd.SOLVER_SERIES)
+        x = x.cpu().numpy()
+        r = b - olat.w3eo(U, kappa, RHO, x, dagger)
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(b), it[:olat.nbs]
+        xb, itb = lat.solve_w3eo(cuda(b), kappa, RHO, dagger, prec, tol=1e-10)
+        assert rel(x, xb.cpu().numpy()) < 1e-8
+        assert min(it[:olat.nbs]) > 0
+
+
+def test_w3eo_geometric_series_diverges_cleanly():
+    """kappa = 0.2 on a smooth field: the series grows, the solve returns
+    LQCD_ERR_NOCONVERGE and the handle stays usable"""
+    L = (8, 4, 4, 4)
+    U = syn.random_links(L, 0.1, 7)
+    lat = lqcd.Lattice(L, 4, -1, l0s=2)
+    lat.set_gauge(cuda(U))
+    b = cuda(syn.gaussian_spinor(lat.Vh, 8))
+    with pytest.raises(lqcd.LqcdError) as e:
+        lat.solve_w3eo(b, 0.2, 0.0, 0, lqcd.PREC_F32, tol=1e-10, method=lqcd.SOLVER_SERIES)
+    assert e.value.status == lqcd.ERR_NOCONVERGE
+    x, it = lat.solve_w3eo(b, 0.1, 0.0, 0, lqcd.PREC_F32, tol=1e-10)
+    assert torch.isfinite(x).all()
+    lat.close()
+
+
 @pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32])
 @pytest.mark.parametrize("term", ["s2", "s1"])
 def test_pf_force_massprec(setup, prec, term):
@@ -114,15 +147,18 @@ def test_md_five_levels_matches_oracle():
     lat.close()
 
 
-@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32])
-def test_hmc_trajectory_five_levels_matches_oracle(prec):
-    """kappa = 0.12 keeps the smooth field at positive quark mass"""
+@pytest.mark.parametrize("prec,method", [(lqcd.PREC_F64, lqcd.SOLVER_BICGSTAB), (lqcd.PREC_F32, lqcd.SOLVER_BICGSTAB),
+                                         (lqcd.PREC_F32, lqcd.SOLVER_SERIES)])
+def test_hmc_trajectory_five_levels_matches_oracle(prec, method):
+    """kappa = 0.12 keeps the smooth field at positive quark mass (and the
+    geometric series of W3,eo convergent)"""
     L, l0, kappa, beta = (8, 4, 4, 4), 4, 0.12, 5.6
     U = syn.random_links(L, 0.3, 51)
     lat = lqcd.Lattice(L, l0, -1, l0s=2)
     olat = O.Lattice(L, l0, -1, l0s=2)
     ns = [2, 2, 1, 1, 3]
-    prm = lqcd.hmc_params(beta, kappa, 0.4, 5, SCHEME5, ns, roll=1, precision=prec, tol=1e-11, **_levels5())
+    prm = lqcd.hmc_params(beta, kappa, 0.4, 5, SCHEME5, ns, roll=1, precision=prec, tol=1e-11, eo_solver=method,
+                          **_levels5())
     oprm = O.hmc_params(beta, kappa, 0.4, 5, SCHEME5, ns, roll=1, tol=1e-13, **_levels5())
     U1, res = lat.hmc_trajectory(cuda(U), prm, 2011, 6)
     Uo, ores, st = olat.hmc_trajectory(U, oprm, 2011, 6)
