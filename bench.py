@@ -56,6 +56,28 @@ def thermalise(lat, U, beta, ntraj, seed):
     return U, res
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
+# DRAM bytes per k_solve launch from the ncu capture summarised in
+# profiles/k_solve_16x16x16x32_f32.md, valid only for the solver source
+# that was captured (bench.py reports null once the source differs)
+SOLVER_TRAFFIC = dict(src_sha256="331f6fdee00e104490d706e3b21799edf5354b64adacde20e9ff5540795f3d34",
+                      block=(332.964096e6 + 276.233984e6), glob=(411.375360e6 + 456.867584e6))
+
+
+def solver_traffic():
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_0710_0066_gb300", "csrc", "lqcd_solver.cu")
+    try:
+        with open(path, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None, None
+    if sha != SOLVER_TRAFFIC["src_sha256"]:
+        return None, None
+    return SOLVER_TRAFFIC["block"], {"batched_slab_solve": SOLVER_TRAFFIC["block"],
+                                     "global_solve": SOLVER_TRAFFIC["glob"],
+                                     "source": "profiles/k_solve_16x16x16x32_f32.md"}
+
 
 def hbm_peak():
     try:
@@ -335,6 +357,7 @@ def run_ours(args):
 
     peak, peak_kind = hbm_peak()
     achieved = by_sol / ms_sol / 1e6 if ms_sol > 0 else None
+    traffic, traffic_detail = solver_traffic() if prec == lqcd.PREC_F32 else (None, None)
     line = {
         "metric": "s/HMC trajectory (16^3x32 Schwarz HMC, mixed precision batched)",
         "value": value, "unit": "s/trajectory", "n_gpus": world, "steps": args.steps,
@@ -346,7 +369,9 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": "persistent batched solver (k_solve)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_per_launch": traffic_detail,
+                     "alg_bytes_per_launch": by_sol / n_sol if n_sol else None,
                      "peak_kind": peak_kind, "launches": n_sol,
                      "kernel_share_of_step": ms_sol / total_ms if total_ms else None},
         "dslash": dslash,
