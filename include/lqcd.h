@@ -240,6 +240,14 @@ int lqcd_gauge_force(lqcd_t h, double* F, double beta, double* S_out, double* pl
  * F: device forces double[4][V][8] (e.g. from lqcd_pf_force).  Asynchronous. */
 int lqcd_force_profile(lqcd_t h, const double* F, double* out);
 
+/* T_U of Sec. 2 eq. (4) on its own: U_mu(x) <- exp(i dt P_mu(x)) U_mu(x)
+ * with P = sum_a P^a T^a (momenta layout), exponential by Cayley-Hamilton
+ * in double precision, then reunitarised.  U: device gauge field, updated
+ * in place; it also becomes the handle's gauge field.  Used by the
+ * autograd binding (actions as functions of Lie-algebra coordinates) and
+ * its finite-difference tests.  Synchronous. */
+int lqcd_link_update(lqcd_t h, double* U, const double* P, double dt);
+
 /* Philox4x32-10 normal deviates (Salmon et al., SC'11) as used by the HMC
  * heatbath: out[k] (device double[n]) for counter (k/2 lo, k/2 hi, stream,
  * traj) and key (seed lo, seed hi); two 53-bit uniforms per counter and

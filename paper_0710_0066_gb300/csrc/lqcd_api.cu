@@ -1003,6 +1003,18 @@ int lqcd_gauge_force(lqcd_t h, double* F, double beta, double* S_out, double* pl
     return LQCD_OK;
 }
 
+int lqcd_link_update(lqcd_t h, double* U, const double* P, double dt)
+{
+    CHECK_H(h);
+    NEED(U && P, "null U / P");
+    LQ_TRY(pack_gauge(h, U));
+    h->have_gauge = true;
+    LQ_TRY(update_links(h, P, dt));
+    LQ_TRY(unpack_gauge(h, U));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LQCD_OK;
+}
+
 int lqcd_rng_normals(lqcd_t h, double* out, int64_t n, uint64_t seed, uint32_t stream, uint32_t traj)
 {
     CHECK_H(h);

@@ -12,11 +12,11 @@
 // Reductions are per system, in double, in a fixed order (warp shuffles,
 // then the group's per-CTA partials summed in CTA order), so every CTA of a
 // group computes bitwise the same scalars and takes the same decisions.
-// Loop termination across systems is agreed through per-system state flags
-// that a group publishes before a barrier and every CTA reads after it.
-// The CTAs meet at a software grid barrier whose wait is bounded (about two
-// seconds): on time-out the kernel records LQCD_ERR_TIMEOUT and every CTA
-// returns.
+// The systems never wait for one another: a group meets only at its own
+// software barrier (one counter per system), loops until its own system has
+// converged and returns; the kernel ends when every group has.  The barrier
+// wait is bounded (about two seconds): on time-out the kernel records
+// LQCD_ERR_TIMEOUT and every CTA returns.
 #include <stdio.h>
 
 #include <algorithm>
@@ -51,9 +51,7 @@ struct SolveArgs {
     double tol, inner_tol;
     int max_iter, max_outer, max_inner;
     double* part;       // [NQ][grid]
-    int* iflag;         // [nsys] inner-loop state
-    int* oflag;         // [nsys] outer-loop state
-    unsigned* bar;
+    unsigned* bar;      // one barrier counter per system, BAR_STRIDE apart
     int* status;
     int* iters;         // [nsys]
     double* resid;      // [nsys]
@@ -63,8 +61,11 @@ struct SolveArgs {
 struct SysSt {  // the CTA's own system
     double bn2, rn2, rr, itol2;
     double2 rho, alpha, omega, beta;
-    int active, idone, it, itc;
+    int active, idone, it, itc, flag;
 };
+
+// barrier counters of different systems sit on different 128-byte lines
+constexpr int BAR_STRIDE = 32;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 {
@@ -73,18 +74,21 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
     return v;
 }
 
-__device__ bool grid_sync(const SolveArgs& A, unsigned& epoch)
+// barrier over the cps CTAs of one system (the systems are independent and
+// never wait for one another); bounded: gives up after SPIN_LIMIT cycles
+__device__ bool sys_sync(const SolveArgs& A, int sys, unsigned& epoch)
 {
     __shared__ int s_bad;
     __syncthreads();
     ++epoch;
     if (threadIdx.x == 0) {
-        const unsigned target = epoch * gridDim.x;
+        unsigned* bar = A.bar + (size_t)sys * BAR_STRIDE;
+        const unsigned target = epoch * (unsigned)A.cps;
         __threadfence();
-        atomicAdd(A.bar, 1u);
+        atomicAdd(bar, 1u);
         const long long t0 = clock64();
         int bad = 0;
-        while (ld_acquire(A.bar) < target) {
+        while (ld_acquire(bar) < target) {
             if (*(volatile int*)A.status == LQCD_ERR_TIMEOUT) { bad = 1; break; }
             if (clock64() - t0 > SPIN_LIMIT) {
                 atomicExch(A.status, LQCD_ERR_TIMEOUT);
@@ -100,8 +104,12 @@ __device__ bool grid_sync(const SolveArgs& A, unsigned& epoch)
     return s_bad == 0;
 }
 
-// CTA sum of up to three doubles -> part[q][cta]
-__device__ void reduce_put(const SolveArgs& A, double a, double b, double c, int nq)
+// CTA sum of up to three doubles -> part[rb][q][cta].  The partials are
+// double-buffered (rb alternates with every gather): a CTA that starts the
+// next reduction while a slower CTA of its system still reads the previous
+// one writes the other buffer, and the barrier inside every put / gather
+// pair keeps the reuse of a buffer two reductions later safe.
+__device__ void reduce_put(const SolveArgs& A, double a, double b, double c, int nq, int rb)
 {
     __shared__ double sh[NQ][SBS / 32];
 #pragma unroll
@@ -120,47 +128,24 @@ __device__ void reduce_put(const SolveArgs& A, double a, double b, double c, int
     if ((int)threadIdx.x < nq) {
         double v = 0.0;
         for (int k = 0; k < SBS / 32; ++k) v += sh[threadIdx.x][k];
-        A.part[threadIdx.x * gridDim.x + blockIdx.x] = v;
+        A.part[((size_t)rb * NQ + threadIdx.x) * gridDim.x + blockIdx.x] = v;
     }
 }
 
 // totals of the own system's partials: warp q sums quantity q
-__device__ void gather_own(const SolveArgs& A, int sys, int nq, double* out)
+__device__ void gather_own(const SolveArgs& A, int sys, int nq, double* out, int& rb)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w < nq) {
-        const double* p = A.part + (size_t)w * gridDim.x + (size_t)sys * A.cps;
+        const double* p = A.part + ((size_t)rb * NQ + w) * gridDim.x + (size_t)sys * A.cps;
         double v = 0.0;
         for (int c = lane; c < A.cps; c += 32) v += p[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) out[w] = v;
     }
+    rb ^= 1;
     __syncthreads();
-}
-
-// OR / max over the systems' flags (read by every CTA after a barrier)
-__device__ void read_flags(const int* flags, int nsys, int* any_active, int* worst)
-{
-    __shared__ int s_a, s_w;
-    if (threadIdx.x < 32) {
-        int a = 0, m = 0;
-        for (int s = threadIdx.x; s < nsys; s += 32) {
-            const int f = flags[s];
-            a |= (f == F_ACTIVE);
-            m = max(m, f);
-        }
-        a = __any_sync(0xffffffffu, a);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) {
-            s_a = a;
-            s_w = m;
-        }
-    }
-    __syncthreads();
-    *any_active = s_a;
-    *worst = s_w;
 }
 
 // per-site dot products in the storage arithmetic (T), accumulated over the
@@ -209,7 +194,7 @@ __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isf
 #define WORD_ADDR const size_t a = (size_t)(f_ / A.nsite) * A.g.Vh + base + (f_ % A.nsite)
 #define W4(f) ((float4*)(f).v)
 #define SYNC_OR_RETURN \
-    if (!grid_sync(A, epoch)) return
+    if (!sys_sync(A, sys, epoch)) return
 
 // y + a x for the two complex numbers of a word
 __device__ __forceinline__ float4 caxpy2(float2 a, float4 x, float4 y)
@@ -233,12 +218,12 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
     constexpr bool WORDS = (P == PREC32);
     const int cta = blockIdx.x, tid = threadIdx.x;
     const int sys = cta / A.cps, cin = cta - sys * A.cps;
-    const bool leader = (cin == 0 && tid == 0);  // publishes the system's flags
+    const bool leader = (cin == 0 && tid == 0);  // writes the system's results
     const int base = (A.mode == MODE_INTRA) ? (A.slab0 + sys * A.slabstep) * A.g.Sh : 0;
     __shared__ SysSt S;
     __shared__ double red[NQ];
     unsigned epoch = 0;
-    int any_active = 0, worst = 0;
+    int rb = 0;  // partial-sum buffer
 
     // ---- x = 0, r64 = b, |b|^2
     {
@@ -256,9 +241,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             store_spinor<PREC64>(A.x, i, z);
             q += nrm_acc(bb);
         }
-        reduce_put(A, q, 0.0, 0.0, 1);
+        reduce_put(A, q, 0.0, 0.0, 1, rb);
         SYNC_OR_RETURN;
-        gather_own(A, sys, 1, red);
+        gather_own(A, sys, 1, red, rb);
         if (tid == 0) {
             S.bn2 = red[0];
             S.rn2 = red[0];
@@ -269,21 +254,19 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 
     int outer = 0, final_flag = F_DONE;
     for (;;) {
-        // publish the system's state, then agree on continuing
+        // the system's state: every CTA of the system takes the same decision
+        // from the same gathered sums
         if (tid == 0) {
             const bool nan = !isfinite(S.rn2);
             const bool conv = !(S.rn2 > A.tol * A.tol * S.bn2) || !(S.bn2 > 0.0);
             S.active = (!nan && !conv) ? 1 : 0;
-            if (leader) {
-                int f = nan ? F_NAN : conv ? F_DONE : F_ACTIVE;
-                if (f == F_ACTIVE && (outer >= A.max_outer || S.it >= A.max_iter)) f = F_MAXIT;
-                A.oflag[sys] = f;
-            }
+            int f = nan ? F_NAN : conv ? F_DONE : F_ACTIVE;
+            if (f == F_ACTIVE && (outer >= A.max_outer || S.it >= A.max_iter)) f = F_MAXIT;
+            S.flag = f;
         }
-        SYNC_OR_RETURN;
-        read_flags(A.oflag, A.nsys, &any_active, &worst);
-        if (worst >= F_NAN || !any_active) {
-            final_flag = worst;
+        __syncthreads();
+        if (S.flag != F_ACTIVE) {
+            final_flag = S.flag;
             break;
         }
         ++outer;
@@ -331,9 +314,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                     q += nrm_acc(r);
                 }
             }
-            reduce_put(A, q, 0.0, 0.0, 1);
+            reduce_put(A, q, 0.0, 0.0, 1, rb);
             SYNC_OR_RETURN;
-            gather_own(A, sys, 1, red);
+            gather_own(A, sys, 1, red, rb);
             if (tid == 0) {
                 S.rho = make_double2(red[0], 0.0);
                 S.idone = !S.active;
@@ -341,7 +324,6 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                 const double need = 0.5 * A.tol * sqrt(S.bn2 / fmax(S.rn2, 1e-300));
                 const double it = fmax(A.inner_tol, need);
                 S.itol2 = it * it;
-                if (leader) A.iflag[sys] = S.idone ? F_DONE : F_ACTIVE;
             }
             __syncthreads();
         }
@@ -353,19 +335,17 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             // barriers per iteration.
             const T k2 = (T)A.k2, dinv = (T)(1.0 / A.diag);
             for (;;) {
-                const bool act = !S.idone;
-                if (act) FOR_SITES
-                    {
-                        const int i = base + j_;
-                        Spinor<T> a;
-                        hop_site<P, false>(A.g, A.mode, 0, 1, i, A.p, A.UP, a);
-                        store_spinor<P>(A.tmp, i, a);
-                    }
+                if (S.idone) break;
+                FOR_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<T> a;
+                    hop_site<P, false>(A.g, A.mode, 0, 1, i, A.p, A.UP, a);
+                    store_spinor<P>(A.tmp, i, a);
+                }
                 SYNC_OR_RETURN;
-                read_flags(A.iflag, A.nsys, &any_active, &worst);
-                if (!any_active) break;
                 double q = 0.0;
-                if (act) FOR_SITES
+                FOR_SITES
                     {
                         const int i = base + j_;
                         Spinor<T> a, pp, rr;
@@ -384,10 +364,10 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                             for (int c = 0; c < 3; ++c) pp.c[s][c] = a.c[s][c] - pp.c[s][c];
                         q += nrm_acc(pp);
                     }
-                reduce_put(A, q, 0.0, 0.0, 1);
+                reduce_put(A, q, 0.0, 0.0, 1, rb);
                 SYNC_OR_RETURN;
-                gather_own(A, sys, 1, red);
-                if (tid == 0 && act) {
+                gather_own(A, sys, 1, red, rb);
+                if (tid == 0) {
                     S.it += 1;
                     S.itc += 1;
                     const double res2 = A.diag * A.diag * red[0];
@@ -399,7 +379,6 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                         S.it = A.max_iter;
                     }
                 }
-                if (leader) A.iflag[sys] = S.idone ? F_DONE : F_ACTIVE;
                 __syncthreads();
             }
             // e = p
@@ -419,18 +398,17 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
         } else
         // ---- BiCGstab: seven barriers per iteration
         for (;;) {
-            const bool act = !S.idone;
+            if (S.idone) break;
+            const bool act = true;
             // tmp = H_oe p
-            if (act) FOR_SITES
-                {
-                    const int i = base + j_;
-                    Spinor<T> a;
-                    hop_site<P, false>(A.g, A.mode, 0, 1, i, A.p, A.UP, a);
-                    store_spinor<P>(A.tmp, i, a);
-                }
+            FOR_SITES
+            {
+                const int i = base + j_;
+                Spinor<T> a;
+                hop_site<P, false>(A.g, A.mode, 0, 1, i, A.p, A.UP, a);
+                store_spinor<P>(A.tmp, i, a);
+            }
             SYNC_OR_RETURN;
-            read_flags(A.iflag, A.nsys, &any_active, &worst);
-            if (!any_active) break;
             // v = p - k2 H_eo tmp ; <rh, v>
             {
                 double qr = 0.0, qi = 0.0;
@@ -452,9 +430,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                         cdot_acc(rh, a, qr, qi);
                     }
                 }
-                reduce_put(A, qr, qi, 0.0, 2);
+                reduce_put(A, qr, qi, 0.0, 2, rb);
                 SYNC_OR_RETURN;
-                gather_own(A, sys, 2, red);
+                gather_own(A, sys, 2, red, rb);
                 if (tid == 0 && act) {
                     const double2 d = make_double2(red[0], red[1]);
                     const double2 al = cdiv(S.rho, d);
@@ -522,9 +500,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                         qt += nrm_acc(a);
                     }
                 }
-                reduce_put(A, qr, qi, qt, 3);
+                reduce_put(A, qr, qi, qt, 3, rb);
                 SYNC_OR_RETURN;
-                gather_own(A, sys, 3, red);
+                gather_own(A, sys, 3, red, rb);
                 if (tid == 0 && act2) {
                     const double tt = red[2];
                     const double2 om = make_double2(red[0] / tt, red[1] / tt);
@@ -582,9 +560,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                         qn += nrm_acc(ss);
                     }
                 }
-                reduce_put(A, qr, qi, qn, 3);
+                reduce_put(A, qr, qi, qn, 3, rb);
                 SYNC_OR_RETURN;
-                gather_own(A, sys, 3, red);
+                gather_own(A, sys, 3, red, rb);
                 if (tid == 0 && act2) {
                     S.it += 1;
                     S.itc += 1;
@@ -600,7 +578,6 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                     }
                 }
                 if (tid == 0 && S.idone) S.idone = 1;
-                if (leader) A.iflag[sys] = S.idone ? F_DONE : F_ACTIVE;
                 __syncthreads();
             }
             // p = r + beta (p - omega v)
@@ -692,9 +669,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                     q += nrm_acc(a);
                 }
             }
-            reduce_put(A, q, 0.0, 0.0, 1);
+            reduce_put(A, q, 0.0, 0.0, 1, rb);
             SYNC_OR_RETURN;
-            gather_own(A, sys, 1, red);
+            gather_own(A, sys, 1, red, rb);
             if (tid == 0 && S.active) S.rn2 = red[0];
             __syncthreads();
         }
@@ -724,9 +701,8 @@ struct Work {
     double2* vec[8] = {nullptr};  // inner vectors, each sized for a double half field
     double2* r64 = nullptr;
     double2* t64 = nullptr;
-    double* part = nullptr;
-    int* flags = nullptr;         // [2][NSYS_MAX]
-    unsigned* bar = nullptr;
+    double* part = nullptr;       // [2][NQ][grid] double-buffered partial sums
+    unsigned* bar = nullptr;      // [NSYS_MAX][BAR_STRIDE] barrier counters
     int* status = nullptr;
     int* iters = nullptr;
     double* resid = nullptr;
@@ -763,9 +739,8 @@ int solver_init(lqcd_ctx* h)
         w->gmax[k] = std::max(1, occ[k]) * h->num_sms;
         gm = std::max(gm, w->gmax[k]);
     }
-    LQ_CUDA(h, cudaMalloc(&w->part, sizeof(double) * NQ * (size_t)gm));
-    LQ_CUDA(h, cudaMalloc(&w->flags, sizeof(int) * 2 * NSYS_MAX));
-    LQ_CUDA(h, cudaMalloc(&w->bar, sizeof(unsigned) * 4));
+    LQ_CUDA(h, cudaMalloc(&w->part, sizeof(double) * 2 * NQ * (size_t)gm));
+    LQ_CUDA(h, cudaMalloc(&w->bar, sizeof(unsigned) * BAR_STRIDE * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->status, sizeof(int) * 4));
     LQ_CUDA(h, cudaMalloc(&w->iters, sizeof(int) * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->resid, sizeof(double) * NSYS_MAX));
@@ -783,7 +758,6 @@ void solver_free(lqcd_ctx* h)
     cudaFree(w->r64);
     cudaFree(w->t64);
     cudaFree(w->part);
-    cudaFree(w->flags);
     cudaFree(w->bar);
     cudaFree(w->status);
     cudaFree(w->iters);
@@ -857,14 +831,12 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.max_outer = prec == PREC64 ? 8 : 40;
     A.max_inner = prec == PREC64 ? max_iter : prec == PREC32 ? 4000 : 600;
     A.part = w->part;
-    A.iflag = w->flags;
-    A.oflag = w->flags + NSYS_MAX;
     A.bar = w->bar;
     A.status = w->status;
     A.iters = w->iters;
     A.resid = w->resid;
     A.outer_out = w->outer;
-    LQ_CUDA(h, cudaMemsetAsync(w->bar, 0, sizeof(unsigned) * 4, h->stream));
+    LQ_CUDA(h, cudaMemsetAsync(w->bar, 0, sizeof(unsigned) * BAR_STRIDE * A.nsys, h->stream));
     LQ_CUDA(h, cudaMemsetAsync(w->status, 0, sizeof(int) * 4, h->stream));
     void* args[] = {&A};
     const void* fn = prec == PREC64 ? (const void*)k_solve<PREC64>

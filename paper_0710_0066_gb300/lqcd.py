@@ -37,7 +37,7 @@ EXPORTS = [
     "lqcd_gauge_force", "lqcd_rng_normals", "lqcd_hmc_trajectory", "lqcd_md",
     "lqcd_profile_enable", "lqcd_profile_reset", "lqcd_profile_read", "lqcd_launch_count",
     "lqcd_gauge_action_static", "lqcd_force_profile", "lqcd_set_subslabs", "lqcd_subblock_dslash",
-    "lqcd_subblock_solve_batched", "lqcd_subblock_eo", "lqcd_pf_force_eo",
+    "lqcd_subblock_solve_batched", "lqcd_subblock_eo", "lqcd_pf_force_eo", "lqcd_link_update",
 ]
 
 
@@ -118,6 +118,7 @@ def load():
         "lqcd_subblock_eo": [vp, vp, vp, d, d, i, i, i, i, d, i, vp],
         "lqcd_pf_force_eo": [vp, vp, vp, d, d, i, i, d, i, vp],
         "lqcd_set_subslabs": [vp, i],
+        "lqcd_link_update": [vp, vp, vp, d],
         "lqcd_subblock_dslash": [vp, vp, vp, d, i, i, i],
         "lqcd_subblock_solve_batched": [vp, vp, vp, d, i, i, i, d, i, vp, vp],
         "lqcd_profile_enable": [vp, i],
@@ -217,6 +218,10 @@ def lqcd_block_solve_batched(h, x, b, kappa, colour=-1, dagger=0, precision=PREC
                                               int(dagger), int(precision), float(tol), int(max_iter),
                                               it, rs))
     return list(it), list(rs)
+
+
+def lqcd_link_update(h, U, P, dt):
+    return _check(h, load().lqcd_link_update(h, _ptr(U), _ptr(P), float(dt)))
 
 
 def lqcd_set_subslabs(h, l0s):
@@ -462,6 +467,12 @@ class Lattice:
         F = self.momenta() if force else None
         S, pl = lqcd_gauge_force(self.h, F, beta)
         return S, pl, F
+
+    def link_update(self, U, P, dt):
+        """exp(i dt P) U (a new tensor); it also becomes the handle's field"""
+        U2 = U.clone().contiguous()
+        lqcd_link_update(self.h, U2, P.contiguous(), dt)
+        return U2
 
     def hmc_trajectory(self, U, prm, seed, traj, P0=None, eta1=None, eta2=None):
         U2 = U.clone().contiguous()
