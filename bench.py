@@ -225,11 +225,16 @@ def run_ours(args):
     lat = lqcd.Lattice(L, l0, -1)
     U0 = syn.random_links_torch(L, WL["eps"], WL["seed"] + rank, "cuda").contiguous()
     U0, rth = thermalise(lat, U0, WL["beta"], WL["therm"], WL["seed"] + rank)
+    # launch schedules measured on this lattice and field (outside the timed region)
+    lat.set_gauge(U0)
+    lqcd.lqcd_autotune(lat.h, 3, WL["kappa"])
+    tune = lqcd.lqcd_tune_read(lat.h)
 
     def params(prec):
         return lqcd.hmc_params(WL["beta"], WL["kappa"], WL["tau"], WL["nlevels"], WL["scheme"], WL["nsteps"],
                                WL["level_gauge"], WL["level_w1"], WL["level_schur"], lam=WL["lam"], roll=1,
-                               metropolis=1, precision=prec, tol=WL["tol"], max_iter=WL["max_iter"])
+                               metropolis=1, precision=prec, tol=WL["tol"], max_iter=WL["max_iter"],
+                               use_graph=0 if args.no_graph else 1)
 
     prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     prm = params(prec)
@@ -316,16 +321,28 @@ def run_ours(args):
         Ud_ = syn.random_links_torch(DSLASH_L, WL["eps"], WL["seed"] + 7, "cuda").contiguous()
         latd.set_gauge(Ud_)
         del Ud_
+        lqcd.lqcd_autotune(latd.h, 1, 0.0)
         x = torch.randn((latd.Vh, 4, 3), dtype=torch.complex128, device="cuda")
         for name, pr in (("f32", lqcd.PREC_F32), ("f16", lqcd.PREC_F16), ("f64", lqcd.PREC_F64)):
-            latd.dslash_eo(x, 0, 0.0, 0, lqcd.OP_HOP, pr)
+            # the k_hop launch alone, timed by the library's CUDA events
+            # around each of 100 launches queued back to back (the layout
+            # conversions of each call run between them); one launch moves
+            # 0.3 GB (f16) to 1.6 GB (f64), far more than the 129 MB L2, so
+            # every launch streams from HBM; median reported
+            for _ in range(5):
+                latd.dslash_eo(x, 0, 0.0, 0, lqcd.OP_HOP, pr)
             lqcd.lqcd_profile_reset(latd.h)
             lqcd.lqcd_profile_enable(latd.h, 1 << lqcd.KERNEL_HOP)
-            for _ in range(10):
+            for _ in range(100):
                 latd.dslash_eo(x, 0, 0.0, 0, lqcd.OP_HOP, pr)
             n, ms, by = lqcd.lqcd_profile_read(latd.h, lqcd.KERNEL_HOP)
+            per = lqcd.lqcd_profile_times(latd.h, lqcd.KERNEL_HOP)
             lqcd.lqcd_profile_enable(latd.h, 0)
-            dslash[name] = {"gbs": by / ms / 1e6, "ms": ms / n, "bytes_per_launch": by / n}
+            med = statistics.median(per)
+            dslash[name] = {"gbs": by / n / med / 1e6, "ms_median": med, "ms_min": min(per),
+                            "bytes_per_launch": by / n, "launches": len(per),
+                            "frac_of_peak": by / n / med / 1e6 / hbm_peak()[0]}
+        dslash["hop_block_size"] = lqcd.lqcd_tune_read(latd.h)["hop_block_size"]
         latd.close()
 
     # ---- force-profile diagnostic (Sec. 3, Fig. 1) on the thermalised field:
@@ -366,7 +383,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "lattice": "x".join(map(str, L)), "l0": l0,
                    "inner_precision": args.precision, "l2": "flushed between timed trajectories",
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "parallelism": "replicas" if world > 1 else "1 GPU", "autotune": tune,
+                   "md_as_cuda_graph": not args.no_graph},
         "roofline": {"bound": "hbm", "kernel": "persistent batched solver (k_solve)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -429,6 +447,9 @@ def run_iterated(args, W=WL_ITER):
     lat = lqcd.Lattice(L, W["l0"], -1, l0s=W["l0s"])
     U0 = syn.random_links_torch(L, W["eps"], W["seed"], "cuda").contiguous()
     U0, rth = thermalise(lat, U0, W["beta"], W["therm"], W["seed"])
+    lat.set_gauge(U0)
+    lqcd.lqcd_autotune(lat.h, 3, W["kappa"])
+    tune = lqcd.lqcd_tune_read(lat.h)
 
     def params(prec):
         return lqcd.hmc_params(W["beta"], W["kappa"], W["tau"], W["nlevels"], W["scheme"], W["nsteps"],
@@ -437,7 +458,8 @@ def run_iterated(args, W=WL_ITER):
                                level_schur2=W["level_schur2"], rho=W.get("rho", 0.0),
                                level_s2=W.get("level_s2", -1), level_s1=W.get("level_s1", -1),
                                step_scheme=W.get("step_scheme", 0),
-                               eo_solver=lqcd.SOLVER_SERIES if args.eo_solver == "series" else lqcd.SOLVER_BICGSTAB)
+                               eo_solver=lqcd.SOLVER_SERIES if args.eo_solver == "series" else lqcd.SOLVER_BICGSTAB,
+                               use_graph=0 if args.no_graph else 1)
 
     prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     prm = params(prec)
@@ -491,6 +513,7 @@ def run_iterated(args, W=WL_ITER):
                    "beta": W["beta"], "nsteps": W["nsteps"], "levels": W["levels"], "rho": W.get("rho"),
                    "step_scheme": W.get("step_scheme", 0), "scheme": W["scheme"], "eo_solver": args.eo_solver,
                    "thermalisation": "%d pure-gauge trajectories from exp(i %.1f H)" % (W["therm"], W["eps"]),
+                   "autotune": tune,
                    "l2": "flushed between timed trajectories"},
         "solver": {"achieved_gbs": achieved, "peak": peak, "peak_kind": peak_kind,
                    "frac": (achieved / peak) if achieved else None, "launches": n_sol,
@@ -576,6 +599,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="run the molecular dynamics eagerly instead of replaying it as a CUDA graph")
     args = ap.parse_args()
     if args.case:
         run_case(args)

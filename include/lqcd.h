@@ -301,6 +301,12 @@ typedef struct {
     int level_s1;
     int eo_solver;      /* inner iteration of the S2 / S1 solves (W3,eo, W2,eo):
                            LQCD_SOLVER_BICGSTAB or LQCD_SOLVER_SERIES */
+    int use_graph;      /* 1: lqcd_hmc_trajectory runs the molecular dynamics
+                           as a CUDA graph, recorded the first time for a
+                           parameter set (not run then) and replayed; the
+                           solves inside report failures once, after the
+                           replay.  Same kernels in the same order: the
+                           results equal the eager run's. */
 } lqcd_hmc_params;
 
 /* Pseudo-fermion fields of lqcd_md (device pointers, NULL where the term
@@ -356,6 +362,25 @@ int lqcd_md(lqcd_t h, double* U, double* P, const lqcd_pf_fields* f, const lqcd_
 int lqcd_profile_enable(lqcd_t h, int enable);
 int lqcd_profile_reset(lqcd_t h);
 int lqcd_profile_read(lqcd_t h, int kernel_id, int64_t* launches, double* ms, double* bytes);
+/* The individual device times (ms) of the launches of kernel_id recorded
+ * since the last reset, in launch order: up to cap of them into ms_out
+ * (host float[cap]); *n_out (host) receives how many were recorded (at most
+ * 65536 are kept).  Synchronises the stream. */
+int lqcd_profile_times(lqcd_t h, int kernel_id, float* ms_out, int64_t cap, int64_t* n_out);
+
+/* Launch schedules picked by measurement on this handle's lattice and
+ * gauge field (the paper has no counterpart; its code ran on CPUs):
+ * what & 1: threads per block of the hopping sweep (64 / 128 / 256), per
+ * storage precision; what & 2: sites per thread of the persistent solver
+ * (1 / 2 / 4, i.e. CTAs per system), per precision, separately for the
+ * batched slab solve and the global solve, each candidate timed on a
+ * solve at `kappa` to 1e-10.  The choices stay with the handle; results
+ * are the same up to rounding for every choice.  Synchronous.
+ * lqcd_tune_read fills out (host int[9]) with hop block size [F64, F32,
+ * F16], slab-solve sites per thread [F64, F32, F16], global-solve sites
+ * per thread [F64, F32, F16]. */
+int lqcd_autotune(lqcd_t h, int what, double kappa);
+int lqcd_tune_read(lqcd_t h, int* out);
 
 /* Number of kernels this handle has launched since lqcd_create (host
  * counter; *count is a host int64). */

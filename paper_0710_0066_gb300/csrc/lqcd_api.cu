@@ -394,6 +394,10 @@ int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
         h->err = "hmc params: the W2 / R2 / S2 / S1 terms need sub-slabs (lqcd_set_subslabs)";
         return LQCD_ERR_STATE;
     }
+    if (p->use_graph != 0 && p->use_graph != 1) {
+        h->err = "hmc params: use_graph must be 0 or 1";
+        return LQCD_ERR_ARG;
+    }
     if (p->eo_solver != LQCD_SOLVER_BICGSTAB && p->eo_solver != LQCD_SOLVER_SERIES) {
         h->err = "hmc params: bad eo_solver";
         return LQCD_ERR_ARG;
@@ -452,7 +456,8 @@ struct PfFields {
     const double2* phi6;
 };
 
-int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, int* nforce)
+// the molecular dynamics of eqs. (5)-(7); ss: device step-size table or null
+int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, int* nforce, const double* ss)
 {
     std::vector<Op> ops;
     const int top = p.nlevels - 1;
@@ -460,8 +465,6 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
     for (int i = 0; i < p.nsteps[top]; ++i) build_step(p, top, dt, ops);
     SolveCfg c{p.precision, p.tol, p.max_iter};
     const SolveCfg ceo{p.precision, p.tol, p.max_iter, p.eo_solver};
-    const double* ss = nullptr;
-    LQ_TRY(md_scale_table(h, p, &ss));
     for (const Op& o : ops) {
         if (o.kind == 1) {
             LQ_TRY(update_links(h, P, o.dt, ss));
@@ -494,6 +497,86 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
         }
     }
     return LQCD_OK;
+}
+
+// the parameters a recorded MD graph depends on (the step table by value)
+std::vector<unsigned char> md_key(const lqcd_ctx* h, const lqcd_hmc_params& p)
+{
+    std::vector<double> k = {p.beta, p.kappa, p.tau, p.lambda, (double)p.nlevels, (double)p.level_gauge,
+                             (double)p.level_w1, (double)p.level_schur, (double)p.level_w2, (double)p.level_schur2,
+                             (double)p.level_s2, (double)p.level_s1, p.rho, (double)p.precision, p.tol,
+                             (double)p.max_iter, (double)p.eo_solver, (double)p.step_scheme};
+    for (int j = 0; j < LQCD_MAX_LEVELS; ++j) {
+        k.push_back((double)p.scheme[j]);
+        k.push_back((double)p.nsteps[j]);
+    }
+    if (p.step_scale)
+        for (int t = 0; t < 2 * h->g.L[0]; ++t) k.push_back(p.step_scale[t]);
+    std::vector<unsigned char> out(k.size() * sizeof(double));
+    memcpy(out.data(), k.data(), out.size());
+    return out;
+}
+
+// the molecular dynamics as a CUDA graph: recorded (not run) the first time
+// for a parameter set, then replayed; the solves inside report their status
+// and iteration counts through device memory, read once after the replay
+int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const double* ss, int* nforce)
+{
+    std::vector<unsigned char> key = md_key(h, p);
+    if (!h->md_exec || key != h->md_key) {
+        if (h->md_exec) {
+            cudaGraphExecDestroy(h->md_exec);
+            h->md_exec = nullptr;
+        }
+        if (!h->cap_stream) LQ_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t user = h->stream;
+        const int64_t l0 = h->launches;
+        const int s0 = h->solve_count;
+        h->stream = h->cap_stream;
+        h->deferred = true;
+        h->capturing = true;
+        cudaError_t eb = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        int nf = 0;
+        int st = eb == cudaSuccess ? do_md(h, p, h->P, pf, &nf, ss) : LQCD_OK;
+        cudaGraph_t graph = nullptr;
+        cudaError_t ee = eb == cudaSuccess ? cudaStreamEndCapture(h->cap_stream, &graph) : eb;
+        h->stream = user;
+        h->deferred = false;
+        h->capturing = false;
+        const int64_t nl = h->launches - l0;
+        const int ns = h->solve_count - s0;
+        h->launches = l0;
+        h->solve_count = s0;
+        if (st != LQCD_OK || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (st == LQCD_OK) {
+                h->err = std::string("recording the MD graph: ") + cudaGetErrorString(ee);
+                st = LQCD_ERR_CUDA;
+            }
+            return st;
+        }
+        cudaError_t ei = cudaGraphInstantiate(&h->md_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            h->md_exec = nullptr;
+            h->err = std::string("instantiating the MD graph: ") + cudaGetErrorString(ei);
+            return LQCD_ERR_CUDA;
+        }
+        h->md_key = key;
+        h->md_launches = nl;
+        h->md_nforce = nf;
+        h->md_solves = ns;
+    }
+    LQ_TRY(solver_collect(h, nullptr, nullptr));  // clears what eager solves left
+    LQ_CUDA(h, cudaGraphLaunch(h->md_exec, h->stream));
+    h->launches += h->md_launches;
+    h->solve_count += h->md_solves;
+    *nforce += h->md_nforce;
+    int64_t it = 0, sit = 0;
+    const int st = solver_collect(h, &it, &sit);
+    h->iter_count += it;
+    h->site_iters += sit;
+    return st;
 }
 
 // host Philox4x32-10 for the Metropolis uniform and the x0 shift
@@ -580,7 +663,7 @@ GaugeF gauge_view(lqcd_ctx* h, int prec)
 void prof_begin(lqcd_ctx* h, int id, cudaEvent_t* a)
 {
     *a = nullptr;
-    if (!(h->prof.on & (1u << id))) return;
+    if (!(h->prof.on & (1u << id)) || h->capturing) return;
     if (h->prof.pool.empty()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -593,7 +676,7 @@ void prof_begin(lqcd_ctx* h, int id, cudaEvent_t* a)
 
 void prof_end(lqcd_ctx* h, int id, cudaEvent_t a, double bytes)
 {
-    if (!(h->prof.on & (1u << id)) || !a) return;
+    if (!(h->prof.on & (1u << id)) || !a || h->capturing) return;
     cudaEvent_t b;
     if (h->prof.pool.empty()) {
         if (cudaEventCreate(&b) != cudaSuccess) return;
@@ -615,6 +698,7 @@ static void prof_flush(lqcd_ctx* h)
         h->prof.launches[r.id] += 1;
         h->prof.ms[r.id] += ms;
         h->prof.bytes[r.id] += r.bytes;
+        if (h->prof.hist[r.id].size() < 65536) h->prof.hist[r.id].push_back(ms);
         h->prof.pool.push_back(r.a);
         h->prof.pool.push_back(r.b);
     }
@@ -699,6 +783,8 @@ int lqcd_destroy(lqcd_t h)
     if (!h) return LQCD_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    if (h->md_exec) cudaGraphExecDestroy(h->md_exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     solver_free(h);
     cudaFree(h->U64);
     cudaFree(h->U64_save);
@@ -1048,7 +1134,9 @@ int lqcd_md(lqcd_t h, double* U, double* P, const lqcd_pf_fields* f, const lqcd_
     if (prm->level_s1 >= 0) LQ_TRY(pack_spinor(h, fld(h, F_PHI6), f->s1, 0, 1));
     int nf = 0;
     const PfFields pf{fld(h, F_PHI1), h->bnd[0], fld(h, F_PHI3), h->bnd[3], fld(h, F_PHI5), fld(h, F_PHI6)};
-    LQ_TRY(do_md(h, *prm, P, pf, &nf));
+    const double* ss = nullptr;
+    LQ_TRY(md_scale_table(h, *prm, &ss));
+    LQ_TRY(do_md(h, *prm, P, pf, &nf, ss));
     LQ_TRY(unpack_gauge(h, U));
     LQ_CUDA(h, cudaStreamSynchronize(h->stream));
     return LQCD_OK;
@@ -1191,7 +1279,10 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
     }
     int nforce = 0;
     const PfFields pf{fld(h, F_PHI1), h->bnd[0], fld(h, F_PHI3), h->bnd[3], fld(h, F_PHI5), fld(h, F_PHI6)};
-    LQ_TRY(do_md(h, p, h->P, pf, &nforce));
+    const double* ss = nullptr;
+    LQ_TRY(md_scale_table(h, p, &ss));
+    if (p.use_graph) LQ_TRY(md_graph(h, p, pf, ss, &nforce));
+    else LQ_TRY(do_md(h, p, h->P, pf, &nforce, ss));
     LQ_TRY(energy(h, p, pf, NTERM));
     double e[2 * NTERM];
     LQ_TRY(read_scalars(h, 2 * NTERM, e));
@@ -1239,6 +1330,117 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
     return LQCD_OK;
 }
 
+int lqcd_autotune(lqcd_t h, int what, double kappa)
+{
+    CHECK_H(h);
+    NEED_GAUGE(h);
+    NEED(what >= 1 && what <= 3, "what: 1 hopping sweep, 2 solver, 3 both");
+    const int Vh = h->g.Vh;
+    double2 *A = fld(h, F_A), *B = fld(h, F_B);
+    LQ_TRY(rng_spinor(h, A, 0x5eedULL, 9, 0));
+    cudaEvent_t e0, e1;
+    LQ_CUDA(h, cudaEventCreate(&e0));
+    LQ_CUDA(h, cudaEventCreate(&e1));
+    int st = LQCD_OK;
+    if (what & 1) {
+        // k_hop: threads per block, per storage precision, timed on this lattice
+        const int cand[3] = {64, 128, 256};
+        for (int prec = 0; prec < 3 && st == LQCD_OK; ++prec) {
+            SpinorF in = sp64(A, 1, Vh), out = sp64(B, 0, Vh);
+            if (prec != PREC64) {
+                auto lowview = [&](double2* buf, int par) {
+                    SpinorF f;
+                    f.v = (char*)buf + (size_t)par * 12 * Vh * sizeof(double2);
+                    f.N = Vh;
+                    f.nrm = prec == PREC16 ? (float*)((uint4*)f.v + (size_t)3 * Vh) : nullptr;
+                    return f;
+                };
+                in = lowview(fld(h, F_C), 1);
+                out = lowview(fld(h, F_D), 0);
+                st = convert_spinor(h, in, prec, sp64(A, 1, Vh), PREC64, Vh);
+            }
+            // candidates interleaved over four rounds, the minimum per
+            // candidate kept; the default stays unless another is 2 % faster
+            const int def = h->tune.hop_bs[prec];
+            float tmin[3] = {1e30f, 1e30f, 1e30f};
+            for (int round = 0; round < 4 && st == LQCD_OK; ++round)
+                for (int k = 0; k < 3 && st == LQCD_OK; ++k) {
+                    h->tune.hop_bs[prec] = cand[k];
+                    st = hop_sweep(h, prec, MODE_ALL, 0, 0, -1, out, in, 0.0, none(), 1.0);  // warm-up
+                    cudaEventRecord(e0, h->stream);
+                    for (int r = 0; r < 5 && st == LQCD_OK; ++r)
+                        st = hop_sweep(h, prec, MODE_ALL, 0, 0, -1, out, in, 0.0, none(), 1.0);
+                    cudaEventRecord(e1, h->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    tmin[k] = std::min(tmin[k], ms);
+                }
+            int pick = def;
+            float tdef = 1e30f;
+            for (int k = 0; k < 3; ++k)
+                if (cand[k] == def) tdef = tmin[k];
+            float best = tdef;
+            for (int k = 0; k < 3; ++k)
+                if (tmin[k] < 0.98f * tdef && tmin[k] < best) {
+                    best = tmin[k];
+                    pick = cand[k];
+                }
+            h->tune.hop_bs[prec] = pick;
+        }
+    }
+    if ((what & 2) && st == LQCD_OK) {
+        // k_solve: sites per thread (CTAs per system), per precision, for the
+        // batched slab solve and the global solve, timed on this lattice
+        const int cand[3] = {1, 2, 4};
+        for (int prec = 0; prec < 3 && st == LQCD_OK; ++prec)
+            for (int kind = 0; kind < 2 && st == LQCD_OK; ++kind) {
+                // candidates interleaved over two rounds, the minimum per
+                // candidate kept; the default stays unless another is 3 % faster
+                const int def = h->tune.solve_spt[prec][kind];
+                double tmin[3] = {1e30, 1e30, 1e30};
+                for (int round = 0; round < 2 && st == LQCD_OK; ++round)
+                    for (int k = 0; k < 3 && st == LQCD_OK; ++k) {
+                        h->tune.solve_spt[prec][kind] = cand[k];
+                        cudaEventRecord(e0, h->stream);
+                        st = solve_full(h, kind == 0 ? MODE_INTRA : MODE_ALL, -1, 0, prec, kappa, B, A, 1e-10, 20000,
+                                        nullptr, nullptr);
+                        cudaEventRecord(e1, h->stream);
+                        cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        tmin[k] = std::min(tmin[k], (double)ms);
+                    }
+                int pick = def;
+                double tdef = 1e30;
+                for (int k = 0; k < 3; ++k)
+                    if (cand[k] == def) tdef = tmin[k];
+                double best = tdef;
+                for (int k = 0; k < 3; ++k)
+                    if (tmin[k] < 0.97 * tdef && tmin[k] < best) {
+                        best = tmin[k];
+                        pick = cand[k];
+                    }
+                h->tune.solve_spt[prec][kind] = pick;
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+int lqcd_tune_read(lqcd_t h, int* out)
+{
+    CHECK_H(h);
+    NEED(out, "null output");
+    for (int p = 0; p < 3; ++p) {
+        out[p] = h->tune.hop_bs[p];
+        out[3 + p] = h->tune.solve_spt[p][0];
+        out[6 + p] = h->tune.solve_spt[p][1];
+    }
+    return LQCD_OK;
+}
+
 int lqcd_profile_enable(lqcd_t h, int enable)
 {
     CHECK_H(h);
@@ -1255,6 +1457,7 @@ int lqcd_profile_reset(lqcd_t h)
         h->prof.launches[k] = 0;
         h->prof.ms[k] = 0.0;
         h->prof.bytes[k] = 0.0;
+        h->prof.hist[k].clear();
     }
     return LQCD_OK;
 }
@@ -1271,6 +1474,18 @@ int lqcd_launch_count(lqcd_t h, int64_t* count)
     CHECK_H(h);
     if (!count) return LQCD_ERR_ARG;
     *count = h->launches;
+    return LQCD_OK;
+}
+
+int lqcd_profile_times(lqcd_t h, int id, float* ms_out, int64_t cap, int64_t* n_out)
+{
+    CHECK_H(h);
+    if (id < 0 || id > 4 || !n_out || (cap > 0 && !ms_out)) return LQCD_ERR_ARG;
+    prof_flush(h);
+    const std::vector<float>& v = h->prof.hist[id];
+    const int64_t n = std::min<int64_t>(cap, (int64_t)v.size());
+    for (int64_t k = 0; k < n; ++k) ms_out[k] = v[k];
+    *n_out = (int64_t)v.size();
     return LQCD_OK;
 }
 

@@ -499,9 +499,16 @@ struct Profiler {
     int64_t launches[5] = {0, 0, 0, 0, 0};
     double ms[5] = {0, 0, 0, 0, 0};
     double bytes[5] = {0, 0, 0, 0, 0};
+    std::vector<float> hist[5];  // per-launch device times since the last reset
 };
 
 struct Work;  // solver workspace (lqcd_solver.cu)
+
+// launch schedules picked by lqcd_autotune (defaults until it runs)
+struct Tune {
+    int hop_bs[3] = {128, 128, 128};           // k_hop threads per block, per precision
+    int solve_spt[3][2] = {{1, 1}, {1, 1}, {1, 1}};  // k_solve sites per thread [prec][block, global]
+};
 
 struct lqcd_ctx {
     Geo g;   // active geometry (level 1, or level 2 inside a GeoScope)
@@ -530,8 +537,18 @@ struct lqcd_ctx {
     int red_blocks = 0;
     Work* work = nullptr;
     Profiler prof;
+    Tune tune;
     double* d_sscale = nullptr;  // step-size table [2][L0] of the current MD
     int64_t launches = 0;    // kernels launched by this handle
+    bool deferred = false;   // solves leave status on the device (graph capture)
+    bool capturing = false;  // a CUDA graph is being recorded: no profiling
+    // the molecular dynamics of one trajectory as a CUDA graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t md_exec = nullptr;
+    std::vector<unsigned char> md_key;  // parameters the graph was recorded for
+    int64_t md_launches = 0;            // kernels per replay
+    int md_nforce = 0;                  // force evaluations per replay
+    int md_solves = 0;                  // solves per replay
     int64_t iter_count = 0;  // inner iterations since reset (trajectory stats)
     int64_t site_iters = 0;  // inner iterations x even sites of the system
     int solve_count = 0;
@@ -608,6 +625,8 @@ int hop_sweep(lqcd_ctx* h, int prec, int mode, int dag, int pout, int colour, Sp
 // solver.cu
 int solver_init(lqcd_ctx* h);
 void solver_free(lqcd_ctx* h);
+// sticky status and iteration sums of the solves since the last call
+int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters);
 // even-odd reduced solve (1 - kappa^2 H_eo H_oe) x_e = b_e on the slabs of
 // `colour` (block mode) or globally; x_e, b_e: double parity-0 views
 // `diag` replaces the 1 of the system: diag - kappa^2 H_eo H_oe (W3,eo = W2,eo + rho)

@@ -7,14 +7,17 @@
 // with 128-bit (single: float4, half: uint4) or 2x64-bit (double2) loads of
 // consecutive sites, spin-projected to a half spinor, multiplied by the
 // (rebuilt) link and accumulated; the output is written once.
+#include <algorithm>
+
 #include "lqcd_common.cuh"
 
 namespace {
 
-constexpr int HOP_BS = 128;
+// block size chosen at run time (lqcd_autotune), at most HOP_BS_MAX
+constexpr int HOP_BS_MAX = 256;
 
 template <int P>
-__global__ void __launch_bounds__(HOP_BS) k_hop(Geo g, int mode, int dag, int pout, int colour,
+__global__ void __launch_bounds__(HOP_BS_MAX) k_hop(Geo g, int mode, int dag, int pout, int colour,
                                                SpinorF out, SpinorF in, GaugeF U, double a, SpinorF x,
                                                double c, int nsites)
 {
@@ -62,16 +65,17 @@ int hop_sweep(lqcd_ctx* h, int prec, int mode, int dag, int pout, int colour, Sp
 {
     const Geo& g = h->g;
     const int nsites = colour < 0 ? g.Vh : (g.nb / 2) * g.Sh;
-    const int nb = (nsites + HOP_BS - 1) / HOP_BS;
+    const int bs = std::min(std::max(h->tune.hop_bs[prec], 32), HOP_BS_MAX);
+    const int nb = (nsites + bs - 1) / bs;
     GaugeF U = gauge_view(h, prec);
     cudaEvent_t ev;
     prof_begin(h, 0, &ev);
     if (prec == PREC64)
-        k_hop<PREC64><<<nb, HOP_BS, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+        k_hop<PREC64><<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
     else if (prec == PREC32)
-        k_hop<PREC32><<<nb, HOP_BS, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+        k_hop<PREC32><<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
     else
-        k_hop<PREC16><<<nb, HOP_BS, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+        k_hop<PREC16><<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
     h->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -53,6 +53,8 @@ struct SolveArgs {
     double* part;       // [NQ][grid]
     unsigned* bar;      // one barrier counter per system, BAR_STRIDE apart
     int* status;
+    int* sticky;        // first failure of any solve since the host last read it
+    unsigned long long* acc;  // [2] inner iterations, iterations x system sites
     int* iters;         // [nsys]
     double* resid;      // [nsys]
     int* outer_out;
@@ -92,6 +94,7 @@ __device__ bool sys_sync(const SolveArgs& A, int sys, unsigned& epoch)
             if (*(volatile int*)A.status == LQCD_ERR_TIMEOUT) { bad = 1; break; }
             if (clock64() - t0 > SPIN_LIMIT) {
                 atomicExch(A.status, LQCD_ERR_TIMEOUT);
+                atomicCAS(A.sticky, 0, LQCD_ERR_TIMEOUT);
                 bad = 1;
                 break;
             }
@@ -683,6 +686,10 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
         if (sys == 0) *A.outer_out = outer;
         if (final_flag == F_NAN) atomicCAS(A.status, 0, LQCD_ERR_NAN);
         if (final_flag == F_MAXIT) atomicCAS(A.status, 0, LQCD_ERR_NOCONVERGE);
+        if (final_flag == F_NAN) atomicCAS(A.sticky, 0, LQCD_ERR_NAN);
+        if (final_flag == F_MAXIT) atomicCAS(A.sticky, 0, LQCD_ERR_NOCONVERGE);
+        atomicAdd(A.acc, (unsigned long long)S.it);
+        atomicAdd(A.acc + 1, (unsigned long long)S.it * (unsigned long long)A.nsite);
     }
 }
 
@@ -704,6 +711,7 @@ struct Work {
     double* part = nullptr;       // [2][NQ][grid] double-buffered partial sums
     unsigned* bar = nullptr;      // [NSYS_MAX][BAR_STRIDE] barrier counters
     int* status = nullptr;
+    int* sticky = nullptr;  // int[4] then unsigned long long[2] (sticky status, iteration sums)
     int* iters = nullptr;
     double* resid = nullptr;
     int* outer = nullptr;
@@ -742,11 +750,35 @@ int solver_init(lqcd_ctx* h)
     LQ_CUDA(h, cudaMalloc(&w->part, sizeof(double) * 2 * NQ * (size_t)gm));
     LQ_CUDA(h, cudaMalloc(&w->bar, sizeof(unsigned) * BAR_STRIDE * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->status, sizeof(int) * 4));
+    LQ_CUDA(h, cudaMalloc(&w->sticky, sizeof(int) * 4 + sizeof(unsigned long long) * 2));
+    LQ_CUDA(h, cudaMemset(w->sticky, 0, sizeof(int) * 4 + sizeof(unsigned long long) * 2));
     LQ_CUDA(h, cudaMalloc(&w->iters, sizeof(int) * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->resid, sizeof(double) * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->outer, sizeof(int) * 4));
     LQ_CUDA(h, cudaMallocHost(&w->h_status, sizeof(int) * (NSYS_MAX + 4)));
     LQ_CUDA(h, cudaMallocHost(&w->h_resid, sizeof(double) * NSYS_MAX));
+    return LQCD_OK;
+}
+
+// reads and clears the sticky status and the iteration sums of the solves
+// run since the last call (synchronises the stream)
+int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters)
+{
+    Work* w = h->work;
+    int hs[4];
+    unsigned long long acc[2];
+    LQ_CUDA(h, cudaMemcpyAsync(hs, w->sticky, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+    LQ_CUDA(h, cudaMemcpyAsync(acc, w->sticky + 4, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+    LQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    LQ_CUDA(h, cudaMemsetAsync(w->sticky, 0, sizeof(int) * 4 + sizeof(acc), h->stream));
+    if (iters) *iters = (int64_t)acc[0];
+    if (site_iters) *site_iters = (int64_t)acc[1];
+    if (hs[0] != 0) {
+        h->err = hs[0] == LQCD_ERR_TIMEOUT ? "solver: grid barrier wait timed out"
+                 : hs[0] == LQCD_ERR_NAN   ? "solver: non-finite residual"
+                                           : "solver: no convergence";
+        return hs[0];
+    }
     return LQCD_OK;
 }
 
@@ -760,6 +792,7 @@ void solver_free(lqcd_ctx* h)
     cudaFree(w->part);
     cudaFree(w->bar);
     cudaFree(w->status);
+    cudaFree(w->sticky);
     cudaFree(w->iters);
     cudaFree(w->resid);
     cudaFree(w->outer);
@@ -809,7 +842,8 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
         return LQCD_ERR_GEOM;
     }
     const int want = (A.nsite + SBS - 1) / SBS;
-    A.cps = std::max(1, std::min(w->gmax[prec] / A.nsys, want));
+    const int spt = std::max(1, h->tune.solve_spt[prec][mode == MODE_INTRA ? 0 : 1]);
+    A.cps = std::max(1, std::min(w->gmax[prec] / A.nsys, (want + spt - 1) / spt));
     const int G = A.cps * A.nsys;
     A.U64 = gauge_view(h, PREC64);
     A.UP = gauge_view(h, prec);
@@ -833,6 +867,8 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.part = w->part;
     A.bar = w->bar;
     A.status = w->status;
+    A.sticky = w->sticky;
+    A.acc = (unsigned long long*)(w->sticky + 4);
     A.iters = w->iters;
     A.resid = w->resid;
     A.outer_out = w->outer;
@@ -844,9 +880,24 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
                                       : (const void*)k_solve<PREC16>;
     cudaEvent_t ev;
     prof_begin(h, 1, &ev);
-    LQ_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(G), dim3(SBS), args, 0, h->stream));
+    // cooperative launch (every CTA resident), expressed as a launch
+    // attribute so that it can also be recorded into a CUDA graph
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(SBS);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    LQ_CUDA(h, cudaLaunchKernelExC(&cfg, fn, args));
     h->launches += 1;
+    h->solve_count += 1;
     prof_end(h, 1, ev, 0.0);
+    // deferred mode (graph capture): status and iterations stay on the
+    // device (sticky status, iteration sums) until solver_collect
+    if (h->deferred) return LQCD_OK;
     const size_t rec = h->prof.recs.size();
     LQ_CUDA(h, cudaMemcpyAsync(w->h_status, w->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LQ_CUDA(h, cudaMemcpyAsync(w->h_status + 1, w->outer, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -869,7 +920,6 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
         h->prof.recs[rec - 1].bytes = (double)A.nsite * ((double)itsum * bi + (double)nouter * A.nsys * bo);
     h->iter_count += itsum;
     h->site_iters += itsum * (int64_t)A.nsite;
-    h->solve_count += 1;
     if (st == LQCD_ERR_TIMEOUT) {
         h->err = "solver: grid barrier wait timed out";
         return LQCD_ERR_TIMEOUT;

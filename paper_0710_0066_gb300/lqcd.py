@@ -38,6 +38,7 @@ EXPORTS = [
     "lqcd_profile_enable", "lqcd_profile_reset", "lqcd_profile_read", "lqcd_launch_count",
     "lqcd_gauge_action_static", "lqcd_force_profile", "lqcd_set_subslabs", "lqcd_subblock_dslash",
     "lqcd_subblock_solve_batched", "lqcd_subblock_eo", "lqcd_pf_force_eo", "lqcd_link_update",
+    "lqcd_autotune", "lqcd_tune_read", "lqcd_profile_times",
 ]
 
 
@@ -50,6 +51,7 @@ class HmcParams(C.Structure):
         ("tol", C.c_double), ("max_iter", C.c_int), ("step_scheme", C.c_int), ("step_scale", C.c_void_p),
         ("level_w2", C.c_int), ("level_schur2", C.c_int),
         ("rho", C.c_double), ("level_s2", C.c_int), ("level_s1", C.c_int), ("eo_solver", C.c_int),
+        ("use_graph", C.c_int),
     ]
 
 
@@ -69,14 +71,15 @@ class HmcResult(C.Structure):
 def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w1=0, level_schur=0,
                lam=1.0 / 6.0, pf_init=0, roll=0, metropolis=1, precision=PREC_F64, tol=1e-10,
                max_iter=20000, step_scheme=0, step_scale=None, level_w2=-1, level_schur2=-1, rho=0.0,
-               level_s2=-1, level_s1=-1, eo_solver=SOLVER_BICGSTAB):
+               level_s2=-1, level_s1=-1, eo_solver=SOLVER_BICGSTAB, use_graph=0):
     """step_scale: None or a host float64 array (2, L0) of s(x0) (space-like,
     time-like rows); it is kept alive on the returned object"""
     sc = list(scheme) + [0] * (MAX_LEVELS - len(scheme))
     ns = list(nsteps) + [1] * (MAX_LEVELS - len(nsteps))
     p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * MAX_LEVELS)(*sc), (C.c_int * MAX_LEVELS)(*ns),
                   level_gauge, level_w1, level_schur, pf_init, roll, metropolis, precision, tol,
-                  max_iter, step_scheme, None, level_w2, level_schur2, rho, level_s2, level_s1, eo_solver)
+                  max_iter, step_scheme, None, level_w2, level_schur2, rho, level_s2, level_s1, eo_solver,
+                  use_graph)
     if step_scale is not None:
         import numpy as np
 
@@ -119,6 +122,9 @@ def load():
         "lqcd_pf_force_eo": [vp, vp, vp, d, d, i, i, d, i, vp],
         "lqcd_set_subslabs": [vp, i],
         "lqcd_link_update": [vp, vp, vp, d],
+        "lqcd_autotune": [vp, i, d],
+        "lqcd_tune_read": [vp, vp],
+        "lqcd_profile_times": [vp, i, vp, i64, vp],
         "lqcd_subblock_dslash": [vp, vp, vp, d, i, i, i],
         "lqcd_subblock_solve_batched": [vp, vp, vp, d, i, i, i, d, i, vp, vp],
         "lqcd_profile_enable": [vp, i],
@@ -218,6 +224,19 @@ def lqcd_block_solve_batched(h, x, b, kappa, colour=-1, dagger=0, precision=PREC
                                               int(dagger), int(precision), float(tol), int(max_iter),
                                               it, rs))
     return list(it), list(rs)
+
+
+def lqcd_autotune(h, what=3, kappa=0.15):
+    return _check(h, load().lqcd_autotune(h, int(what), float(kappa)))
+
+
+def lqcd_tune_read(h):
+    out = (C.c_int * 9)()
+    _check(h, load().lqcd_tune_read(h, out))
+    v = list(out)
+    return {"hop_block_size": dict(zip(("f64", "f32", "f16"), v[0:3])),
+            "slab_solve_sites_per_thread": dict(zip(("f64", "f32", "f16"), v[3:6])),
+            "global_solve_sites_per_thread": dict(zip(("f64", "f32", "f16"), v[6:9]))}
 
 
 def lqcd_link_update(h, U, P, dt):
@@ -328,6 +347,16 @@ def lqcd_launch_count(h):
     n = C.c_int64(0)
     _check(h, load().lqcd_launch_count(h, C.byref(n)))
     return n.value
+
+
+def lqcd_profile_times(h, kernel_id, cap=65536):
+    """per-launch device times (ms) of kernel_id since the last reset"""
+    n = C.c_int64(0)
+    _check(h, load().lqcd_profile_times(h, int(kernel_id), None, 0, C.byref(n)))
+    k = min(cap, n.value)
+    buf = (C.c_float * max(k, 1))()
+    _check(h, load().lqcd_profile_times(h, int(kernel_id), buf, k, C.byref(n)))
+    return list(buf)[:k]
 
 
 def lqcd_profile_read(h, kernel_id):
