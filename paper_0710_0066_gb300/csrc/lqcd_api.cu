@@ -505,7 +505,8 @@ std::vector<unsigned char> md_key(const lqcd_ctx* h, const lqcd_hmc_params& p)
     std::vector<double> k = {p.beta, p.kappa, p.tau, p.lambda, (double)p.nlevels, (double)p.level_gauge,
                              (double)p.level_w1, (double)p.level_schur, (double)p.level_w2, (double)p.level_schur2,
                              (double)p.level_s2, (double)p.level_s1, p.rho, (double)p.precision, p.tol,
-                             (double)p.max_iter, (double)p.eo_solver, (double)p.step_scheme};
+                             (double)p.max_iter, (double)p.eo_solver, (double)p.step_scheme,
+                             (double)h->prof.on};
     for (int j = 0; j < LQCD_MAX_LEVELS; ++j) {
         k.push_back((double)p.scheme[j]);
         k.push_back((double)p.nsteps[j]);
@@ -528,6 +529,11 @@ int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const do
             cudaGraphExecDestroy(h->md_exec);
             h->md_exec = nullptr;
         }
+        for (auto& r : h->prof.graph_recs) {
+            h->prof.pool.push_back(r.a);
+            h->prof.pool.push_back(r.b);
+        }
+        h->prof.graph_recs.clear();
         if (!h->cap_stream) LQ_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
         cudaStream_t user = h->stream;
         const int64_t l0 = h->launches;
@@ -572,10 +578,25 @@ int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const do
     h->launches += h->md_launches;
     h->solve_count += h->md_solves;
     *nforce += h->md_nforce;
-    int64_t it = 0, sit = 0;
-    const int st = solver_collect(h, &it, &sit);
+    int64_t it = 0, sit = 0, osit = 0;
+    const int st = solver_collect(h, &it, &sit, &osit);
     h->iter_count += it;
     h->site_iters += sit;
+    // kernel times of this replay (the stream is synchronised); the solver's
+    // algorithmic bytes follow from the replay's iteration sums
+    if (!h->prof.graph_recs.empty()) {
+        for (const auto& r : h->prof.graph_recs) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, r.a, r.b);
+            h->prof.launches[r.id] += 1;
+            h->prof.ms[r.id] += ms;
+            if (r.id != 1) h->prof.bytes[r.id] += r.bytes;
+            if (h->prof.hist[r.id].size() < 65536) h->prof.hist[r.id].push_back(ms);
+        }
+        double bi, bo;
+        solver_site_bytes(p.precision, SOLVER_BICGSTAB, &bi, &bo);
+        h->prof.bytes[1] += (double)sit * bi + (double)osit * bo;
+    }
     return st;
 }
 
@@ -663,7 +684,7 @@ GaugeF gauge_view(lqcd_ctx* h, int prec)
 void prof_begin(lqcd_ctx* h, int id, cudaEvent_t* a)
 {
     *a = nullptr;
-    if (!(h->prof.on & (1u << id)) || h->capturing) return;
+    if (!(h->prof.on & (1u << id))) return;
     if (h->prof.pool.empty()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -671,12 +692,15 @@ void prof_begin(lqcd_ctx* h, int id, cudaEvent_t* a)
     }
     *a = h->prof.pool.back();
     h->prof.pool.pop_back();
-    cudaEventRecord(*a, h->stream);
+    // while a graph is recorded, an external record makes the event a node
+    // of the graph, updated by every replay
+    if (h->capturing) cudaEventRecordWithFlags(*a, h->stream, cudaEventRecordExternal);
+    else cudaEventRecord(*a, h->stream);
 }
 
 void prof_end(lqcd_ctx* h, int id, cudaEvent_t a, double bytes)
 {
-    if (!(h->prof.on & (1u << id)) || !a || h->capturing) return;
+    if (!(h->prof.on & (1u << id)) || !a) return;
     cudaEvent_t b;
     if (h->prof.pool.empty()) {
         if (cudaEventCreate(&b) != cudaSuccess) return;
@@ -684,8 +708,12 @@ void prof_end(lqcd_ctx* h, int id, cudaEvent_t a, double bytes)
         b = h->prof.pool.back();
         h->prof.pool.pop_back();
     }
-    cudaEventRecord(b, h->stream);
-    h->prof.recs.push_back({a, b, id, bytes});
+    if (h->capturing) cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal);
+    else cudaEventRecord(b, h->stream);
+    // inside a graph recording the pair becomes two event-record nodes,
+    // read after every replay
+    if (h->capturing) h->prof.graph_recs.push_back({a, b, id, bytes});
+    else h->prof.recs.push_back({a, b, id, bytes});
 }
 
 static void prof_flush(lqcd_ctx* h)
@@ -799,6 +827,10 @@ int lqcd_destroy(lqcd_t h)
     cudaFree(h->red_out);
     cudaFreeHost(h->red_host);
     for (auto& r : h->prof.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto& r : h->prof.graph_recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }

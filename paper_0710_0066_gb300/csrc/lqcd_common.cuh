@@ -500,6 +500,7 @@ struct Profiler {
     double ms[5] = {0, 0, 0, 0, 0};
     double bytes[5] = {0, 0, 0, 0, 0};
     std::vector<float> hist[5];  // per-launch device times since the last reset
+    std::vector<Rec> graph_recs;  // event pairs recorded inside the MD graph
 };
 
 struct Work;  // solver workspace (lqcd_solver.cu)
@@ -626,7 +627,9 @@ int hop_sweep(lqcd_ctx* h, int prec, int mode, int dag, int pout, int colour, Sp
 int solver_init(lqcd_ctx* h);
 void solver_free(lqcd_ctx* h);
 // sticky status and iteration sums of the solves since the last call
-int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters);
+int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* outer_sites = nullptr);
+// algorithmic bytes per system site of one inner iteration / outer cycle
+void solver_site_bytes(int prec, int method, double* inner, double* outer);
 // even-odd reduced solve (1 - kappa^2 H_eo H_oe) x_e = b_e on the slabs of
 // `colour` (block mode) or globally; x_e, b_e: double parity-0 views
 // `diag` replaces the 1 of the system: diag - kappa^2 H_eo H_oe (W3,eo = W2,eo + rho)

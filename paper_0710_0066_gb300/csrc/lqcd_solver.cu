@@ -54,7 +54,7 @@ struct SolveArgs {
     unsigned* bar;      // one barrier counter per system, BAR_STRIDE apart
     int* status;
     int* sticky;        // first failure of any solve since the host last read it
-    unsigned long long* acc;  // [2] inner iterations, iterations x system sites
+    unsigned long long* acc;  // [3] inner iterations, iterations x sites, outer cycles x sites
     int* iters;         // [nsys]
     double* resid;      // [nsys]
     int* outer_out;
@@ -690,6 +690,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
         if (final_flag == F_MAXIT) atomicCAS(A.sticky, 0, LQCD_ERR_NOCONVERGE);
         atomicAdd(A.acc, (unsigned long long)S.it);
         atomicAdd(A.acc + 1, (unsigned long long)S.it * (unsigned long long)A.nsite);
+        atomicAdd(A.acc + 2, (unsigned long long)outer * (unsigned long long)A.nsite);
     }
 }
 
@@ -711,7 +712,7 @@ struct Work {
     double* part = nullptr;       // [2][NQ][grid] double-buffered partial sums
     unsigned* bar = nullptr;      // [NSYS_MAX][BAR_STRIDE] barrier counters
     int* status = nullptr;
-    int* sticky = nullptr;  // int[4] then unsigned long long[2] (sticky status, iteration sums)
+    int* sticky = nullptr;  // int[4] then unsigned long long[3] (sticky status, iteration sums)
     int* iters = nullptr;
     double* resid = nullptr;
     int* outer = nullptr;
@@ -750,8 +751,8 @@ int solver_init(lqcd_ctx* h)
     LQ_CUDA(h, cudaMalloc(&w->part, sizeof(double) * 2 * NQ * (size_t)gm));
     LQ_CUDA(h, cudaMalloc(&w->bar, sizeof(unsigned) * BAR_STRIDE * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->status, sizeof(int) * 4));
-    LQ_CUDA(h, cudaMalloc(&w->sticky, sizeof(int) * 4 + sizeof(unsigned long long) * 2));
-    LQ_CUDA(h, cudaMemset(w->sticky, 0, sizeof(int) * 4 + sizeof(unsigned long long) * 2));
+    LQ_CUDA(h, cudaMalloc(&w->sticky, sizeof(int) * 4 + sizeof(unsigned long long) * 3));
+    LQ_CUDA(h, cudaMemset(w->sticky, 0, sizeof(int) * 4 + sizeof(unsigned long long) * 3));
     LQ_CUDA(h, cudaMalloc(&w->iters, sizeof(int) * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->resid, sizeof(double) * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->outer, sizeof(int) * 4));
@@ -762,17 +763,18 @@ int solver_init(lqcd_ctx* h)
 
 // reads and clears the sticky status and the iteration sums of the solves
 // run since the last call (synchronises the stream)
-int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters)
+int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* outer_sites)
 {
     Work* w = h->work;
     int hs[4];
-    unsigned long long acc[2];
+    unsigned long long acc[3];
     LQ_CUDA(h, cudaMemcpyAsync(hs, w->sticky, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
     LQ_CUDA(h, cudaMemcpyAsync(acc, w->sticky + 4, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
     LQ_CUDA(h, cudaStreamSynchronize(h->stream));
     LQ_CUDA(h, cudaMemsetAsync(w->sticky, 0, sizeof(int) * 4 + sizeof(acc), h->stream));
     if (iters) *iters = (int64_t)acc[0];
     if (site_iters) *site_iters = (int64_t)acc[1];
+    if (outer_sites) *outer_sites = (int64_t)acc[2];
     if (hs[0] != 0) {
         h->err = hs[0] == LQCD_ERR_TIMEOUT ? "solver: grid barrier wait timed out"
                  : hs[0] == LQCD_ERR_NAN   ? "solver: non-finite residual"
@@ -804,7 +806,7 @@ void solver_free(lqcd_ctx* h)
 
 // algorithmic DRAM bytes per system site: one inner iteration and one outer
 // cycle (each vector and the eight links moved once per phase)
-static void solver_site_bytes(int prec, int method, double* inner, double* outer)
+void solver_site_bytes(int prec, int method, double* inner, double* outer)
 {
     const double sp = prec == PREC64 ? 192.0 : prec == PREC32 ? 96.0 : 52.0;
     const double lk = prec == PREC64 ? 1152.0 : prec == PREC32 ? 384.0 : 192.0;

@@ -49,6 +49,26 @@ def test_graph_trajectories_equal_eager():
     lat_g.close()
 
 
+def test_graph_kernel_times():
+    """kernel timing inside the replayed graph: the same solver launches and
+    algorithmic bytes as the eager trajectory, times of the same order"""
+    U0 = torch.from_numpy(syn.random_links(L, 0.6, 19)).cuda()
+    out = {}
+    for graph in (0, 1):
+        lat = lqcd.Lattice(L, L0S, -1)
+        lqcd.lqcd_profile_enable(lat.h, 1 << lqcd.KERNEL_SOLVER)
+        lat.hmc_trajectory(U0, _prm(graph), 3, 0)  # records the graph
+        lqcd.lqcd_profile_reset(lat.h)
+        lat.hmc_trajectory(U0, _prm(graph), 3, 0)
+        out[graph] = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
+        assert len(lqcd.lqcd_profile_times(lat.h, lqcd.KERNEL_SOLVER)) == out[graph][0]
+        lat.close()
+    (n0, ms0, b0), (n1, ms1, b1) = out[0], out[1]
+    assert n0 == n1 > 10
+    assert abs(b1 - b0) < 0.02 * b0
+    assert 0.5 * ms0 < ms1 < 1.5 * ms0
+
+
 def test_graph_reports_a_failed_solve():
     U0 = torch.from_numpy(syn.random_links(L, 0.6, 18)).cuda()
     lat = lqcd.Lattice(L, L0S, -1)
