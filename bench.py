@@ -168,11 +168,13 @@ def oracle_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
-# Wilson-matrix applications in one trajectory of this workload: four
-# half-lattice hopping sweeps per inner iteration and system site, counted by
-# the library (site_iters); the value below is the mixed-precision count of a
-# 16^3x32 run, used when no GPU run is made in the same process
-M_APPS_PER_TRAJ_DEFAULT = 6000.0
+# Wilson-matrix applications in one trajectory of this workload: the
+# library counts the half-lattice hopping site updates of every inner
+# iteration (hop_sites; a full application is V of them); the value below is
+# that count for the default 16^3x32 run (geometric series for W1, BiCGstab
+# elsewhere, single-precision inner storage), used by the reference arm,
+# which runs without a GPU
+M_APPS_PER_TRAJ_DEFAULT = 25187.0
 
 
 # ---------------------------------------------------------------------------
@@ -234,7 +236,9 @@ def run_ours(args):
         return lqcd.hmc_params(WL["beta"], WL["kappa"], WL["tau"], WL["nlevels"], WL["scheme"], WL["nsteps"],
                                WL["level_gauge"], WL["level_w1"], WL["level_schur"], lam=WL["lam"], roll=1,
                                metropolis=1, precision=prec, tol=WL["tol"], max_iter=WL["max_iter"],
-                               use_graph=0 if args.no_graph else 1)
+                               use_graph=0 if args.no_graph else 1,
+                               block_solver=lqcd.SOLVER_SERIES if args.block_solver == "series"
+                               else lqcd.SOLVER_BICGSTAB)
 
     prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     prm = params(prec)
@@ -363,8 +367,9 @@ def run_ours(args):
             profile[name] = [round(v, 5) for v in lat.force_profile(F)[0].tolist()]
 
     # ---- oracle on the host cores (bounded sample)
-    site_iters = statistics.mean(r.site_iters for r in results)
-    m_apps = 4.0 * site_iters / lat.V
+    # Wilson-matrix applications of one trajectory's inner iterations (a
+    # full application is two half-lattice sweeps, V site updates)
+    m_apps = statistics.mean(r.hop_sites for r in results) / lat.V
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         t_M, n = oracle_M_seconds(args.cpu_seconds, L, l0, WL["eps"], WL["seed"])
@@ -384,7 +389,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD_NAME, "lattice": "x".join(map(str, L)), "l0": l0,
                    "inner_precision": args.precision, "l2": "flushed between timed trajectories",
                    "parallelism": "replicas" if world > 1 else "1 GPU", "autotune": tune,
-                   "md_as_cuda_graph": not args.no_graph},
+                   "md_as_cuda_graph": not args.no_graph, "w1_block_solver": args.block_solver},
         "roofline": {"bound": "hbm", "kernel": "persistent batched solver (k_solve)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -402,6 +407,7 @@ def run_ours(args):
                        "step_ms": step_ms},
         "e2e": {"value": e2e_value, "unit": "s/trajectory", "h2d_bytes_per_step": ubytes,
                 "d2h_bytes_per_step": ubytes},
+        "m_apps_per_traj": m_apps,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -594,6 +600,9 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f16", "f32", "f64"],
                     help="storage of the inner Krylov iterations (outer residuals stay double)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--block-solver", default="series", choices=["bicgstab", "series"],
+                    help="inner iteration of the W1 slab solves of the trajectory (the paper's "
+                         "geometric series by default)")
     ap.add_argument("--eo-solver", default="bicgstab", choices=["bicgstab", "series"],
                     help="inner iteration of the S2 / S1 solves (--case production)")
     ap.add_argument("--no-fp64", action="store_true")

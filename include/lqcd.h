@@ -301,6 +301,12 @@ typedef struct {
     int level_s1;
     int eo_solver;      /* inner iteration of the S2 / S1 solves (W3,eo, W2,eo):
                            LQCD_SOLVER_BICGSTAB or LQCD_SOLVER_SERIES */
+    int block_solver;   /* inner iteration of the W1 / W2 block solves of the
+                           |W1^-1 phi1|^2 and |W2^-1 phi3|^2 terms (the solves
+                           inside R and R2 keep BiCGstab):
+                           LQCD_SOLVER_BICGSTAB or LQCD_SOLVER_SERIES, the
+                           geometric series of Sec. 3 (which needs its
+                           spectral radius below one) */
     int use_graph;      /* 1: lqcd_hmc_trajectory runs the molecular dynamics
                            as a CUDA graph, recorded the first time for a
                            parameter set (not run then) and replayed; the
@@ -331,8 +337,10 @@ typedef struct {
     int n_solves;
     int n_force;        /* force evaluations */
     int64_t site_iters; /* sum over solves of inner iterations x even sites
-                           of the system (each is four half-lattice hopping
-                           site updates) */
+                           of the system */
+    int64_t hop_sites;  /* half-lattice hopping site updates of those inner
+                           iterations (four per BiCGstab iteration and site,
+                           two per geometric-series iteration and site) */
 } lqcd_hmc_result;
 
 /* One HMC trajectory (Sec. 2): heatbath (momenta p^a ~ N(0,1), eta ~

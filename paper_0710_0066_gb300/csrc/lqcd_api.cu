@@ -63,7 +63,8 @@ int hop_full(lqcd_ctx* h, int mode, int dag, int colour, double2* out, const dou
 // x = W^-1 b (block: W1 on the slabs of `colour`; global: M).  x, b full
 // double fields, b is not modified, x must not alias b.
 int solve_full(lqcd_ctx* h, int mode, int colour, int dagger, int prec, double kappa, double2* x,
-               const double2* b, double tol, int max_iter, int* iters, double* resid)
+               const double2* b, double tol, int max_iter, int* iters, double* resid,
+               int method = SOLVER_BICGSTAB)
 {
     const int Vh = h->g.Vh;
     const double2* bb = b;
@@ -75,7 +76,7 @@ int solve_full(lqcd_ctx* h, int mode, int colour, int dagger, int prec, double k
     // b_e' = b_e + kappa H_eo b_o
     LQ_TRY(hop_sweep(h, PREC64, mode, 0, 0, col, sp64(fld(h, F_T2), 0, Vh), sp64((double2*)bb, 1, Vh), 1.0,
                      sp64((double2*)bb, 0, Vh), kappa));
-    LQ_TRY(eo_solve(h, mode, col, prec, kappa, x, fld(h, F_T2), tol, max_iter, iters, resid));
+    LQ_TRY(eo_solve(h, mode, col, prec, kappa, x, fld(h, F_T2), tol, max_iter, iters, resid, 1.0, method));
     // x_o = b_o + kappa H_oe x_e
     LQ_TRY(hop_sweep(h, PREC64, mode, 0, 1, col, sp64(x, 1, Vh), sp64(x, 0, Vh), 1.0, sp64((double2*)bb, 1, Vh),
                      kappa));
@@ -129,10 +130,12 @@ int pf_w1(lqcd_ctx* h, double* F, const double2* phi, double kappa, double coef,
           double* S_dev, const double* ss = nullptr)
 {
     double2 *eta = fld(h, F_A), *xi = fld(h, F_B);
-    LQ_TRY(solve_full(h, MODE_INTRA, -1, 0, c.prec, kappa, eta, phi, c.tol, c.max_iter, nullptr, nullptr));
+    LQ_TRY(solve_full(h, MODE_INTRA, -1, 0, c.prec, kappa, eta, phi, c.tol, c.max_iter, nullptr, nullptr,
+                      c.method));
     if (S_dev) LQ_TRY(norm2_dev(h, (const double*)eta, (int64_t)48 * h->g.Vh, S_dev));
     if (!F) return LQCD_OK;
-    LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, xi, eta, c.tol, c.max_iter, nullptr, nullptr));
+    LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, xi, eta, c.tol, c.max_iter, nullptr, nullptr,
+                      c.method));
     return force_bilinear(h, F, xi, eta, MODE_INTRA, kappa * coef, nullptr, nullptr, 0, 0.0, c.prec, ss);
 }
 
@@ -398,8 +401,9 @@ int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
         h->err = "hmc params: use_graph must be 0 or 1";
         return LQCD_ERR_ARG;
     }
-    if (p->eo_solver != LQCD_SOLVER_BICGSTAB && p->eo_solver != LQCD_SOLVER_SERIES) {
-        h->err = "hmc params: bad eo_solver";
+    if ((p->eo_solver != LQCD_SOLVER_BICGSTAB && p->eo_solver != LQCD_SOLVER_SERIES) ||
+        (p->block_solver != LQCD_SOLVER_BICGSTAB && p->block_solver != LQCD_SOLVER_SERIES)) {
+        h->err = "hmc params: bad eo_solver / block_solver";
         return LQCD_ERR_ARG;
     }
     if (!p->step_scale && p->step_scheme) {
@@ -465,6 +469,7 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
     for (int i = 0; i < p.nsteps[top]; ++i) build_step(p, top, dt, ops);
     SolveCfg c{p.precision, p.tol, p.max_iter};
     const SolveCfg ceo{p.precision, p.tol, p.max_iter, p.eo_solver};
+    const SolveCfg cblk{p.precision, p.tol, p.max_iter, p.block_solver};
     for (const Op& o : ops) {
         if (o.kind == 1) {
             LQ_TRY(update_links(h, P, o.dt, ss));
@@ -472,7 +477,7 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
         }
         if (p.level_gauge == o.level) LQ_TRY(gauge_force_kick(h, P, -o.dt * p.beta / 6.0, p.precision, ss));
         if (p.level_w1 == o.level) {
-            LQ_TRY(pf_w1(h, P, pf.phi1, p.kappa, -o.dt, c, nullptr, ss));
+            LQ_TRY(pf_w1(h, P, pf.phi1, p.kappa, -o.dt, cblk, nullptr, ss));
             ++*nforce;
         }
         if (p.level_schur == o.level) {
@@ -480,7 +485,7 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
             ++*nforce;
         }
         if (p.level_w2 == o.level) {
-            LQ_TRY(pf_w2(h, P, pf.phi3, p.kappa, -o.dt, c, nullptr, ss));
+            LQ_TRY(pf_w2(h, P, pf.phi3, p.kappa, -o.dt, cblk, nullptr, ss));
             ++*nforce;
         }
         if (p.level_schur2 == o.level) {
@@ -505,7 +510,8 @@ std::vector<unsigned char> md_key(const lqcd_ctx* h, const lqcd_hmc_params& p)
     std::vector<double> k = {p.beta, p.kappa, p.tau, p.lambda, (double)p.nlevels, (double)p.level_gauge,
                              (double)p.level_w1, (double)p.level_schur, (double)p.level_w2, (double)p.level_schur2,
                              (double)p.level_s2, (double)p.level_s1, p.rho, (double)p.precision, p.tol,
-                             (double)p.max_iter, (double)p.eo_solver, (double)p.step_scheme,
+                             (double)p.max_iter, (double)p.eo_solver, (double)p.block_solver,
+                             (double)p.step_scheme,
                              (double)h->prof.on};
     for (int j = 0; j < LQCD_MAX_LEVELS; ++j) {
         k.push_back((double)p.scheme[j]);
@@ -578,10 +584,11 @@ int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const do
     h->launches += h->md_launches;
     h->solve_count += h->md_solves;
     *nforce += h->md_nforce;
-    int64_t it = 0, sit = 0, osit = 0;
-    const int st = solver_collect(h, &it, &sit, &osit);
+    int64_t it = 0, sit = 0, osit = 0, ssit = 0;
+    const int st = solver_collect(h, &it, &sit, &osit, &ssit);
     h->iter_count += it;
-    h->site_iters += sit;
+    h->site_iters += sit + ssit;
+    h->hop_sites += 4 * sit + 2 * ssit;
     // kernel times of this replay (the stream is synchronised); the solver's
     // algorithmic bytes follow from the replay's iteration sums
     if (!h->prof.graph_recs.empty()) {
@@ -593,9 +600,10 @@ int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const do
             if (r.id != 1) h->prof.bytes[r.id] += r.bytes;
             if (h->prof.hist[r.id].size() < 65536) h->prof.hist[r.id].push_back(ms);
         }
-        double bi, bo;
+        double bi, bo, bs;
         solver_site_bytes(p.precision, SOLVER_BICGSTAB, &bi, &bo);
-        h->prof.bytes[1] += (double)sit * bi + (double)osit * bo;
+        solver_site_bytes(p.precision, SOLVER_SERIES, &bs, &bo);
+        h->prof.bytes[1] += (double)sit * bi + (double)ssit * bs + (double)osit * bo;
     }
     return st;
 }
@@ -625,9 +633,10 @@ int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, int base)
     double* e = h->red_out + base;
     LQ_TRY(kinetic_sum(h, h->P, e));
     if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, e + 1));
-    if (p.level_w1 >= 0) LQ_TRY(pf_w1(h, nullptr, pf.phi1, p.kappa, 0.0, c, e + 2));
+    const SolveCfg cblk{p.precision, p.tol, p.max_iter, p.block_solver};
+    if (p.level_w1 >= 0) LQ_TRY(pf_w1(h, nullptr, pf.phi1, p.kappa, 0.0, cblk, e + 2));
     if (p.level_schur >= 0) LQ_TRY(pf_schur(h, nullptr, pf.phi2, p.kappa, 0.0, c, e + 3));
-    if (p.level_w2 >= 0) LQ_TRY(pf_w2(h, nullptr, pf.phi3, p.kappa, 0.0, c, e + 4));
+    if (p.level_w2 >= 0) LQ_TRY(pf_w2(h, nullptr, pf.phi3, p.kappa, 0.0, cblk, e + 4));
     if (p.level_schur2 >= 0) LQ_TRY(pf_schur2(h, nullptr, pf.phi4, p.kappa, 0.0, c, e + 5));
     const SolveCfg ceo{p.precision, p.tol, p.max_iter, p.eo_solver};
     if (p.level_s2 >= 0) LQ_TRY(pf_s2(h, nullptr, pf.phi5, p.kappa, p.rho, 0.0, ceo, e + 6));
@@ -1238,6 +1247,7 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
     const int nbd = 2 * nbnd_of(g);
     h->iter_count = 0;
     h->site_iters = 0;
+    h->hop_sites = 0;
     h->solve_count = 0;
     LQ_TRY(pack_gauge(h, U));
     h->have_gauge = true;
@@ -1263,7 +1273,8 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
         } else {
             LQ_CUDA(h, cudaMemcpyAsync(fld(h, F_PHI1), et, sizeof(double2) * 24 * (size_t)g.Vh,
                                        cudaMemcpyDeviceToDevice, h->stream));
-            LQ_TRY(pf_w1(h, nullptr, fld(h, F_PHI1), p.kappa, 0.0, c, e0 + 2));
+            const SolveCfg cblk{p.precision, p.tol, p.max_iter, p.block_solver};
+            LQ_TRY(pf_w1(h, nullptr, fld(h, F_PHI1), p.kappa, 0.0, cblk, e0 + 2));
         }
     }
     if (p.level_schur >= 0) {
@@ -1357,6 +1368,7 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
     res->shift = shift;
     res->solver_iters = h->iter_count;
     res->site_iters = h->site_iters;
+    res->hop_sites = h->hop_sites;
     res->n_solves = h->solve_count;
     res->n_force = nforce;
     return LQCD_OK;

@@ -552,6 +552,7 @@ struct lqcd_ctx {
     int md_solves = 0;                  // solves per replay
     int64_t iter_count = 0;  // inner iterations since reset (trajectory stats)
     int64_t site_iters = 0;  // inner iterations x even sites of the system
+    int64_t hop_sites = 0;   // half-lattice hopping site updates of those iterations
     int solve_count = 0;
 };
 
@@ -627,7 +628,10 @@ int hop_sweep(lqcd_ctx* h, int prec, int mode, int dag, int pout, int colour, Sp
 int solver_init(lqcd_ctx* h);
 void solver_free(lqcd_ctx* h);
 // sticky status and iteration sums of the solves since the last call
-int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* outer_sites = nullptr);
+// (site_iters: BiCGstab iterations x system sites; series_sites: the same
+// for geometric-series iterations)
+int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* outer_sites = nullptr,
+                   int64_t* series_sites = nullptr);
 // algorithmic bytes per system site of one inner iteration / outer cycle
 void solver_site_bytes(int prec, int method, double* inner, double* outer);
 // even-odd reduced solve (1 - kappa^2 H_eo H_oe) x_e = b_e on the slabs of

@@ -54,7 +54,8 @@ struct SolveArgs {
     unsigned* bar;      // one barrier counter per system, BAR_STRIDE apart
     int* status;
     int* sticky;        // first failure of any solve since the host last read it
-    unsigned long long* acc;  // [3] inner iterations, iterations x sites, outer cycles x sites
+    unsigned long long* acc;  // [4] inner iterations, BiCGstab iterations x sites,
+                              // outer cycles x sites, series iterations x sites
     int* iters;         // [nsys]
     double* resid;      // [nsys]
     int* outer_out;
@@ -689,7 +690,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
         if (final_flag == F_NAN) atomicCAS(A.sticky, 0, LQCD_ERR_NAN);
         if (final_flag == F_MAXIT) atomicCAS(A.sticky, 0, LQCD_ERR_NOCONVERGE);
         atomicAdd(A.acc, (unsigned long long)S.it);
-        atomicAdd(A.acc + 1, (unsigned long long)S.it * (unsigned long long)A.nsite);
+        atomicAdd(A.acc + (A.method == SOLVER_SERIES ? 3 : 1), (unsigned long long)S.it * (unsigned long long)A.nsite);
         atomicAdd(A.acc + 2, (unsigned long long)outer * (unsigned long long)A.nsite);
     }
 }
@@ -712,7 +713,7 @@ struct Work {
     double* part = nullptr;       // [2][NQ][grid] double-buffered partial sums
     unsigned* bar = nullptr;      // [NSYS_MAX][BAR_STRIDE] barrier counters
     int* status = nullptr;
-    int* sticky = nullptr;  // int[4] then unsigned long long[3] (sticky status, iteration sums)
+    int* sticky = nullptr;  // int[4] then unsigned long long[4] (sticky status, iteration sums)
     int* iters = nullptr;
     double* resid = nullptr;
     int* outer = nullptr;
@@ -751,8 +752,8 @@ int solver_init(lqcd_ctx* h)
     LQ_CUDA(h, cudaMalloc(&w->part, sizeof(double) * 2 * NQ * (size_t)gm));
     LQ_CUDA(h, cudaMalloc(&w->bar, sizeof(unsigned) * BAR_STRIDE * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->status, sizeof(int) * 4));
-    LQ_CUDA(h, cudaMalloc(&w->sticky, sizeof(int) * 4 + sizeof(unsigned long long) * 3));
-    LQ_CUDA(h, cudaMemset(w->sticky, 0, sizeof(int) * 4 + sizeof(unsigned long long) * 3));
+    LQ_CUDA(h, cudaMalloc(&w->sticky, sizeof(int) * 4 + sizeof(unsigned long long) * 4));
+    LQ_CUDA(h, cudaMemset(w->sticky, 0, sizeof(int) * 4 + sizeof(unsigned long long) * 4));
     LQ_CUDA(h, cudaMalloc(&w->iters, sizeof(int) * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->resid, sizeof(double) * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->outer, sizeof(int) * 4));
@@ -763,11 +764,12 @@ int solver_init(lqcd_ctx* h)
 
 // reads and clears the sticky status and the iteration sums of the solves
 // run since the last call (synchronises the stream)
-int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* outer_sites)
+int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* outer_sites,
+                   int64_t* series_sites)
 {
     Work* w = h->work;
     int hs[4];
-    unsigned long long acc[3];
+    unsigned long long acc[4];
     LQ_CUDA(h, cudaMemcpyAsync(hs, w->sticky, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
     LQ_CUDA(h, cudaMemcpyAsync(acc, w->sticky + 4, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
     LQ_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -775,6 +777,7 @@ int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* ou
     if (iters) *iters = (int64_t)acc[0];
     if (site_iters) *site_iters = (int64_t)acc[1];
     if (outer_sites) *outer_sites = (int64_t)acc[2];
+    if (series_sites) *series_sites = (int64_t)acc[3];
     if (hs[0] != 0) {
         h->err = hs[0] == LQCD_ERR_TIMEOUT ? "solver: grid barrier wait timed out"
                  : hs[0] == LQCD_ERR_NAN   ? "solver: non-finite residual"
@@ -922,6 +925,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
         h->prof.recs[rec - 1].bytes = (double)A.nsite * ((double)itsum * bi + (double)nouter * A.nsys * bo);
     h->iter_count += itsum;
     h->site_iters += itsum * (int64_t)A.nsite;
+    h->hop_sites += itsum * (int64_t)A.nsite * (method == SOLVER_SERIES ? 2 : 4);
     if (st == LQCD_ERR_TIMEOUT) {
         h->err = "solver: grid barrier wait timed out";
         return LQCD_ERR_TIMEOUT;

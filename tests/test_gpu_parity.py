@@ -209,6 +209,25 @@ def test_hmc_trajectory_matches_oracle(pf_init):
     lat.close()
 
 
+def test_hmc_trajectory_block_series_matches_oracle():
+    """the W1 solves by the geometric series (Sec. 3): kappa = 0.12 on a
+    smooth field keeps the series convergent"""
+    L, l0, kappa, beta = (8, 4, 4, 4), 2, 0.12, 5.6
+    U = syn.random_links(L, 0.3, 2013)
+    lat = lqcd.Lattice(L, l0, -1)
+    olat = O.Lattice(L, l0, -1)
+    prm = lqcd.hmc_params(beta, kappa, 0.5, 2, (lqcd.SW, lqcd.LF), [2, 4], 0, 0, 1, roll=1,
+                          precision=lqcd.PREC_F32, tol=1e-11, block_solver=lqcd.SOLVER_SERIES)
+    oprm = O.hmc_params(beta, kappa, 0.5, 2, (O.SW, O.LF), [2, 4], 0, 0, 1, roll=1, tol=1e-13)
+    U1, res = lat.hmc_trajectory(cuda(U), prm, 2013, 1)
+    Uo, ores, st = olat.hmc_trajectory(U, oprm, 2013, 1)
+    assert st == 0
+    assert abs(res.dH - ores.dH) < 1e-4
+    assert res.accepted == ores.accepted and res.shift == ores.shift
+    assert rel(U1, Uo) < 1e-6
+    lat.close()
+
+
 @pytest.mark.parametrize("scheme,L,l0,kappa", [(2, (8, 4, 4, 4), 2, 0.15), (1, (12, 4, 4, 4), 2, 0.12)])
 def test_md_step_scheme_matches_oracle(scheme, L, l0, kappa):
     """position-dependent step sizes (Sec. 2): per-link dt * s(x0); links
