@@ -177,6 +177,22 @@ def oracle_threads():
 M_APPS_PER_TRAJ_DEFAULT = 25187.0
 
 
+def job_time(rank_ms, steps, dist=None, device="cpu"):
+    """whole-job timing of N replicas: the slowest rank's time of its timed
+    steps (max over ranks) and the job's seconds per trajectory, that time
+    divided by every trajectory of the job (weak scaling: each rank runs
+    `steps` trajectories of its own replica)"""
+    import torch
+
+    world = dist.get_world_size() if dist is not None else 1
+    total_ms = float(rank_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, total_ms / 1e3 / (steps * world)
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -278,12 +294,7 @@ def run_ours(args):
     launches = lqcd.lqcd_launch_count(lat.h) - l0_launch
     n_sol, ms_sol, by_sol = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
     lqcd.lqcd_profile_enable(lat.h, 0)
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = total_ms / 1e3 / (args.steps * world)
+    total_ms, value = job_time(sum(step_ms), args.steps, dist, "cuda")
 
     # ---- plain double-precision GPU form on the first timed input
     fp64 = None
@@ -558,11 +569,23 @@ def run_case(args):
         b = torch.randn((lat.V, 4, 3), dtype=torch.complex128, device="cuda", generator=g)
         lqcd.lqcd_profile_enable(lat.h, 1 << lqcd.KERNEL_SOLVER)
         out = {}
-        for name in ("block", "global"):
+        for name in ("block", "block_series", "global"):
             lqcd.lqcd_profile_reset(lat.h)
             if name == "block":
                 x, it, rs = lat.block_solve(b, WL["kappa"], -1, 0, prec, tol=WL["tol"])
                 it, rs = it[:lat.nb], max(rs[:lat.nb])
+            elif name == "block_series":
+                # the same 8 slab systems by the geometric series: W1,eo of the
+                # l0 = 4 slabs is the sub-slab operator of an l0 = 8 handle
+                lat2 = lqcd.Lattice(L, 2 * l0, -1, l0s=l0)
+                lat2.set_gauge(U)
+                lqcd.lqcd_profile_enable(lat2.h, 1 << lqcd.KERNEL_SOLVER)
+                x, it = lat2.solve_w3eo(b[:lat.Vh].contiguous(), WL["kappa"], 0.0, 0, prec, tol=WL["tol"],
+                                        method=lqcd.SOLVER_SERIES)
+                n, ms, by = lqcd.lqcd_profile_read(lat2.h, lqcd.KERNEL_SOLVER)
+                out[name] = {"iters": it[:lat2.nbs], "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6}
+                lat2.close()
+                continue
             else:
                 x, it, rs = lat.solve(b, WL["kappa"], 0, prec, tol=WL["tol"])
             n, ms, by = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
