@@ -59,8 +59,9 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes per k_solve launch from the ncu capture summarised in
 # profiles/k_solve_16x16x16x32_f32.md, valid only for the solver source
 # that was captured (bench.py reports null once the source differs)
-SOLVER_TRAFFIC = dict(src_sha256="331f6fdee00e104490d706e3b21799edf5354b64adacde20e9ff5540795f3d34",
-                      block=(332.964096e6 + 276.233984e6), glob=(411.375360e6 + 456.867584e6))
+SOLVER_TRAFFIC = dict(src_sha256="22301b6a483032528f6e8cef2339ea9e8b7e2f053e9e22b94dda621a929c7bda",
+                      block_series=(290.925568e6 + 142.578944e6), block=(329.253632e6 + 340.842240e6),
+                      glob=(434.955264e6 + 561.454592e6))
 
 
 def solver_traffic():
@@ -74,9 +75,10 @@ def solver_traffic():
         return None, None
     if sha != SOLVER_TRAFFIC["src_sha256"]:
         return None, None
-    return SOLVER_TRAFFIC["block"], {"batched_slab_solve": SOLVER_TRAFFIC["block"],
-                                     "global_solve": SOLVER_TRAFFIC["glob"],
-                                     "source": "profiles/k_solve_16x16x16x32_f32.md"}
+    return SOLVER_TRAFFIC["block_series"], {"batched_slab_solve_series": SOLVER_TRAFFIC["block_series"],
+                                            "batched_slab_solve_bicgstab": SOLVER_TRAFFIC["block"],
+                                            "global_solve_bicgstab": SOLVER_TRAFFIC["glob"],
+                                            "source": "profiles/k_solve_16x16x16x32_f32.md"}
 
 
 def hbm_peak():
