@@ -596,8 +596,9 @@ def run_case(args):
                           **out}), flush=True)
         lat.close()
     else:
-        # even-odd hopping sweep at 24^3 x 48 (fields larger than L2)
-        L = (48, 24, 24, 24)
+        # even-odd hopping sweep at 32^3 x 64, the lattice of the bench's
+        # Dslash figure (one launch moves 0.3-1.6 GB, far more than L2)
+        L = DSLASH_L
         lat = lqcd.Lattice(L, 8, -1)
         U = syn.random_links_torch(L, WL["eps"], WL["seed"], "cuda").contiguous()
         lat.set_gauge(U)
@@ -605,11 +606,12 @@ def run_case(args):
         lqcd.lqcd_profile_enable(lat.h, 1 << lqcd.KERNEL_HOP)
         out = {}
         for name, pr in (("f32", lqcd.PREC_F32), ("f16", lqcd.PREC_F16), ("f64", lqcd.PREC_F64)):
+            lat.dslash_eo(x, 0, 0.0, 0, lqcd.OP_HOP, pr)  # warm-up: launch 4k of this precision
             lqcd.lqcd_profile_reset(lat.h)
             for _ in range(3):
                 lat.dslash_eo(x, 0, 0.0, 0, lqcd.OP_HOP, pr)
             n, ms, by = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_HOP)
-            out[name] = {"ms": ms / n, "gbs": by / ms / 1e6}
+            out[name] = {"ms": ms / n, "gbs": by / ms / 1e6, "bytes_per_launch": by / n}
         print(json.dumps({"case": "dslash", "lattice": "x".join(map(str, L)), **out}), flush=True)
         lat.close()
 
