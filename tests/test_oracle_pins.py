@@ -290,6 +290,26 @@ def test_boundary_subspace():
     assert abs(np.vdot(lat.embed(c), lat.embed(c)) - np.vdot(c, c)) < 1e-12 * np.vdot(c, c).real
 
 
+def test_free_field_R_conserves_spatial_momentum():
+    """U = 1: R commutes with spatial translations, so a boundary field that
+    is a spatial plane wave exp(i p.x) stays one (with the same p), with a
+    boundary-coordinate amplitude matrix that does not depend on x"""
+    L = (8, 4, 2, 2)
+    lat = O.Lattice(L, 2, -1)
+    U = unit_links(lat.V)
+    nj = lat.nb // 2
+    x1, x2, x3 = np.meshgrid(np.arange(L[1]), np.arange(L[2]), np.arange(L[3]), indexing="ij")
+    p = 2 * np.pi * np.array([1, 1, 0]) / np.array(L[1:])
+    wave = np.exp(1j * (p[0] * x1 + p[1] * x2 + p[2] * x3)).reshape(-1)  # lexicographic (x1,x2,x3)
+    rng = np.random.default_rng(4)
+    amp = rng.standard_normal((nj, 2, 2, 3)) + 1j * rng.standard_normal((nj, 2, 2, 3))
+    c = amp[:, :, None, :, :] * wave[None, None, :, None, None]
+    out = lat.schur(U, 0.12, c, O.R, tol=1e-14)
+    ratio = out / wave[None, None, :, None, None]
+    assert np.max(np.abs(ratio - ratio[:, :, :1])) < 1e-12 * np.max(np.abs(ratio))
+    assert np.max(np.abs(ratio)) > 1e-3  # and the result is not trivially zero
+
+
 # ---------------------------------------------------------------------------
 # forces against central finite differences of the actions
 # ---------------------------------------------------------------------------
