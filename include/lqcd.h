@@ -11,6 +11,8 @@
  *   lqcd_last_error() gives a one-line description.  No function exits,
  *   traps or waits without bound: device-side waits are bounded and
  *   report LQCD_ERR_TIMEOUT.
+ * Threads: a handle is not thread-safe; calls on one handle must not
+ *   overlap (separate handles are independent).
  * Memory: every field pointer is a DEVICE pointer owned by the caller
  *   (16-byte aligned); the library reads/writes it on the handle's stream
  *   and owns only its internal workspace, allocated in lqcd_create.

@@ -512,7 +512,12 @@ std::vector<unsigned char> md_key(const lqcd_ctx* h, const lqcd_hmc_params& p)
                              (double)p.level_s2, (double)p.level_s1, p.rho, (double)p.precision, p.tol,
                              (double)p.max_iter, (double)p.eo_solver, (double)p.block_solver,
                              (double)p.step_scheme,
-                             (double)h->prof.on};
+                             (double)h->prof.on, (double)h->g1.l0s};
+    for (int q = 0; q < 3; ++q) {
+        k.push_back((double)h->tune.hop_bs[q]);
+        k.push_back((double)h->tune.solve_spt[q][0]);
+        k.push_back((double)h->tune.solve_spt[q][1]);
+    }
     for (int j = 0; j < LQCD_MAX_LEVELS; ++j) {
         k.push_back((double)p.scheme[j]);
         k.push_back((double)p.nsteps[j]);
