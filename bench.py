@@ -465,6 +465,20 @@ WL_PROD = dict(L=(32, 16, 16, 16), l0=16, l0s=8, kappa=0.1575, beta=5.6, eps=0.6
                levels="gauge/S1/S2/S3(R2)/S4(R)")
 
 
+# Table 1's last row (Sec. 3): 32 x 24^3, kappa = 0.15825, scheme C,
+# rho = 0.15, (n4, n3, n2, n1, n0) = (5, 3, 2, 2, 4): the configuration of
+# the paper's timing remark (about 2.5 h per trajectory on 8 CPUs), here on
+# a seeded quenched-thermalised field instead of the paper's ensemble
+WL_TABLE1 = dict(L=(32, 24, 24, 24), l0=16, l0s=8, kappa=0.15825, beta=5.6, eps=0.6, seed=2012, tau=1.0,
+                 nlevels=5, scheme=(1, 1, 0, 0, 0), nsteps=(4, 2, 2, 3, 5), lam=1.0 / 6.0,
+                 level_gauge=0, level_w2=-1, level_schur2=3, level_schur=4, rho=0.15, level_s2=2, level_s1=1,
+                 step_scheme=3, tol=1e-10, max_iter=40000, therm=40, name="table1",
+                 metric="s/HMC trajectory (32x24^3, kappa=0.15825, Table 1 schedule)",
+                 levels="gauge/S1/S2/S3(R2)/S4(R)",
+                 paper_context="about 2.5 h per trajectory on 8 CPUs (AMD Opteron 2.2 GHz, Cray XD1), "
+                               "the paper's thermalised ensemble (Sec. 3)")
+
+
 def run_iterated(args, W=WL_ITER):
     """--case iterated / production: K trajectories of a four-part action in
     the mixed-precision form, the first input again in the plain double
@@ -554,6 +568,7 @@ def run_iterated(args, W=WL_ITER):
                        "n_solves": results[-1].n_solves, "n_force": results[-1].n_force, "step_ms": step_ms},
         "acceptance": sum(r.accepted for r in results) / len(results),
         "fp64_form": fp64, "thermalisation_plaq": rth.plaq if rth else None, "clocks": clk,
+        "paper_context": W.get("paper_context"),
     }
     print(json.dumps(line), flush=True)
     lat.close()
@@ -573,6 +588,8 @@ def run_case(args):
         return run_iterated(args, WL_ITER)
     if args.case == "production":
         return run_iterated(args, WL_PROD)
+    if args.case == "table1":
+        return run_iterated(args, WL_TABLE1)
     if args.case == "solver":
         # the batched slab solve (8 slabs) and the global solve of the workload
         L, l0 = WL["L"], WL["l0"]
@@ -630,7 +647,7 @@ def run_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default=None, choices=["solver", "dslash", "iterated", "production"],
+    ap.add_argument("--case", default=None, choices=["solver", "dslash", "iterated", "production", "table1"],
                     help="run one small kernel case instead of the benchmark (profiler captures)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
