@@ -1425,6 +1425,10 @@ int lqcd_autotune(lqcd_t h, int what, double kappa)
                     cudaEventElapsedTime(&ms, e0, e1);
                     tmin[k] = std::min(tmin[k], ms);
                 }
+            if (st != LQCD_OK) {
+                h->tune.hop_bs[prec] = def;
+                break;
+            }
             int pick = def;
             float tdef = 1e30f;
             for (int k = 0; k < 3; ++k)
@@ -1458,8 +1462,19 @@ int lqcd_autotune(lqcd_t h, int what, double kappa)
                         cudaEventSynchronize(e1);
                         float ms = 0.f;
                         cudaEventElapsedTime(&ms, e0, e1);
-                        tmin[k] = std::min(tmin[k], (double)ms);
+                        if (st == LQCD_ERR_NOCONVERGE || st == LQCD_ERR_NAN) {
+                            // this precision does not solve the test system at
+                            // kappa: its schedule stays at the default
+                            st = LQCD_OK;
+                            tmin[k] = 2e30;
+                        } else {
+                            tmin[k] = std::min(tmin[k], (double)ms);
+                        }
                     }
+                if (st != LQCD_OK) {
+                    h->tune.solve_spt[prec][kind] = def;
+                    break;
+                }
                 int pick = def;
                 double tdef = 1e30;
                 for (int k = 0; k < 3; ++k)
