@@ -548,6 +548,32 @@ def run_iterated(args, W=WL_ITER):
         fp64 = {"s_per_traj": t64, "dH": r64.dH, "dH_mixed": results[0].dH,
                 "abs_dH_diff": abs(r64.dH - results[0].dH), "speedup_mixed_vs_fp64": t64 / (step_ms[0] / 1e3),
                 "accepted": r64.accepted}
+    # force profile of every term (Sec. 3, Fig. 1 analogue) on the field of
+    # the last trajectory, pseudo-fermions drawn as the heatbath draws them
+    profile = {}
+    if W.get("level_s1", -1) >= 0 and not args.no_dslash:
+        lat.set_gauge(U)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(W["seed"] + 11)
+
+        def gauss(shape):
+            return (torch.randn(shape, dtype=torch.complex128, device="cuda", generator=g)
+                    * math.sqrt(0.5)).contiguous()
+
+        k, rho = W["kappa"], W["rho"]
+        tol = W["tol"]
+        phi4 = lat.schur(gauss(lat.boundary().shape), k, lqcd.SCHUR_R, lqcd.PREC_F32, tol=tol)
+        phi3 = lat.schur(gauss(lat.boundary2().shape), k, lqcd.SCHUR2_R, lqcd.PREC_F32, tol=tol)
+        e2, _ = lat.solve_w3eo(gauss((lat.Vh, 4, 3)), k, rho, 0, lqcd.PREC_F32, tol=tol)
+        phi2 = lat.w3eo(e2, k, 0.0)
+        phi1 = lat.w3eo(gauss((lat.Vh, 4, 3)), k, rho)
+        terms = {"S4": lat.pf_force(phi4, k, lqcd.TERM_SCHUR, lqcd.PREC_F32, tol)[1],
+                 "S3": lat.pf_force(phi3, k, lqcd.TERM_SCHUR2, lqcd.PREC_F32, tol)[1],
+                 "S2": lat.pf_force_eo(phi2, k, rho, lqcd.TERM_S2, lqcd.PREC_F32, tol)[1],
+                 "S1": lat.pf_force_eo(phi1, k, rho, lqcd.TERM_S1, lqcd.PREC_F32, tol)[1],
+                 "S0": lat.gauge_force(W["beta"])[2]}
+        for name, F in terms.items():
+            profile[name] = [round(v, 5) for v in lat.force_profile(F)[0].tolist()]
     peak, peak_kind = hbm_peak()
     achieved = by_sol / ms_sol / 1e6 if ms_sol > 0 else None
     line = {
@@ -569,6 +595,7 @@ def run_iterated(args, W=WL_ITER):
         "acceptance": sum(r.accepted for r in results) / len(results),
         "fp64_form": fp64, "thermalisation_plaq": rth.plaq if rth else None, "clocks": clk,
         "paper_context": W.get("paper_context"),
+        "force_profile_spatial": profile,
     }
     print(json.dumps(line), flush=True)
     lat.close()
