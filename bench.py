@@ -409,7 +409,7 @@ def run_ours(args):
         "metric": "s/HMC trajectory (16^3x32 Schwarz HMC, mixed precision batched)",
         "value": value, "unit": "s/trajectory", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.precision + "-storage/f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "lattice": "x".join(map(str, L)), "l0": l0,
                    "inner_precision": args.precision, "l2": "flushed between timed trajectories",
