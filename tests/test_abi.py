@@ -53,3 +53,30 @@ def test_create_rejects_bad_geometry_without_gpu(lib):
         assert st == -2, (L, l0, st)
     st = lib.lqcd_create(ctypes.byref(h), (ctypes.c_int * 4)(4, 4, 4, 4), 1, 3, None)
     assert st == -1
+
+
+def test_create_rejects_oversized_lattice_without_gpu(lib):
+    # 128 x 128^2 x 64 sites exceed the 32-bit index range of the internal
+    # fields: rejected on the host
+    h = ctypes.c_void_p()
+    st = lib.lqcd_create(ctypes.byref(h), (ctypes.c_int * 4)(128, 128, 128, 64), 8, -1, None)
+    assert st == -2
+
+
+def test_static_gauge_action_validates_on_the_host(lib):
+    f = lib.lqcd_gauge_action_static
+    f.argtypes = [ctypes.POINTER(ctypes.c_int * 4), ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    dummy = ctypes.c_void_p(16)  # never dereferenced: every case fails before any device access
+    ok_L = (ctypes.c_int * 4)(4, 4, 4, 4)
+    assert f(ctypes.byref(ok_L), None, 5.6, dummy, None) == -1
+    assert f(ctypes.byref(ok_L), dummy, 5.6, None, None) == -1
+    assert f(ctypes.byref((ctypes.c_int * 4)(4, 3, 4, 4)), dummy, 5.6, dummy, None) == -2
+    # more than 2,097,152 sites: beyond the fixed partial-sum array
+    assert f(ctypes.byref((ctypes.c_int * 4)(128, 32, 32, 32)), dummy, 5.6, dummy, None) == -2
+
+
+def test_null_handle_is_an_argument_error(lib):
+    for name, args in [("lqcd_set_gauge", [None, None]), ("lqcd_launch_count", [None, None]),
+                       ("lqcd_set_subslabs", [None, 0])]:
+        assert getattr(lib, name)(*args) == -1, name

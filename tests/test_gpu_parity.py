@@ -21,8 +21,11 @@ from paper_0710_0066_gb300 import lqcd  # noqa: E402
 
 # (L, l0, eps, kappa): the 4^4 and 16x8^3 rows are the small and the solver
 # configurations (kappa = 0.15 and 0.156); eps = 0.6 at kappa = 0.156 keeps
-# the synthetic field on the positive-mass side, like the paper's ensembles
-GEOMS = [((4, 4, 4, 4), 2, 0.3, 0.15), ((8, 4, 2, 6), 2, 0.3, 0.14), ((16, 8, 8, 8), 4, 0.6, 0.156)]
+# the synthetic field on the positive-mass side, like the paper's ensembles;
+# 8x4^3 with l0 = 1 is the degenerate slab of one time slice (both faces of
+# a black slab on the same slice, W1 without time-like hops)
+GEOMS = [((4, 4, 4, 4), 2, 0.3, 0.15), ((8, 4, 2, 6), 2, 0.3, 0.14), ((16, 8, 8, 8), 4, 0.6, 0.156),
+         ((8, 4, 4, 4), 1, 0.3, 0.14)]
 
 
 def rel(a, b):
