@@ -254,7 +254,7 @@ def run_ours(args):
         return lqcd.hmc_params(WL["beta"], WL["kappa"], WL["tau"], WL["nlevels"], WL["scheme"], WL["nsteps"],
                                WL["level_gauge"], WL["level_w1"], WL["level_schur"], lam=WL["lam"], roll=1,
                                metropolis=1, precision=prec, tol=WL["tol"], max_iter=WL["max_iter"],
-                               use_graph=0 if args.no_graph else 1,
+                               use_graph=0 if args.no_graph else 1, chrono=0 if args.no_chrono else 1,
                                block_solver=lqcd.SOLVER_SERIES if args.block_solver == "series"
                                else lqcd.SOLVER_BICGSTAB)
 
@@ -414,7 +414,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD_NAME, "lattice": "x".join(map(str, L)), "l0": l0,
                    "inner_precision": args.precision, "l2": "flushed between timed trajectories",
                    "parallelism": "replicas" if world > 1 else "1 GPU", "autotune": tune,
-                   "md_as_cuda_graph": not args.no_graph, "w1_block_solver": block_solver},
+                   "md_as_cuda_graph": not args.no_graph, "w1_block_solver": block_solver,
+                   "chronological_guesses": not args.no_chrono},
         "roofline": {"bound": "hbm", "kernel": "persistent batched solver (k_solve)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -504,7 +505,7 @@ def run_iterated(args, W=WL_ITER):
                                level_s2=W.get("level_s2", -1), level_s1=W.get("level_s1", -1),
                                step_scheme=W.get("step_scheme", 0),
                                eo_solver=lqcd.SOLVER_SERIES if args.eo_solver == "series" else lqcd.SOLVER_BICGSTAB,
-                               use_graph=0 if args.no_graph else 1)
+                               use_graph=0 if args.no_graph else 1, chrono=0 if args.no_chrono else 1)
 
     prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     prm = params(prec)
@@ -583,6 +584,7 @@ def run_iterated(args, W=WL_ITER):
         "config": {"lattice": "x".join(map(str, L)), "l0": W["l0"], "l0s": W["l0s"], "kappa": W["kappa"],
                    "beta": W["beta"], "nsteps": W["nsteps"], "levels": W["levels"], "rho": W.get("rho"),
                    "step_scheme": W.get("step_scheme", 0), "scheme": W["scheme"], "eo_solver": args.eo_solver,
+                   "chronological_guesses": not args.no_chrono,
                    "thermalisation": "%d pure-gauge trajectories from exp(i %.1f H)" % (W["therm"], W["eps"]),
                    "autotune": tune,
                    "l2": "flushed between timed trajectories"},
@@ -691,6 +693,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-chrono", action="store_true",
+                    help="start every force solve from zero instead of the previous solution of its term")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the molecular dynamics eagerly instead of replaying it as a CUDA graph")
     args = ap.parse_args()

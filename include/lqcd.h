@@ -315,6 +315,14 @@ typedef struct {
                            solves inside report failures once, after the
                            replay.  Same kernels in the same order: the
                            results equal the eager run's. */
+    int chrono;         /* 1: each force solve of the molecular dynamics
+                           starts from the solution of the same solve at the
+                           previous force evaluation of its term (the first
+                           one of a trajectory from zero); the solves still
+                           run to tol, so the forces agree with chrono = 0 to
+                           the solver tolerance, and reversibility holds to
+                           it.  Needs 12 extra full double fields on the
+                           device (allocated on first use). */
 } lqcd_hmc_params;
 
 /* Pseudo-fermion fields of lqcd_md (device pointers, NULL where the term

@@ -61,10 +61,12 @@ int hop_full(lqcd_ctx* h, int mode, int dag, int colour, double2* out, const dou
 }
 
 // x = W^-1 b (block: W1 on the slabs of `colour`; global: M).  x, b full
-// double fields, b is not modified, x must not alias b.
+// double fields, b is not modified, x must not alias b.  slot >= 0: the
+// previous solution kept in chronological slot `slot` (if valid) is the
+// initial guess, and the new solution replaces it.
 int solve_full(lqcd_ctx* h, int mode, int colour, int dagger, int prec, double kappa, double2* x,
                const double2* b, double tol, int max_iter, int* iters, double* resid,
-               int method = SOLVER_BICGSTAB)
+               int method = SOLVER_BICGSTAB, int slot = -1)
 {
     const int Vh = h->g.Vh;
     const double2* bb = b;
@@ -73,15 +75,29 @@ int solve_full(lqcd_ctx* h, int mode, int colour, int dagger, int prec, double k
         bb = fld(h, F_T1);
     }
     const int col = mode == MODE_ALL ? -1 : colour;
+    double2* cb = slot >= 0 ? h->chrono_buf[slot] : nullptr;
+    int guess = 0;
+    if (cb && h->chrono_valid[slot]) {
+        // the even part of the unknown: gamma5 x_prev for the adjoint system
+        if (dagger) LQ_TRY(gamma5_full(h, x, cb));
+        else LQ_CUDA(h, cudaMemcpyAsync(x, cb, sizeof(double2) * 12 * (size_t)Vh, cudaMemcpyDeviceToDevice,
+                                        h->stream));
+        guess = 1;
+    }
     // b_e' = b_e + kappa H_eo b_o
     LQ_TRY(hop_sweep(h, PREC64, mode, 0, 0, col, sp64(fld(h, F_T2), 0, Vh), sp64((double2*)bb, 1, Vh), 1.0,
                      sp64((double2*)bb, 0, Vh), kappa));
-    LQ_TRY(eo_solve(h, mode, col, prec, kappa, x, fld(h, F_T2), tol, max_iter, iters, resid, 1.0, method));
+    LQ_TRY(eo_solve(h, mode, col, prec, kappa, x, fld(h, F_T2), tol, max_iter, iters, resid, 1.0, method,
+                    guess));
     // x_o = b_o + kappa H_oe x_e
     LQ_TRY(hop_sweep(h, PREC64, mode, 0, 1, col, sp64(x, 1, Vh), sp64(x, 0, Vh), 1.0, sp64((double2*)bb, 1, Vh),
                      kappa));
     if (col >= 0) LQ_TRY(keep_colour(h, x, col));
     if (dagger) LQ_TRY(gamma5_full(h, x, x));
+    if (cb) {
+        LQ_CUDA(h, cudaMemcpyAsync(cb, x, sizeof(double2) * 24 * (size_t)Vh, cudaMemcpyDeviceToDevice, h->stream));
+        h->chrono_valid[slot] = true;
+    }
     return LQCD_OK;
 }
 
@@ -90,7 +106,11 @@ struct SolveCfg {
     double tol;
     int max_iter;
     int method = SOLVER_BICGSTAB;  // inner iteration of the W3,eo / W2,eo solves
+    int slot = -1;                 // first chronological slot of the term (force solves), or -1
 };
+
+// slot k + 1 for the second (adjoint) solve of a term, or -1
+inline int next_slot(int k) { return k >= 0 ? k + 1 : -1; }
 
 // R, R^dag, R^-1, R^-dag on boundary coordinates (device doubles)
 int schur_op(lqcd_ctx* h, double* out, const double* in, double kappa, int op, const SolveCfg& c)
@@ -131,11 +151,11 @@ int pf_w1(lqcd_ctx* h, double* F, const double2* phi, double kappa, double coef,
 {
     double2 *eta = fld(h, F_A), *xi = fld(h, F_B);
     LQ_TRY(solve_full(h, MODE_INTRA, -1, 0, c.prec, kappa, eta, phi, c.tol, c.max_iter, nullptr, nullptr,
-                      c.method));
+                      c.method, c.slot));
     if (S_dev) LQ_TRY(norm2_dev(h, (const double*)eta, (int64_t)48 * h->g.Vh, S_dev));
     if (!F) return LQCD_OK;
     LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, xi, eta, c.tol, c.max_iter, nullptr, nullptr,
-                      c.method));
+                      c.method, next_slot(c.slot)));
     return force_bilinear(h, F, xi, eta, MODE_INTRA, kappa * coef, nullptr, nullptr, 0, 0.0, c.prec, ss);
 }
 
@@ -148,14 +168,16 @@ int pf_schur(lqcd_ctx* h, double* F, const double* phi, double kappa, double coe
     const int nbd = 2 * nbnd_of(h->g);
     double* eta = h->bnd[1];
     LQ_TRY(embed_boundary(h, A, phi));
-    LQ_TRY(solve_full(h, MODE_ALL, -1, 0, c.prec, kappa, psi, A, c.tol, c.max_iter, nullptr, nullptr));
+    LQ_TRY(solve_full(h, MODE_ALL, -1, 0, c.prec, kappa, psi, A, c.tol, c.max_iter, nullptr, nullptr,
+                      SOLVER_BICGSTAB, c.slot));
     LQ_TRY(hop_full(h, MODE_INTRA, 0, 1, C, psi, 1.0, psi, -kappa));
     LQ_TRY(project_boundary(h, eta, C));
     if (S_dev) LQ_TRY(norm2_dev(h, eta, nbd, S_dev));
     if (!F) return LQCD_OK;
     LQ_TRY(embed_boundary(h, et, eta));
     LQ_TRY(hop_full(h, MODE_INTRA, 1, 1, E, et, 1.0, et, -kappa));
-    LQ_TRY(solve_full(h, MODE_ALL, -1, 1, c.prec, kappa, chi, E, c.tol, c.max_iter, nullptr, nullptr));
+    LQ_TRY(solve_full(h, MODE_ALL, -1, 1, c.prec, kappa, chi, E, c.tol, c.max_iter, nullptr, nullptr,
+                      SOLVER_BICGSTAB, next_slot(c.slot)));
     return force_bilinear(h, F, et, psi, MODE_INTRA, -kappa * coef, chi, psi, MODE_ALL, kappa * coef, c.prec, ss);
 }
 
@@ -235,14 +257,16 @@ int pf_schur2(lqcd_ctx* h, double* F, const double* phi, double kappa, double co
             *chi = fld(h, F_G);
     double* eta = h->bnd[1];
     LQ_TRY(embed2(h, A, phi));
-    LQ_TRY(solve_full(h, MODE_INTRA, -1, 0, c.prec, kappa, psi, A, c.tol, c.max_iter, nullptr, nullptr));
+    LQ_TRY(solve_full(h, MODE_INTRA, -1, 0, c.prec, kappa, psi, A, c.tol, c.max_iter, nullptr, nullptr,
+                      SOLVER_BICGSTAB, c.slot));
     LQ_TRY(sub_hop(h, 0, 1, C, psi, 1.0, psi, -kappa));
     LQ_TRY(project2(h, eta, C));
     if (S_dev) LQ_TRY(norm2_dev(h, eta, 2 * nbnd2_of(h->g1), S_dev));
     if (!F) return LQCD_OK;
     LQ_TRY(embed2(h, et, eta));
     LQ_TRY(sub_hop(h, 1, 1, E, et, 1.0, et, -kappa));
-    LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, chi, E, c.tol, c.max_iter, nullptr, nullptr));
+    LQ_TRY(solve_full(h, MODE_INTRA, -1, 1, c.prec, kappa, chi, E, c.tol, c.max_iter, nullptr, nullptr,
+                      SOLVER_BICGSTAB, next_slot(c.slot)));
     return force_bilinear(h, F, et, psi, MODE_INTRA2, -kappa * coef, chi, psi, MODE_INTRA, kappa * coef, c.prec,
                           ss);
 }
@@ -271,16 +295,29 @@ int w3eo_apply(lqcd_ctx* h, double2* out, const double2* in, double kappa, doubl
 // x_e = W3,eo^-1 b_e, all sub-slabs in one batched launch (dag: W3,eo^-dag =
 // g5 W3,eo^-1 g5); x must not alias b
 int w3eo_solve(lqcd_ctx* h, double2* x, const double2* b, double kappa, double rho, int dag, const SolveCfg& c,
-               int* iters = nullptr, double* resid = nullptr)
+               int* iters = nullptr, double* resid = nullptr, int slot = -1)
 {
     GeoScope sc(h, sub_geo(h->g1));
+    const size_t half = sizeof(double2) * 12 * (size_t)h->g.Vh;
     const double2* bb = b;
     if (dag) {
         LQ_TRY(gamma5_full(h, fld(h, F_T2), b));
         bb = fld(h, F_T2);
     }
-    LQ_TRY(eo_solve(h, MODE_INTRA, -1, c.prec, kappa, x, bb, c.tol, c.max_iter, iters, resid, 1.0 + rho, c.method));
+    double2* cb = slot >= 0 ? h->chrono_buf[slot] : nullptr;
+    int guess = 0;
+    if (cb && h->chrono_valid[slot]) {  // previous solution as the initial guess
+        if (dag) LQ_TRY(gamma5_full(h, x, cb));
+        else LQ_CUDA(h, cudaMemcpyAsync(x, cb, half, cudaMemcpyDeviceToDevice, h->stream));
+        guess = 1;
+    }
+    LQ_TRY(eo_solve(h, MODE_INTRA, -1, c.prec, kappa, x, bb, c.tol, c.max_iter, iters, resid, 1.0 + rho, c.method,
+                    guess));
     if (dag) LQ_TRY(gamma5_full(h, x, x));
+    if (cb) {
+        LQ_CUDA(h, cudaMemcpyAsync(cb, x, half, cudaMemcpyDeviceToDevice, h->stream));
+        h->chrono_valid[slot] = true;
+    }
     return LQCD_OK;
 }
 
@@ -299,10 +336,10 @@ int pf_s1(lqcd_ctx* h, double* F, const double2* phi, double kappa, double rho, 
           double* S_dev, const double* ss = nullptr)
 {
     double2 *eta = fld(h, F_A), *xi = fld(h, F_B);
-    LQ_TRY(w3eo_solve(h, eta, phi, kappa, rho, 0, c));
+    LQ_TRY(w3eo_solve(h, eta, phi, kappa, rho, 0, c, nullptr, nullptr, c.slot));
     if (S_dev) LQ_TRY(norm2_dev(h, (const double*)eta, (int64_t)24 * h->g.Vh, S_dev));
     if (!F) return LQCD_OK;
-    LQ_TRY(w3eo_solve(h, xi, eta, kappa, rho, 1, c));
+    LQ_TRY(w3eo_solve(h, xi, eta, kappa, rho, 1, c, nullptr, nullptr, next_slot(c.slot)));
     return eo_force(h, F, xi, eta, kappa * kappa * coef, c.prec, ss);
 }
 
@@ -310,12 +347,12 @@ int pf_s2(lqcd_ctx* h, double* F, const double2* phi, double kappa, double rho, 
           double* S_dev, const double* ss = nullptr)
 {
     double2 *zeta = fld(h, F_A), *lam = fld(h, F_B), *chi = fld(h, F_C);
-    LQ_TRY(w3eo_solve(h, zeta, phi, kappa, 0.0, 0, c));
+    LQ_TRY(w3eo_solve(h, zeta, phi, kappa, 0.0, 0, c, nullptr, nullptr, c.slot));
     LQ_TRY(axpby_full(h, chi, 1.0, phi, 0.0, -1));
     LQ_TRY(axpby_full(h, chi, rho, zeta, 1.0, -1));
     if (S_dev) LQ_TRY(norm2_dev(h, (const double*)chi, (int64_t)24 * h->g.Vh, S_dev));
     if (!F) return LQCD_OK;
-    LQ_TRY(w3eo_solve(h, lam, chi, kappa, 0.0, 1, c));
+    LQ_TRY(w3eo_solve(h, lam, chi, kappa, 0.0, 1, c, nullptr, nullptr, next_slot(c.slot)));
     return eo_force(h, F, lam, zeta, rho * kappa * kappa * coef, c.prec, ss);
 }
 
@@ -370,6 +407,21 @@ void build_step(const lqcd_hmc_params& p, int j, double dt, std::vector<Op>& v)
     }
 }
 
+// the chronological slots of the force solves (full double fields, zeroed
+// once: a slot's odd half is never read as a guess); before any capture
+int chrono_alloc(lqcd_ctx* h, const lqcd_hmc_params* p)
+{
+    if (!p->chrono) return LQCD_OK;
+    const size_t bytes = sizeof(double2) * 24 * (size_t)h->g.Vh;
+    for (int k = 0; k < lqcd_ctx::NCHRONO; ++k) {
+        if (h->chrono_buf[k]) continue;
+        LQ_CUDA(h, cudaMalloc(&h->chrono_buf[k], bytes));
+        LQ_CUDA(h, cudaMemsetAsync(h->chrono_buf[k], 0, bytes, h->stream));
+        h->chrono_valid[k] = false;
+    }
+    return LQCD_OK;
+}
+
 int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
 {
     if (!p || p->nlevels < 1 || p->nlevels > LQCD_MAX_LEVELS || !(p->tau > 0) || !prec_ok(p->precision) || !(p->tol > 0)) {
@@ -399,6 +451,10 @@ int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
     }
     if (p->use_graph != 0 && p->use_graph != 1) {
         h->err = "hmc params: use_graph must be 0 or 1";
+        return LQCD_ERR_ARG;
+    }
+    if (p->chrono != 0 && p->chrono != 1) {
+        h->err = "hmc params: chrono must be 0 or 1";
         return LQCD_ERR_ARG;
     }
     if ((p->eo_solver != LQCD_SOLVER_BICGSTAB && p->eo_solver != LQCD_SOLVER_SERIES) ||
@@ -467,9 +523,15 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
     const int top = p.nlevels - 1;
     const double dt = p.tau / p.nsteps[top];
     for (int i = 0; i < p.nsteps[top]; ++i) build_step(p, top, dt, ops);
-    SolveCfg c{p.precision, p.tol, p.max_iter};
-    const SolveCfg ceo{p.precision, p.tol, p.max_iter, p.eo_solver};
-    const SolveCfg cblk{p.precision, p.tol, p.max_iter, p.block_solver};
+    // chronological slots (two per term: the solve and its adjoint)
+    const bool ch = p.chrono != 0;
+    const SolveCfg cw1{p.precision, p.tol, p.max_iter, p.block_solver, ch ? 0 : -1};
+    const SolveCfg csch{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? 2 : -1};
+    const SolveCfg cw2{p.precision, p.tol, p.max_iter, p.block_solver, ch ? 4 : -1};
+    const SolveCfg csch2{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? 6 : -1};
+    const SolveCfg cs2{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 8 : -1};
+    const SolveCfg cs1{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 10 : -1};
+    for (bool& v : h->chrono_valid) v = false;
     for (const Op& o : ops) {
         if (o.kind == 1) {
             LQ_TRY(update_links(h, P, o.dt, ss));
@@ -477,27 +539,27 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
         }
         if (p.level_gauge == o.level) LQ_TRY(gauge_force_kick(h, P, -o.dt * p.beta / 6.0, p.precision, ss));
         if (p.level_w1 == o.level) {
-            LQ_TRY(pf_w1(h, P, pf.phi1, p.kappa, -o.dt, cblk, nullptr, ss));
+            LQ_TRY(pf_w1(h, P, pf.phi1, p.kappa, -o.dt, cw1, nullptr, ss));
             ++*nforce;
         }
         if (p.level_schur == o.level) {
-            LQ_TRY(pf_schur(h, P, pf.phi2, p.kappa, -o.dt, c, nullptr, ss));
+            LQ_TRY(pf_schur(h, P, pf.phi2, p.kappa, -o.dt, csch, nullptr, ss));
             ++*nforce;
         }
         if (p.level_w2 == o.level) {
-            LQ_TRY(pf_w2(h, P, pf.phi3, p.kappa, -o.dt, cblk, nullptr, ss));
+            LQ_TRY(pf_w2(h, P, pf.phi3, p.kappa, -o.dt, cw2, nullptr, ss));
             ++*nforce;
         }
         if (p.level_schur2 == o.level) {
-            LQ_TRY(pf_schur2(h, P, pf.phi4, p.kappa, -o.dt, c, nullptr, ss));
+            LQ_TRY(pf_schur2(h, P, pf.phi4, p.kappa, -o.dt, csch2, nullptr, ss));
             ++*nforce;
         }
         if (p.level_s2 == o.level) {
-            LQ_TRY(pf_s2(h, P, pf.phi5, p.kappa, p.rho, -o.dt, ceo, nullptr, ss));
+            LQ_TRY(pf_s2(h, P, pf.phi5, p.kappa, p.rho, -o.dt, cs2, nullptr, ss));
             ++*nforce;
         }
         if (p.level_s1 == o.level) {
-            LQ_TRY(pf_s1(h, P, pf.phi6, p.kappa, p.rho, -o.dt, ceo, nullptr, ss));
+            LQ_TRY(pf_s1(h, P, pf.phi6, p.kappa, p.rho, -o.dt, cs1, nullptr, ss));
             ++*nforce;
         }
     }
@@ -511,7 +573,7 @@ std::vector<unsigned char> md_key(const lqcd_ctx* h, const lqcd_hmc_params& p)
                              (double)p.level_w1, (double)p.level_schur, (double)p.level_w2, (double)p.level_schur2,
                              (double)p.level_s2, (double)p.level_s1, p.rho, (double)p.precision, p.tol,
                              (double)p.max_iter, (double)p.eo_solver, (double)p.block_solver,
-                             (double)p.step_scheme,
+                             (double)p.step_scheme, (double)p.chrono,
                              (double)h->prof.on, (double)h->g1.l0s};
     for (int q = 0; q < 3; ++q) {
         k.push_back((double)h->tune.hop_bs[q]);
@@ -830,6 +892,7 @@ int lqcd_destroy(lqcd_t h)
     solver_free(h);
     cudaFree(h->U64);
     cudaFree(h->U64_save);
+    for (double2* f : h->chrono_buf) cudaFree(f);
     cudaFree(h->U32);
     cudaFree(h->U16);
     for (double2* f : h->f64) cudaFree(f);
@@ -1160,6 +1223,7 @@ int lqcd_md(lqcd_t h, double* U, double* P, const lqcd_pf_fields* f, const lqcd_
     CHECK_H(h);
     NEED(U && P && f, "null U / P / fields");
     LQ_TRY(check_params(h, prm));
+    LQ_TRY(chrono_alloc(h, prm));
     NEED(prm->level_w1 < 0 || f->w1, "the W1 field is needed");
     NEED(prm->level_schur < 0 || f->schur, "the boundary field is needed");
     NEED(prm->level_w2 < 0 || f->w2, "the W2 field is needed");
@@ -1247,6 +1311,7 @@ int lqcd_hmc_trajectory(lqcd_t h, double* U, const lqcd_hmc_params* prm, uint64_
     CHECK_H(h);
     NEED(U && res, "null U / result");
     LQ_TRY(check_params(h, prm));
+    LQ_TRY(chrono_alloc(h, prm));
     const lqcd_hmc_params& p = *prm;
     const Geo& g = h->g;
     const int nbd = 2 * nbnd_of(g);

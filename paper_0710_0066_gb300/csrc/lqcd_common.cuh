@@ -548,6 +548,11 @@ struct lqcd_ctx {
     cudaGraphExec_t md_exec = nullptr;
     std::vector<unsigned char> md_key;  // parameters the graph was recorded for
     int64_t md_launches = 0;            // kernels per replay
+    // chronological initial guesses of the MD's solves (one full double
+    // field per solve site of the force terms)
+    static constexpr int NCHRONO = 12;
+    double2* chrono_buf[NCHRONO] = {};
+    bool chrono_valid[NCHRONO] = {};
     int md_nforce = 0;                  // force evaluations per replay
     int md_solves = 0;                  // solves per replay
     int64_t iter_count = 0;  // inner iterations since reset (trajectory stats)
@@ -640,9 +645,11 @@ void solver_site_bytes(int prec, int method, double* inner, double* outer);
 // `method`: inner iteration, BiCGstab or the geometric series (which needs
 // the spectral radius of kappa^2 H_eo H_oe / diag below one)
 enum { SOLVER_BICGSTAB = 0, SOLVER_SERIES = 1 };
+// `guess`: 1 if x_e holds an initial guess (its residual is computed in
+// double before the first inner cycle), 0 to start from x = 0
 int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e,
              const double2* b_e, double tol, int max_iter, int* iters_sys, double* resid_sys,
-             double diag = 1.0, int method = SOLVER_BICGSTAB);
+             double diag = 1.0, int method = SOLVER_BICGSTAB, int guess = 0);
 
 // force.cu
 // prec: PREC64 runs the link arithmetic in double, otherwise in single

@@ -39,6 +39,7 @@ struct SolveArgs {
     double k2;
     double diag;  // the system is diag - k2 H_eo H_oe (1, or 1 + rho for W3,eo)
     int method;   // SOLVER_BICGSTAB or SOLVER_SERIES (inner iteration)
+    int guess;    // 1: x holds an initial guess on entry, 0: start from x = 0
     int nsys, cps;
     int slab0, slabstep;
     int nsite;
@@ -229,7 +230,8 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
     unsigned epoch = 0;
     int rb = 0;  // partial-sum buffer
 
-    // ---- x = 0, r64 = b, |b|^2
+    // ---- x = 0, r64 = b, |b|^2; with an initial guess (x given): |b|^2 and
+    // t64 = H_oe x here, r64 = b - diag x + k2 H_eo t64 below
     {
         double q = 0.0;
         FOR_SITES
@@ -237,12 +239,17 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             const int i = base + j_;
             Spinor<double> bb, z;
             load_spinor<PREC64, true>(A.b, i, bb);
-            store_spinor<PREC64>(A.r64, i, bb);
+            if (A.guess) {
+                hop_site<PREC64, false>(A.g, A.mode, 0, 1, i, A.x, A.U64, z);
+                store_spinor<PREC64>(A.t64, i, z);
+            } else {
+                store_spinor<PREC64>(A.r64, i, bb);
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
+                for (int s = 0; s < 4; ++s)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) z.c[s][c] = mk(0.0, 0.0);
-            store_spinor<PREC64>(A.x, i, z);
+                    for (int c = 0; c < 3; ++c) z.c[s][c] = mk(0.0, 0.0);
+                store_spinor<PREC64>(A.x, i, z);
+            }
             q += nrm_acc(bb);
         }
         reduce_put(A, q, 0.0, 0.0, 1, rb);
@@ -254,6 +261,37 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             S.it = 0;
         }
         __syncthreads();
+    }
+    if (A.guess) {
+        double q = 0.0;
+        FOR_SITES
+        {
+            const int i = base + j_;
+            Spinor<double> a, xx, bb;
+            hop_site<PREC64, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, a);
+            load_spinor<PREC64, false>(A.x, i, xx);
+            load_spinor<PREC64, true>(A.b, i, bb);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) a.c[s][c] = bb.c[s][c] - A.diag * xx.c[s][c] + A.k2 * a.c[s][c];
+            store_spinor<PREC64>(A.r64, i, a);
+            q += nrm_acc(a);
+        }
+        reduce_put(A, q, 0.0, 0.0, 1, rb);
+        SYNC_OR_RETURN;
+        gather_own(A, sys, 1, red, rb);
+        if (tid == 0) S.rn2 = red[0];
+        __syncthreads();
+        if (!(S.bn2 > 0.0)) FOR_SITES  // b = 0: the solution is 0, whatever the guess
+            {
+                Spinor<double> z;
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) z.c[s][c] = mk(0.0, 0.0);
+                store_spinor<PREC64>(A.x, base + j_, z);
+            }
     }
 
     int outer = 0, final_flag = F_DONE;
@@ -821,7 +859,7 @@ void solver_site_bytes(int prec, int method, double* inner, double* outer)
 }
 
 int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e, const double2* b_e,
-             double tol, int max_iter, int* iters_sys, double* resid_sys, double diag, int method)
+             double tol, int max_iter, int* iters_sys, double* resid_sys, double diag, int method, int guess)
 {
     Work* w = h->work;
     const Geo& g = h->g;
@@ -831,6 +869,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.k2 = kappa * kappa;
     A.diag = diag;
     A.method = method;
+    A.guess = guess;
     if (mode == MODE_INTRA) {
         A.nsys = colour < 0 ? g.nb : g.nb / 2;
         A.slab0 = colour < 0 ? 0 : colour;

@@ -51,7 +51,7 @@ class HmcParams(C.Structure):
         ("tol", C.c_double), ("max_iter", C.c_int), ("step_scheme", C.c_int), ("step_scale", C.c_void_p),
         ("level_w2", C.c_int), ("level_schur2", C.c_int),
         ("rho", C.c_double), ("level_s2", C.c_int), ("level_s1", C.c_int), ("eo_solver", C.c_int),
-        ("block_solver", C.c_int), ("use_graph", C.c_int),
+        ("block_solver", C.c_int), ("use_graph", C.c_int), ("chrono", C.c_int),
     ]
 
 
@@ -71,7 +71,8 @@ class HmcResult(C.Structure):
 def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w1=0, level_schur=0,
                lam=1.0 / 6.0, pf_init=0, roll=0, metropolis=1, precision=PREC_F64, tol=1e-10,
                max_iter=20000, step_scheme=0, step_scale=None, level_w2=-1, level_schur2=-1, rho=0.0,
-               level_s2=-1, level_s1=-1, eo_solver=SOLVER_BICGSTAB, block_solver=SOLVER_BICGSTAB, use_graph=0):
+               level_s2=-1, level_s1=-1, eo_solver=SOLVER_BICGSTAB, block_solver=SOLVER_BICGSTAB, use_graph=0,
+               chrono=0):
     """step_scale: None or a host float64 array (2, L0) of s(x0) (space-like,
     time-like rows); it is kept alive on the returned object"""
     sc = list(scheme) + [0] * (MAX_LEVELS - len(scheme))
@@ -79,7 +80,7 @@ def hmc_params(beta, kappa, tau, nlevels, scheme, nsteps, level_gauge=0, level_w
     p = HmcParams(beta, kappa, tau, lam, nlevels, (C.c_int * MAX_LEVELS)(*sc), (C.c_int * MAX_LEVELS)(*ns),
                   level_gauge, level_w1, level_schur, pf_init, roll, metropolis, precision, tol,
                   max_iter, step_scheme, None, level_w2, level_schur2, rho, level_s2, level_s1, eo_solver,
-                  block_solver, use_graph)
+                  block_solver, use_graph, chrono)
     if step_scale is not None:
         import numpy as np
 
