@@ -316,13 +316,15 @@ typedef struct {
                            replay.  Same kernels in the same order: the
                            results equal the eager run's. */
     int chrono;         /* 1: each force solve of the molecular dynamics
-                           starts from the solution of the same solve at the
-                           previous force evaluation of its term (the first
-                           one of a trajectory from zero); the solves still
-                           run to tol, so the forces agree with chrono = 0 to
-                           the solver tolerance, and reversibility holds to
-                           it.  Needs 12 extra full double fields on the
-                           device (allocated on first use). */
+                           starts from a chronological guess: the linear
+                           extrapolation in MD time of its solutions at the
+                           two previous force evaluations of its term (one
+                           kept: that one; the first solve of a trajectory
+                           starts from zero).  The solves still run to tol,
+                           so the forces agree with chrono = 0 to the solver
+                           tolerance, and reversibility holds to it.  Needs
+                           24 extra even-site double fields on the device
+                           (allocated on first use). */
 } lqcd_hmc_params;
 
 /* Pseudo-fermion fields of lqcd_md (device pointers, NULL where the term

@@ -60,10 +60,47 @@ int hop_full(lqcd_ctx* h, int mode, int dag, int colour, double2* out, const dou
     return LQCD_OK;
 }
 
+// Chronological initial guess of slot k for a solve on the links at MD
+// time h->md_time (even half of x): nothing kept, zero (*guess = 0); one
+// solution, that solution; two, their linear extrapolation in MD time
+// (Brower, Ivanenko, Levi, Orginos, Nucl. Phys. B 484 (1997) 353: the
+// chronological inverter with two vectors).  dag: the unknown of the
+// adjoint system is gamma5 x.
+int chrono_guess(lqcd_ctx* h, int k, double2* x, int dag, int* guess)
+{
+    *guess = 0;
+    if (k < 0 || !h->chrono_buf[2 * k] || h->chrono_n[k] == 0) return LQCD_OK;
+    const double2* x1 = h->chrono_buf[2 * k + h->chrono_cur[k]];
+    const double2* x0 = h->chrono_buf[2 * k + 1 - h->chrono_cur[k]];
+    const double t0 = h->chrono_t[k][0], t1 = h->chrono_t[k][1];
+    double a = 1.0, b = 0.0;
+    if (h->chrono_n[k] == 2 && t1 != t0) {
+        const double s = (h->md_time - t1) / (t1 - t0);
+        a = 1.0 + s;
+        b = -s;
+    }
+    LQ_TRY(lincomb_even(h, x, a, x1, b, x0, dag));
+    *guess = 1;
+    return LQCD_OK;
+}
+
+// keep the even half of the solution x of slot k (the older one is dropped)
+int chrono_store(lqcd_ctx* h, int k, const double2* x)
+{
+    if (k < 0 || !h->chrono_buf[2 * k]) return LQCD_OK;
+    h->chrono_cur[k] ^= 1;
+    LQ_CUDA(h, cudaMemcpyAsync(h->chrono_buf[2 * k + h->chrono_cur[k]], x, sizeof(double2) * 12 * (size_t)h->g.Vh,
+                               cudaMemcpyDeviceToDevice, h->stream));
+    h->chrono_t[k][0] = h->chrono_t[k][1];
+    h->chrono_t[k][1] = h->md_time;
+    h->chrono_n[k] = h->chrono_n[k] < 2 ? h->chrono_n[k] + 1 : 2;
+    return LQCD_OK;
+}
+
 // x = W^-1 b (block: W1 on the slabs of `colour`; global: M).  x, b full
 // double fields, b is not modified, x must not alias b.  slot >= 0: the
-// previous solution kept in chronological slot `slot` (if valid) is the
-// initial guess, and the new solution replaces it.
+// solve starts from the chronological guess of that slot and keeps its
+// solution there.
 int solve_full(lqcd_ctx* h, int mode, int colour, int dagger, int prec, double kappa, double2* x,
                const double2* b, double tol, int max_iter, int* iters, double* resid,
                int method = SOLVER_BICGSTAB, int slot = -1)
@@ -75,30 +112,21 @@ int solve_full(lqcd_ctx* h, int mode, int colour, int dagger, int prec, double k
         bb = fld(h, F_T1);
     }
     const int col = mode == MODE_ALL ? -1 : colour;
-    double2* cb = slot >= 0 ? h->chrono_buf[slot] : nullptr;
     int guess = 0;
-    if (cb && h->chrono_valid[slot]) {
-        // the even part of the unknown: gamma5 x_prev for the adjoint system
-        if (dagger) LQ_TRY(gamma5_full(h, x, cb));
-        else LQ_CUDA(h, cudaMemcpyAsync(x, cb, sizeof(double2) * 12 * (size_t)Vh, cudaMemcpyDeviceToDevice,
-                                        h->stream));
-        guess = 1;
-    }
-    // b_e' = b_e + kappa H_eo b_o
-    LQ_TRY(hop_sweep(h, PREC64, mode, 0, 0, col, sp64(fld(h, F_T2), 0, Vh), sp64((double2*)bb, 1, Vh), 1.0,
+    LQ_TRY(chrono_guess(h, slot, x, dagger, &guess));
+    // b_e' = b_e + kappa H_eo b_o (double fields; double-float arithmetic
+    // around a mixed-precision solve)
+    const int hp = prec == PREC64 ? PREC64 : PRECDF;
+    LQ_TRY(hop_sweep(h, hp, mode, 0, 0, col, sp64(fld(h, F_T2), 0, Vh), sp64((double2*)bb, 1, Vh), 1.0,
                      sp64((double2*)bb, 0, Vh), kappa));
     LQ_TRY(eo_solve(h, mode, col, prec, kappa, x, fld(h, F_T2), tol, max_iter, iters, resid, 1.0, method,
                     guess));
     // x_o = b_o + kappa H_oe x_e
-    LQ_TRY(hop_sweep(h, PREC64, mode, 0, 1, col, sp64(x, 1, Vh), sp64(x, 0, Vh), 1.0, sp64((double2*)bb, 1, Vh),
+    LQ_TRY(hop_sweep(h, hp, mode, 0, 1, col, sp64(x, 1, Vh), sp64(x, 0, Vh), 1.0, sp64((double2*)bb, 1, Vh),
                      kappa));
     if (col >= 0) LQ_TRY(keep_colour(h, x, col));
     if (dagger) LQ_TRY(gamma5_full(h, x, x));
-    if (cb) {
-        LQ_CUDA(h, cudaMemcpyAsync(cb, x, sizeof(double2) * 24 * (size_t)Vh, cudaMemcpyDeviceToDevice, h->stream));
-        h->chrono_valid[slot] = true;
-    }
-    return LQCD_OK;
+    return chrono_store(h, slot, x);
 }
 
 struct SolveCfg {
@@ -298,27 +326,17 @@ int w3eo_solve(lqcd_ctx* h, double2* x, const double2* b, double kappa, double r
                int* iters = nullptr, double* resid = nullptr, int slot = -1)
 {
     GeoScope sc(h, sub_geo(h->g1));
-    const size_t half = sizeof(double2) * 12 * (size_t)h->g.Vh;
     const double2* bb = b;
     if (dag) {
         LQ_TRY(gamma5_full(h, fld(h, F_T2), b));
         bb = fld(h, F_T2);
     }
-    double2* cb = slot >= 0 ? h->chrono_buf[slot] : nullptr;
     int guess = 0;
-    if (cb && h->chrono_valid[slot]) {  // previous solution as the initial guess
-        if (dag) LQ_TRY(gamma5_full(h, x, cb));
-        else LQ_CUDA(h, cudaMemcpyAsync(x, cb, half, cudaMemcpyDeviceToDevice, h->stream));
-        guess = 1;
-    }
+    LQ_TRY(chrono_guess(h, slot, x, dag, &guess));
     LQ_TRY(eo_solve(h, MODE_INTRA, -1, c.prec, kappa, x, bb, c.tol, c.max_iter, iters, resid, 1.0 + rho, c.method,
                     guess));
     if (dag) LQ_TRY(gamma5_full(h, x, x));
-    if (cb) {
-        LQ_CUDA(h, cudaMemcpyAsync(cb, x, half, cudaMemcpyDeviceToDevice, h->stream));
-        h->chrono_valid[slot] = true;
-    }
-    return LQCD_OK;
+    return chrono_store(h, slot, x);
 }
 
 // F += coef * d/dw 2 Re <a, d(H_eo H_oe) b> for even-site a, b (parity-0
@@ -407,17 +425,16 @@ void build_step(const lqcd_hmc_params& p, int j, double dt, std::vector<Op>& v)
     }
 }
 
-// the chronological slots of the force solves (full double fields, zeroed
-// once: a slot's odd half is never read as a guess); before any capture
+// the chronological slots of the force solves (two even-half double fields
+// each), allocated before any capture
 int chrono_alloc(lqcd_ctx* h, const lqcd_hmc_params* p)
 {
     if (!p->chrono) return LQCD_OK;
-    const size_t bytes = sizeof(double2) * 24 * (size_t)h->g.Vh;
-    for (int k = 0; k < lqcd_ctx::NCHRONO; ++k) {
+    const size_t bytes = sizeof(double2) * 12 * (size_t)h->g.Vh;
+    for (int k = 0; k < 2 * lqcd_ctx::NCHRONO; ++k) {
         if (h->chrono_buf[k]) continue;
         LQ_CUDA(h, cudaMalloc(&h->chrono_buf[k], bytes));
         LQ_CUDA(h, cudaMemsetAsync(h->chrono_buf[k], 0, bytes, h->stream));
-        h->chrono_valid[k] = false;
     }
     return LQCD_OK;
 }
@@ -531,10 +548,12 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
     const SolveCfg csch2{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? 6 : -1};
     const SolveCfg cs2{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 8 : -1};
     const SolveCfg cs1{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 10 : -1};
-    for (bool& v : h->chrono_valid) v = false;
+    for (int k = 0; k < lqcd_ctx::NCHRONO; ++k) h->chrono_n[k] = h->chrono_cur[k] = 0;
+    h->md_time = 0.0;
     for (const Op& o : ops) {
         if (o.kind == 1) {
             LQ_TRY(update_links(h, P, o.dt, ss));
+            h->md_time += o.dt;
             continue;
         }
         if (p.level_gauge == o.level) LQ_TRY(gauge_force_kick(h, P, -o.dt * p.beta / 6.0, p.precision, ss));
@@ -753,7 +772,9 @@ GaugeF gauge_view(lqcd_ctx* h, int prec)
 {
     GaugeF g;
     g.Vh = h->g.Vh;
-    g.v = prec == PREC64 ? (const void*)h->U64 : prec == PREC32 ? (const void*)h->U32 : (const void*)h->U16;
+    g.v = (prec == PREC64 || prec == PRECDF) ? (const void*)h->U64
+          : prec == PREC32                     ? (const void*)h->U32
+                                               : (const void*)h->U16;
     return g;
 }
 

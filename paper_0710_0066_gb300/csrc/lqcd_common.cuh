@@ -23,6 +23,8 @@
 
 #define LQ_HD __host__ __device__ __forceinline__
 
+#include "lqcd_df.cuh"
+
 // ---------------------------------------------------------------------------
 // geometry
 // ---------------------------------------------------------------------------
@@ -197,7 +199,9 @@ LQ_HD void accum_recon(int mu, int sg, const HalfSp<T>& w, Spinor<T>& acc)
 // ---------------------------------------------------------------------------
 // field views
 // ---------------------------------------------------------------------------
-enum { PREC64 = 0, PREC32 = 1, PREC16 = 2 };
+// PRECDF: double storage (fields and links), double-float arithmetic; the
+// double sweeps of the mixed-precision path (internal, not an API precision)
+enum { PREC64 = 0, PREC32 = 1, PREC16 = 2, PRECDF = 3 };
 
 struct SpinorF {  // one parity block of a spinor field in some precision
     void* v;      // double2* / float4* / uint4*
@@ -223,6 +227,10 @@ struct Real<PREC32> {
 template <>
 struct Real<PREC16> {
     typedef float T;
+};
+template <>
+struct Real<PRECDF> {
+    typedef df T;
 };
 
 // RO = true: the field is not written during the kernel (read-only path);
@@ -322,6 +330,35 @@ struct SpIO<PREC16, RO> {
     }
 };
 
+template <bool RO>
+struct SpIO<PRECDF, RO> {
+    static __device__ __forceinline__ void load(const SpinorF& f, int i, Spinor<df>& s)
+    {
+        const double2* p = (const double2*)f.v;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 d = ldv<double2, RO>(p + (size_t)c * f.N + i);
+            s.c[c / 3][c % 3] = mk(df_split(d.x), df_split(d.y));
+        }
+    }
+    static __device__ __forceinline__ void store(const SpinorF& f, int i, const Spinor<df>& s)
+    {
+        double2* p = (double2*)f.v;
+#pragma unroll
+        for (int c = 0; c < 12; ++c)
+            p[(size_t)c * f.N + i] = make_double2(df_to_double(s.c[c / 3][c % 3].re), df_to_double(s.c[c / 3][c % 3].im));
+    }
+};
+
+// a spinor of any arithmetic type as doubles
+LQ_HD void to_double(const Spinor<double>& s, Spinor<double>& d) { d = s; }
+LQ_HD void to_double(const Spinor<df>& s, Spinor<double>& d)
+{
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+        d.c[k / 3][k % 3] = mk(df_to_double(s.c[k / 3][k % 3].re), df_to_double(s.c[k / 3][k % 3].im));
+}
+
 template <int P, bool RO = true>
 __device__ __forceinline__ void load_spinor(const SpinorF& f, int i, Spinor<typename Real<P>::T>& s)
 {
@@ -345,6 +382,16 @@ __device__ __forceinline__ void load_link<PREC64>(const GaugeF& g, int mu, int p
     for (int k = 0; k < 9; ++k) {
         double2 d = __ldg(p + (size_t)k * g.Vh + i);
         u.m[k / 3][k % 3] = mk(d.x, d.y);
+    }
+}
+template <>
+__device__ __forceinline__ void load_link<PRECDF>(const GaugeF& g, int mu, int par, int i, Su3<df>& u)
+{
+    const double2* p = (const double2*)g.v + (size_t)(mu * 2 + par) * 9 * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        double2 d = __ldg(p + (size_t)k * g.Vh + i);
+        u.m[k / 3][k % 3] = mk(df_split(d.x), df_split(d.y));
     }
 }
 template <>
@@ -548,11 +595,16 @@ struct lqcd_ctx {
     cudaGraphExec_t md_exec = nullptr;
     std::vector<unsigned char> md_key;  // parameters the graph was recorded for
     int64_t md_launches = 0;            // kernels per replay
-    // chronological initial guesses of the MD's solves (one full double
-    // field per solve site of the force terms)
+    // chronological initial guesses of the MD's solves: per solve site of
+    // the force terms the even halves of its last two solutions (buffers
+    // 2k, 2k + 1; chrono_cur[k] names the newer) and the MD times of the
+    // links they were solved on
     static constexpr int NCHRONO = 12;
-    double2* chrono_buf[NCHRONO] = {};
-    bool chrono_valid[NCHRONO] = {};
+    double2* chrono_buf[2 * NCHRONO] = {};
+    int chrono_n[NCHRONO] = {};    // solutions kept (0, 1, 2)
+    int chrono_cur[NCHRONO] = {};
+    double chrono_t[NCHRONO][2] = {};  // [older, newer]
+    double md_time = 0.0;              // MD time of the links in do_md
     int md_nforce = 0;                  // force evaluations per replay
     int md_solves = 0;                  // solves per replay
     int64_t iter_count = 0;  // inner iterations since reset (trajectory stats)
@@ -616,6 +668,8 @@ int embed_boundary(lqcd_ctx* h, double2* full, const double* coords, int nface =
 int project_boundary(lqcd_ctx* h, double* coords, const double2* full, int nface = 2);
 int axpby_full(lqcd_ctx* h, double2* y, double a, const double2* x, double b, int colour);
 int gamma5_full(lqcd_ctx* h, double2* y, const double2* x);
+// even half: y = gamma5^g5 (a x1 + b x0); x0 not read when b = 0
+int lincomb_even(lqcd_ctx* h, double2* y, double a, const double2* x1, double b, const double2* x0, int g5);
 int keep_colour(lqcd_ctx* h, double2* y, int colour);
 int norm2_dev(lqcd_ctx* h, const double* x, int64_t n, double* dev_out);
 int rng_normals(lqcd_ctx* h, double* out, int64_t n, uint64_t seed, uint32_t stream, uint32_t traj,

@@ -17,9 +17,8 @@ namespace {
 constexpr int HOP_BS_MAX = 256;
 
 template <int P>
-__global__ void __launch_bounds__(HOP_BS_MAX) k_hop(Geo g, int mode, int dag, int pout, int colour,
-                                               SpinorF out, SpinorF in, GaugeF U, double a, SpinorF x,
-                                               double c, int nsites)
+__device__ __forceinline__ void hop_body(Geo g, int mode, int dag, int pout, int colour, SpinorF out, SpinorF in,
+                                         GaugeF U, double a, SpinorF x, double c, int nsites)
 {
     typedef typename Real<P>::T T;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -49,14 +48,30 @@ __global__ void __launch_bounds__(HOP_BS_MAX) k_hop(Geo g, int mode, int dag, in
     store_spinor<P>(out, i, acc);
 }
 
+template <int P>
+__global__ void __launch_bounds__(HOP_BS_MAX) k_hop(Geo g, int mode, int dag, int pout, int colour, SpinorF out,
+                                               SpinorF in, GaugeF U, double a, SpinorF x, double c, int nsites)
+{
+    hop_body<P>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+}
+
+// the double-float sweep: its long dependent chains want more resident
+// warps than its natural register count allows
+__global__ void __launch_bounds__(HOP_BS_MAX, 2) k_hop_df(Geo g, int mode, int dag, int pout, int colour, SpinorF out,
+                                                     SpinorF in, GaugeF U, double a, SpinorF x, double c, int nsites)
+{
+    hop_body<PRECDF>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+}
+
 }  // namespace
 
 // algorithmic DRAM bytes of one output site: the output, the input site and
 // the eight links, each moved once (neighbour spinors reused from cache)
 double hop_site_bytes(int prec, bool with_x)
 {
-    const double sp = prec == PREC64 ? 192.0 : prec == PREC32 ? 96.0 : 52.0;
-    const double lk = prec == PREC64 ? 144.0 : prec == PREC32 ? 48.0 : 24.0;
+    const bool dbl = prec == PREC64 || prec == PRECDF;
+    const double sp = dbl ? 192.0 : prec == PREC32 ? 96.0 : 52.0;
+    const double lk = dbl ? 144.0 : prec == PREC32 ? 48.0 : 24.0;
     return 2.0 * sp + 8.0 * lk + (with_x ? sp : 0.0);
 }
 
@@ -65,13 +80,15 @@ int hop_sweep(lqcd_ctx* h, int prec, int mode, int dag, int pout, int colour, Sp
 {
     const Geo& g = h->g;
     const int nsites = colour < 0 ? g.Vh : (g.nb / 2) * g.Sh;
-    const int bs = std::min(std::max(h->tune.hop_bs[prec], 32), HOP_BS_MAX);
+    const int bs = std::min(std::max(h->tune.hop_bs[prec == PRECDF ? PREC64 : prec], 32), HOP_BS_MAX);
     const int nb = (nsites + bs - 1) / bs;
     GaugeF U = gauge_view(h, prec);
     cudaEvent_t ev;
     prof_begin(h, 0, &ev);
     if (prec == PREC64)
         k_hop<PREC64><<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+    else if (prec == PRECDF)
+        k_hop_df<<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
     else if (prec == PREC32)
         k_hop<PREC32><<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
     else

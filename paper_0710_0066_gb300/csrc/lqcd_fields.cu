@@ -247,6 +247,16 @@ __global__ void k_gamma5(double2* y, const double2* x, int Vh)
     y[t] = make_double2(s * v.x, s * v.y);
 }
 
+__global__ void k_lincomb_even(double2* y, double a, const double2* x1, double b, const double2* x0, int Vh, int g5)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)12 * Vh) return;
+    const double s = (g5 && (int)(t / Vh) >= 6) ? -1.0 : 1.0;  // spins 2, 3
+    const double2 u = x1[t];
+    const double2 v = (b != 0.0) ? x0[t] : make_double2(0.0, 0.0);
+    y[t] = make_double2(s * (a * u.x + b * v.x), s * (a * u.y + b * v.y));
+}
+
 // ---------------------------------------------------------------------------
 // deterministic two-stage sums of squares
 // ---------------------------------------------------------------------------
@@ -462,6 +472,13 @@ int keep_colour(lqcd_ctx* h, double2* y, int colour)
 int gamma5_full(lqcd_ctx* h, double2* y, const double2* x)
 {
     k_gamma5<<<nblk((int64_t)24 * h->g.Vh), BS, 0, h->stream>>>(y, x, h->g.Vh);
+    LAUNCH_CHECK(h);
+    return LQCD_OK;
+}
+
+int lincomb_even(lqcd_ctx* h, double2* y, double a, const double2* x1, double b, const double2* x0, int g5)
+{
+    k_lincomb_even<<<nblk((int64_t)12 * h->g.Vh), BS, 0, h->stream>>>(y, a, x1, b, x0, h->g.Vh, g5);
     LAUNCH_CHECK(h);
     return LQCD_OK;
 }

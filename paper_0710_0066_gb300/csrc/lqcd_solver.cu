@@ -220,6 +220,10 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
     typedef typename Real<P>::T T;
     constexpr int PE = (P == PREC64) ? PREC64 : PREC32;
     typedef typename Real<PE>::T TE;
+    // the double residual sweeps: FP64 for a double solve, double-float
+    // arithmetic on the double fields and links for a mixed one
+    constexpr int PR = (P == PREC64) ? PREC64 : PRECDF;
+    typedef typename Real<PR>::T TR;
     constexpr bool WORDS = (P == PREC32);
     const int cta = blockIdx.x, tid = threadIdx.x;
     const int sys = cta / A.cps, cin = cta - sys * A.cps;
@@ -240,8 +244,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             Spinor<double> bb, z;
             load_spinor<PREC64, true>(A.b, i, bb);
             if (A.guess) {
-                hop_site<PREC64, false>(A.g, A.mode, 0, 1, i, A.x, A.U64, z);
-                store_spinor<PREC64>(A.t64, i, z);
+                Spinor<TR> hz;
+                hop_site<PR, false>(A.g, A.mode, 0, 1, i, A.x, A.U64, hz);
+                store_spinor<PR>(A.t64, i, hz);
             } else {
                 store_spinor<PREC64>(A.r64, i, bb);
 #pragma unroll
@@ -268,7 +273,11 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
         {
             const int i = base + j_;
             Spinor<double> a, xx, bb;
-            hop_site<PREC64, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, a);
+            {
+                Spinor<TR> ha;
+                hop_site<PR, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, ha);
+                to_double(ha, a);
+            }
             load_spinor<PREC64, false>(A.x, i, xx);
             load_spinor<PREC64, true>(A.b, i, bb);
 #pragma unroll
@@ -687,9 +696,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
         if (S.active) FOR_SITES
             {
                 const int i = base + j_;
-                Spinor<double> a;
-                hop_site<PREC64, false>(A.g, A.mode, 0, 1, i, A.x, A.U64, a);
-                store_spinor<PREC64>(A.t64, i, a);
+                Spinor<TR> a;
+                hop_site<PR, false>(A.g, A.mode, 0, 1, i, A.x, A.U64, a);
+                store_spinor<PR>(A.t64, i, a);
             }
         SYNC_OR_RETURN;
         // ---- r64 = b - x + k2 H_eo t64 ; |r64|^2
@@ -700,7 +709,11 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                 {
                     const int i = base + j_;
                     Spinor<double> a, xx, bb;
-                    hop_site<PREC64, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, a);
+                    {
+                        Spinor<TR> ha;
+                        hop_site<PR, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, ha);
+                        to_double(ha, a);
+                    }
                     load_spinor<PREC64, false>(A.x, i, xx);
                     load_spinor<PREC64, true>(A.b, i, bb);
 #pragma unroll

@@ -1,6 +1,7 @@
 """Chronological initial guesses of the molecular-dynamics force solves
-(lqcd_hmc_params.chrono): each solve starts from the solution of the same
-solve at the previous force evaluation of its term.  The solves still run
+(lqcd_hmc_params.chrono): each solve starts from the linear extrapolation
+in MD time of its solutions at the two previous force evaluations of its
+term (Brower et al.'s chronological inverter).  The solves still run
 to the requested residual, so trajectories agree with the FP64 oracle (which
 always starts from zero) to the tolerances of the other trajectory tests;
 a solve whose guess already meets the residual takes no iteration; the
