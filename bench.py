@@ -59,9 +59,9 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes per k_solve launch from the ncu capture summarised in
 # profiles/k_solve_16x16x16x32_f32.md, valid only for the solver source
 # that was captured (bench.py reports null once the source differs)
-SOLVER_TRAFFIC = dict(src_sha256="22301b6a483032528f6e8cef2339ea9e8b7e2f053e9e22b94dda621a929c7bda",
-                      block_series=(290.925568e6 + 142.578944e6), block=(329.253632e6 + 340.842240e6),
-                      glob=(434.955264e6 + 561.454592e6))
+SOLVER_TRAFFIC = dict(src_sha256="4c942884cf825d7cf72254a66847dc6ed9818dba5294c0e85a13750f7cdd4433",
+                      block_series=(321.114112e6 + 164.535040e6), block=(352.731904e6 + 328.770560e6),
+                      glob=(435.131136e6 + 513.426688e6))
 
 
 def solver_traffic():
