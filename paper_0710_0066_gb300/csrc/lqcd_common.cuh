@@ -144,6 +144,41 @@ LQ_HD void su3_dagmul_half(const Su3<T>& u, const HalfSp<T>& h, HalfSp<T>& w)
 //   upper half h = u + sg*Q_mu d, lower half = K_mu h,
 // u = (psi0, psi1), d = (psi2, psi3).  sg = -1 gives (1 - gamma_mu).
 // ---------------------------------------------------------------------------
+// the same projection for one colour: (h0, h1) from the spin components
+// (p0, p1, p2, p3) (the double-float sweep projects as its loads arrive)
+template <class T>
+LQ_HD void project1(int mu, int sg, const cx<T>& p0, const cx<T>& p1, const cx<T>& p2, const cx<T>& p3, cx<T>& h0,
+                    cx<T>& h1)
+{
+    cx<T> a, b;
+    switch (mu) {
+        case 0: a = p2; b = p3; break;                  // gamma_0 psi = (-d, -u): h = u - sg d
+        case 1: a = mul_i(p3); b = mul_i(p2); break;    // -i s1 d = (-i d1, -i d0): h = u - sg i s1 d
+        case 2: a = p3; b = -p2; break;                 // i s2 d = (d1, -d0)
+        default: a = mul_i(p2); b = mul_mi(p3); break;  // i s3 d = (i d0, -i d1)
+    }
+    if (sg < 0) { h0 = p0 + a; h1 = p1 + b; }
+    else        { h0 = p0 - a; h1 = p1 - b; }
+}
+
+// colour i of acc += (1 + sg*gamma_mu) psi rebuilt from its upper half
+// (w0, w1): lower half = sg * l with l = -w (mu = 0) or l = (i s_k) w (mu = k)
+template <class T>
+LQ_HD void accum_recon1(int mu, int sg, const cx<T>& w0, const cx<T>& w1, Spinor<T>& acc, int i)
+{
+    acc.c[0][i] = acc.c[0][i] + w0;
+    acc.c[1][i] = acc.c[1][i] + w1;
+    cx<T> l0, l1;
+    switch (mu) {
+        case 0: l0 = -w0; l1 = -w1; break;
+        case 1: l0 = mul_i(w1); l1 = mul_i(w0); break;
+        case 2: l0 = w1; l1 = -w0; break;
+        default: l0 = mul_i(w0); l1 = mul_mi(w1); break;
+    }
+    if (sg < 0) { acc.c[2][i] = acc.c[2][i] - l0; acc.c[3][i] = acc.c[3][i] - l1; }
+    else        { acc.c[2][i] = acc.c[2][i] + l0; acc.c[3][i] = acc.c[3][i] + l1; }
+}
+
 template <class T>
 LQ_HD void project(int mu, int sg, const Spinor<T>& p, HalfSp<T>& h)
 {
@@ -200,8 +235,11 @@ LQ_HD void accum_recon(int mu, int sg, const HalfSp<T>& w, Spinor<T>& acc)
 // field views
 // ---------------------------------------------------------------------------
 // PRECDF: double storage (fields and links), double-float arithmetic; the
-// double sweeps of the mixed-precision path (internal, not an API precision)
-enum { PREC64 = 0, PREC32 = 1, PREC16 = 2, PRECDF = 3 };
+// double sweeps of the mixed-precision path.  PRECDS: the same arithmetic
+// on a spinor stored as df pairs (float4 = re.hi, im.hi, re.lo, im.lo per
+// complex, 16 bytes like a double2), for intermediates that never leave
+// the solver.  Internal, not API precisions.
+enum { PREC64 = 0, PREC32 = 1, PREC16 = 2, PRECDF = 3, PRECDS = 4 };
 
 struct SpinorF {  // one parity block of a spinor field in some precision
     void* v;      // double2* / float4* / uint4*
@@ -230,6 +268,10 @@ struct Real<PREC16> {
 };
 template <>
 struct Real<PRECDF> {
+    typedef df T;
+};
+template <>
+struct Real<PRECDS> {
     typedef df T;
 };
 
@@ -350,6 +392,28 @@ struct SpIO<PRECDF, RO> {
     }
 };
 
+template <bool RO>
+struct SpIO<PRECDS, RO> {
+    static __device__ __forceinline__ void load(const SpinorF& f, int i, Spinor<df>& s)
+    {
+        const float4* p = (const float4*)f.v;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            float4 d = ldv<float4, RO>(p + (size_t)c * f.N + i);
+            s.c[c / 3][c % 3] = mk(df(d.x, d.z), df(d.y, d.w));
+        }
+    }
+    static __device__ __forceinline__ void store(const SpinorF& f, int i, const Spinor<df>& s)
+    {
+        float4* p = (float4*)f.v;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const cx<df> v = s.c[c / 3][c % 3];
+            p[(size_t)c * f.N + i] = make_float4(v.re.hi, v.im.hi, v.re.lo, v.im.lo);
+        }
+    }
+};
+
 // a spinor of any arithmetic type as doubles
 LQ_HD void to_double(const Spinor<double>& s, Spinor<double>& d) { d = s; }
 LQ_HD void to_double(const Spinor<df>& s, Spinor<double>& d)
@@ -393,6 +457,11 @@ __device__ __forceinline__ void load_link<PRECDF>(const GaugeF& g, int mu, int p
         double2 d = __ldg(p + (size_t)k * g.Vh + i);
         u.m[k / 3][k % 3] = mk(df_split(d.x), df_split(d.y));
     }
+}
+template <>
+__device__ __forceinline__ void load_link<PRECDS>(const GaugeF& g, int mu, int par, int i, Su3<df>& u)
+{
+    load_link<PRECDF>(g, mu, par, i, u);
 }
 template <>
 __device__ __forceinline__ void load_link<PREC32>(const GaugeF& g, int mu, int par, int i, Su3<float>& u)
@@ -450,13 +519,20 @@ template <int P, class Loader>
 __device__ __forceinline__ void hop_site_ld(const Geo& g, int mode, int dag, int pout, int i, Loader ld,
                                             const GaugeF& U, Spinor<typename Real<P>::T>& acc);
 
+template <int P, bool RO>
+__device__ __forceinline__ void hop_site_df(const Geo& g, int mode, int dag, int pout, int i, const SpinorF& in,
+                                            const GaugeF& U, Spinor<df>& acc);
+
 template <int P, bool RO = true>
 __device__ __forceinline__ void hop_site(const Geo& g, int mode, int dag, int pout, int i,
                                          const SpinorF& in, const GaugeF& U,
                                          Spinor<typename Real<P>::T>& acc)
 {
-    hop_site_ld<P>(g, mode, dag, pout, i,
-                   [&](int j, Spinor<typename Real<P>::T>& s) { load_spinor<P, RO>(in, j, s); }, U, acc);
+    if constexpr (P == PRECDF || P == PRECDS)
+        hop_site_df<P, RO>(g, mode, dag, pout, i, in, U, acc);
+    else
+        hop_site_ld<P>(g, mode, dag, pout, i,
+                       [&](int j, Spinor<typename Real<P>::T>& s) { load_spinor<P, RO>(in, j, s); }, U, acc);
 }
 
 template <int P, class Loader>
@@ -525,6 +601,89 @@ __device__ __forceinline__ void hop_site_ld(const Geo& g, int mode, int dag, int
                         for (int c = 0; c < 3; ++c) w.c[s][c] = -w.c[s][c];
                 }
                 accum_recon(mu, sg, w, acc);
+            }
+        }
+        stride *= g.L[mu];
+    }
+}
+
+// The hopping term in double-float arithmetic, arranged for registers: a
+// neighbour is projected colour by colour as its components arrive (the
+// full spinor is never held), and the link is applied row by row (column
+// by column for U^dag), each row's result accumulated at once.  Same
+// operations as hop_site_ld, about 90 instead of 130 live registers.
+template <int P, bool RO>
+__device__ __forceinline__ cx<df> df_in(const SpinorF& f, int c, int j)
+{
+    if constexpr (P == PRECDS) {
+        const float4 d = ldv<float4, RO>((const float4*)f.v + (size_t)c * f.N + j);
+        return mk(df(d.x, d.z), df(d.y, d.w));
+    } else {
+        const double2 d = ldv<double2, RO>((const double2*)f.v + (size_t)c * f.N + j);
+        return mk(df_split(d.x), df_split(d.y));
+    }
+}
+
+__device__ __forceinline__ cx<df> df_link(const double2* p, int k, int Vh, int i)
+{
+    const double2 d = __ldg(p + (size_t)k * Vh + i);
+    return mk(df_split(d.x), df_split(d.y));
+}
+
+template <int P, bool RO>
+__device__ __forceinline__ void hop_site_df(const Geo& g, int mode, int dag, int pout, int i, const SpinorF& in,
+                                            const GaugeF& U, Spinor<df>& acc)
+{
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc.c[s][c] = mk(df(0), df(0));
+    int x[4];
+    eo_coords(g, pout, i, x);
+    const int lex = lex_of(g, x);
+    int stride = 1;
+    const int pin = 1 - pout;
+#pragma unroll
+    for (int mu = 3; mu >= 0; --mu) {
+#pragma unroll
+        for (int fw = 1; fw >= 0; --fw) {
+            int nl = fw ? lex + stride : lex - stride;
+            const bool wrap = fw ? (x[mu] == g.L[mu] - 1) : (x[mu] == 0);
+            if (wrap) nl += fw ? -g.L[mu] * stride : g.L[mu] * stride;
+            bool use = true;
+            if (mu == 0) use = t_hop_kept(g, mode, fw ? x[0] + 1 : x[0]);
+            else if (mode == MODE_CROSS || mode == MODE_CROSS2) use = false;
+            if (!use) continue;
+            const int j = nl >> 1;
+            const int sg = fw ? (dag ? +1 : -1) : (dag ? -1 : +1);
+            HalfSp<df> h;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                project1(mu, sg, df_in<P, RO>(in, c, j), df_in<P, RO>(in, 3 + c, j), df_in<P, RO>(in, 6 + c, j),
+                         df_in<P, RO>(in, 9 + c, j), h.c[0][c], h.c[1][c]);
+            // forward: U_mu(x) at this site; backward: U_mu(x - mu)^dag
+            const double2* up = (const double2*)U.v + (size_t)(mu * 2 + (fw ? pout : pin)) * 9 * U.Vh;
+            const int li = fw ? i : j;
+            const bool neg = mu == 0 && wrap && g.bc_t < 0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cx<df> w0, w1;
+                if (fw) {
+                    const cx<df> u0 = df_link(up, 3 * r, U.Vh, li), u1 = df_link(up, 3 * r + 1, U.Vh, li),
+                                 u2 = df_link(up, 3 * r + 2, U.Vh, li);
+                    w0 = u0 * h.c[0][0] + u1 * h.c[0][1] + u2 * h.c[0][2];
+                    w1 = u0 * h.c[1][0] + u1 * h.c[1][1] + u2 * h.c[1][2];
+                } else {
+                    const cx<df> u0 = df_link(up, r, U.Vh, li), u1 = df_link(up, 3 + r, U.Vh, li),
+                                 u2 = df_link(up, 6 + r, U.Vh, li);
+                    w0 = cjmul(u0, h.c[0][0]) + cjmul(u1, h.c[0][1]) + cjmul(u2, h.c[0][2]);
+                    w1 = cjmul(u0, h.c[1][0]) + cjmul(u1, h.c[1][1]) + cjmul(u2, h.c[1][2]);
+                }
+                if (neg) {
+                    w0 = -w0;
+                    w1 = -w1;
+                }
+                accum_recon1(mu, sg, w0, w1, acc, r);
             }
         }
         stride *= g.L[mu];

@@ -45,7 +45,7 @@ struct SolveArgs {
     int nsite;
     GaugeF U64, UP;
     SpinorF b, x, r64;  // double, parity 0
-    SpinorF t64;        // double, parity 1
+    SpinorF t64;        // parity 1: double (double solve) or df pairs (mixed)
     SpinorF r, rh, p, v, s, t;  // inner precision, parity 0
     SpinorF tmp;        // inner precision, parity 1
     SpinorF e;          // inner solution (single; double for the double solver)
@@ -224,6 +224,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
     // arithmetic on the double fields and links for a mixed one
     constexpr int PR = (P == PREC64) ? PREC64 : PRECDF;
     typedef typename Real<PR>::T TR;
+    // t64 = H_oe x between the two residual sweeps: kept as df pairs in the
+    // mixed case (no conversion to double and back)
+    constexpr int PT = (P == PREC64) ? PREC64 : PRECDS;
     constexpr bool WORDS = (P == PREC32);
     const int cta = blockIdx.x, tid = threadIdx.x;
     const int sys = cta / A.cps, cin = cta - sys * A.cps;
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             if (A.guess) {
                 Spinor<TR> hz;
                 hop_site<PR, false>(A.g, A.mode, 0, 1, i, A.x, A.U64, hz);
-                store_spinor<PR>(A.t64, i, hz);
+                store_spinor<PT>(A.t64, i, hz);
             } else {
                 store_spinor<PREC64>(A.r64, i, bb);
 #pragma unroll
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             Spinor<double> a, xx, bb;
             {
                 Spinor<TR> ha;
-                hop_site<PR, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, ha);
+                hop_site<PT, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, ha);
                 to_double(ha, a);
             }
             load_spinor<PREC64, false>(A.x, i, xx);
@@ -698,7 +701,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                 const int i = base + j_;
                 Spinor<TR> a;
                 hop_site<PR, false>(A.g, A.mode, 0, 1, i, A.x, A.U64, a);
-                store_spinor<PR>(A.t64, i, a);
+                store_spinor<PT>(A.t64, i, a);
             }
         SYNC_OR_RETURN;
         // ---- r64 = b - x + k2 H_eo t64 ; |r64|^2
@@ -711,7 +714,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                     Spinor<double> a, xx, bb;
                     {
                         Spinor<TR> ha;
-                        hop_site<PR, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, ha);
+                        hop_site<PT, false>(A.g, A.mode, 0, 0, i, A.t64, A.U64, ha);
                         to_double(ha, a);
                     }
                     load_spinor<PREC64, false>(A.x, i, xx);

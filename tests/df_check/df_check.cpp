@@ -27,7 +27,7 @@ static long double val(df a) { return (long double)a.hi + (long double)a.lo; }
 
 int main()
 {
-    long double e_split = 0, e_add = 0, e_mul = 0, e_dot = 0, e_back = 0, lo_ulp = 0;
+    long double e_split = 0, e_add = 0, e_mul = 0, e_dot = 0, e_chain = 0, e_back = 0, lo_ulp = 0;
     int bad_special = 0;
     for (int n = 0; n < 200000; ++n) {
         const double x = rnd(-70, 70), y = rnd(-70, 70);
@@ -63,6 +63,18 @@ int main()
                    fabsl(val(ui) * val(vr));
         }
         e_dot = fmaxl(e_dot, fmaxl(fabsl(val(re) - rr), fabsl(val(im) - ri)) / mag);
+        // a long unnormalised chain: 48 products summed (one output
+        // component of a hopping sweep), relative to the sum of |terms|
+        df acc(0);
+        long double ex = 0, mg = 0;
+        for (int k = 0; k < 48; ++k) {
+            const df p = df_split(rnd(-3, 1)), q = df_split(rnd(-6, 4));
+            acc = ((k & 3) == 1) ? acc - p * q : acc + p * q;
+            ex += ((k & 3) == 1 ? -1 : 1) * val(p) * val(q);
+            mg += fabsl(val(p) * val(q));
+        }
+        e_chain = fmaxl(e_chain, fabsl(val(acc) - ex) / mg);
+        e_chain = fmaxl(e_chain, fabsl(val(df_norm(acc)) - val(acc)) / mg);
     }
     // zeros, a power of two, huge and tiny values
     if (val(df_split(0.0)) != 0 || val(df_split(-0.0)) != 0) ++bad_special;
@@ -72,7 +84,7 @@ int main()
     if (fabsl(val(df_split(1e-20)) - 1e-20L) > 1e-20L * 0x1.0p-46L) ++bad_special;
     if (fabsl(val(df_split(3e-30)) - 3e-30L) > 3e-30L * 0x1.0p-23L) ++bad_special;  // below 2^-80: hi only
     if (val(df_split(1e-300)) != 0 && fabsl(val(df_split(1e-300))) > 1e-299L) ++bad_special;
-    printf("split %.3Le\nadd %.3Le\nmul %.3Le\ndot %.3Le\nback %.3Le\nlo_ulp %.3Lf\nspecial %d\n", e_split,
-           e_add, e_mul, e_dot, e_back, lo_ulp, bad_special);
+    printf("split %.3Le\nadd %.3Le\nmul %.3Le\ndot %.3Le\nchain %.3Le\nback %.3Le\nlo_ulp %.3Lf\nspecial %d\n",
+           e_split, e_add, e_mul, e_dot, e_chain, e_back, lo_ulp, bad_special);
     return 0;
 }

@@ -1,8 +1,9 @@
 """The double-float arithmetic of the mixed-precision path's double sweeps
 (csrc/lqcd_df.cuh), compiled for the host and checked against long-double
 arithmetic: the integer split of a double is exact to 2^-46, sums and
-products of two df numbers and a complex three-term row product (the link
-multiplication) keep about 46 bits, the way back to double is exact, and
+products of two df numbers, a complex three-term row product (the link
+multiplication) and a 48-term unnormalised chain (one output component
+of a hopping sweep) keep about 44-46 bits, the way back to double is exact, and
 zeros, infinities, NaN and tiny values split as documented.  These bounds
 make the double sweeps' results agree with FP64 to ~1e-14 relative, far
 below the 1e-10 residual the solves are run to."""
@@ -30,6 +31,7 @@ def test_df_arithmetic(tmp_path):
     assert r["add"] <= 2.0 ** -45
     assert r["mul"] <= 2.0 ** -44
     assert r["dot"] <= 2.0 ** -44
+    assert r["chain"] <= 2.0 ** -43
     assert r["back"] == 0.0
     assert r["lo_ulp"] <= 1.0
     assert r["special"] == 0
