@@ -59,6 +59,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes per k_solve launch from the ncu capture summarised in
 # profiles/k_solve_16x16x16x32_f32.md, valid only for the solver source
 # that was captured (bench.py reports null once the source differs)
+SOLVER_SOURCES = ("lqcd_solver.cu", "lqcd_common.cuh", "lqcd_df.cuh")  # the sources k_solve is built from
 SOLVER_TRAFFIC = dict(src_sha256="4c942884cf825d7cf72254a66847dc6ed9818dba5294c0e85a13750f7cdd4433",
                       block_series=(321.114112e6 + 164.535040e6), block=(352.731904e6 + 328.770560e6),
                       glob=(435.131136e6 + 513.426688e6))
@@ -67,12 +68,14 @@ SOLVER_TRAFFIC = dict(src_sha256="4c942884cf825d7cf72254a66847dc6ed9818dba5294c0
 def solver_traffic():
     import hashlib
 
-    path = os.path.join(ROOT, "paper_0710_0066_gb300", "csrc", "lqcd_solver.cu")
+    h = hashlib.sha256()
     try:
-        with open(path, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        for name in SOLVER_SOURCES:
+            with open(os.path.join(ROOT, "paper_0710_0066_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
     except OSError:
         return None, None
+    sha = h.hexdigest()
     if sha != SOLVER_TRAFFIC["src_sha256"]:
         return None, None
     return SOLVER_TRAFFIC["block_series"], {"batched_slab_solve_series": SOLVER_TRAFFIC["block_series"],

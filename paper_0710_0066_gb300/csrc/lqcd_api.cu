@@ -713,20 +713,28 @@ void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1)
 // -> red_out[base..base+7]
 constexpr int NTERM = 8;
 
+// the energies at the end of the molecular dynamics.  With chronological
+// guesses every term's solve starts from the solution of its last force
+// evaluation, which was on these same final links (every integrator level
+// ends with a kick), so it needs no iteration.
 int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, int base)
 {
-    SolveCfg c{p.precision, p.tol, p.max_iter};
+    const bool ch = p.chrono != 0;
     double* e = h->red_out + base;
     LQ_TRY(kinetic_sum(h, h->P, e));
     if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, e + 1));
-    const SolveCfg cblk{p.precision, p.tol, p.max_iter, p.block_solver};
-    if (p.level_w1 >= 0) LQ_TRY(pf_w1(h, nullptr, pf.phi1, p.kappa, 0.0, cblk, e + 2));
-    if (p.level_schur >= 0) LQ_TRY(pf_schur(h, nullptr, pf.phi2, p.kappa, 0.0, c, e + 3));
-    if (p.level_w2 >= 0) LQ_TRY(pf_w2(h, nullptr, pf.phi3, p.kappa, 0.0, cblk, e + 4));
-    if (p.level_schur2 >= 0) LQ_TRY(pf_schur2(h, nullptr, pf.phi4, p.kappa, 0.0, c, e + 5));
-    const SolveCfg ceo{p.precision, p.tol, p.max_iter, p.eo_solver};
-    if (p.level_s2 >= 0) LQ_TRY(pf_s2(h, nullptr, pf.phi5, p.kappa, p.rho, 0.0, ceo, e + 6));
-    if (p.level_s1 >= 0) LQ_TRY(pf_s1(h, nullptr, pf.phi6, p.kappa, p.rho, 0.0, ceo, e + 7));
+    const SolveCfg cw1{p.precision, p.tol, p.max_iter, p.block_solver, ch ? 0 : -1};
+    const SolveCfg csch{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? 2 : -1};
+    const SolveCfg cw2{p.precision, p.tol, p.max_iter, p.block_solver, ch ? 4 : -1};
+    const SolveCfg csch2{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? 6 : -1};
+    const SolveCfg cs2{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 8 : -1};
+    const SolveCfg cs1{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 10 : -1};
+    if (p.level_w1 >= 0) LQ_TRY(pf_w1(h, nullptr, pf.phi1, p.kappa, 0.0, cw1, e + 2));
+    if (p.level_schur >= 0) LQ_TRY(pf_schur(h, nullptr, pf.phi2, p.kappa, 0.0, csch, e + 3));
+    if (p.level_w2 >= 0) LQ_TRY(pf_w2(h, nullptr, pf.phi3, p.kappa, 0.0, cw2, e + 4));
+    if (p.level_schur2 >= 0) LQ_TRY(pf_schur2(h, nullptr, pf.phi4, p.kappa, 0.0, csch2, e + 5));
+    if (p.level_s2 >= 0) LQ_TRY(pf_s2(h, nullptr, pf.phi5, p.kappa, p.rho, 0.0, cs2, e + 6));
+    if (p.level_s1 >= 0) LQ_TRY(pf_s1(h, nullptr, pf.phi6, p.kappa, p.rho, 0.0, cs1, e + 7));
     return LQCD_OK;
 }
 
