@@ -60,9 +60,9 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # profiles/k_solve_16x16x16x32_f32.md, valid only for the solver source
 # that was captured (bench.py reports null once the source differs)
 SOLVER_SOURCES = ("lqcd_solver.cu", "lqcd_common.cuh", "lqcd_df.cuh")  # the sources k_solve is built from
-SOLVER_TRAFFIC = dict(src_sha256="4c942884cf825d7cf72254a66847dc6ed9818dba5294c0e85a13750f7cdd4433",
-                      block_series=(321.114112e6 + 164.535040e6), block=(352.731904e6 + 328.770560e6),
-                      glob=(435.131136e6 + 513.426688e6))
+SOLVER_TRAFFIC = dict(src_sha256="7fa603f6d2a7ac59799771f4f2296474a27bfa8db912a152917335271615022c",
+                      block_series=(301.616128e6 + 145.132800e6), block=(326.892544e6 + 324.286976e6),
+                      glob=(418.285056e6 + 516.481024e6))
 
 
 def solver_traffic():

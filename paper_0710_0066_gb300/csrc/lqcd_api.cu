@@ -87,7 +87,7 @@ int chrono_guess(lqcd_ctx* h, int k, double2* x, int dag, int* guess)
 // keep the even half of the solution x of slot k (the older one is dropped)
 int chrono_store(lqcd_ctx* h, int k, const double2* x)
 {
-    if (k < 0 || !h->chrono_buf[2 * k]) return LQCD_OK;
+    if (k < 0 || !h->chrono_buf[2 * k] || h->chrono_frozen) return LQCD_OK;
     h->chrono_cur[k] ^= 1;
     LQ_CUDA(h, cudaMemcpyAsync(h->chrono_buf[2 * k + h->chrono_cur[k]], x, sizeof(double2) * 12 * (size_t)h->g.Vh,
                                cudaMemcpyDeviceToDevice, h->stream));
@@ -716,10 +716,19 @@ constexpr int NTERM = 8;
 // the energies at the end of the molecular dynamics.  With chronological
 // guesses every term's solve starts from the solution of its last force
 // evaluation, which was on these same final links (every integrator level
-// ends with a kick), so it needs no iteration.
+// ends with a kick), so it needs no iteration.  The slots are only read:
+// a replayed MD graph relies on the host-side slot state it was recorded
+// with.
+struct ChronoFreeze {
+    lqcd_ctx* h;
+    explicit ChronoFreeze(lqcd_ctx* c) : h(c) { h->chrono_frozen = true; }
+    ~ChronoFreeze() { h->chrono_frozen = false; }
+};
+
 int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, int base)
 {
     const bool ch = p.chrono != 0;
+    ChronoFreeze freeze(h);
     double* e = h->red_out + base;
     LQ_TRY(kinetic_sum(h, h->P, e));
     if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, e + 1));

@@ -764,6 +764,7 @@ struct lqcd_ctx {
     int chrono_cur[NCHRONO] = {};
     double chrono_t[NCHRONO][2] = {};  // [older, newer]
     double md_time = 0.0;              // MD time of the links in do_md
+    bool chrono_frozen = false;        // guesses are read but not replaced
     int md_nforce = 0;                  // force evaluations per replay
     int md_solves = 0;                  // solves per replay
     int64_t iter_count = 0;  // inner iterations since reset (trajectory stats)
