@@ -36,3 +36,25 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[cname]) == C.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
+
+
+def test_solver_traffic_is_keyed_to_the_captured_sources(monkeypatch):
+    """bench.py reports the ncu DRAM traffic of k_solve only while the
+    sources the kernel is built from are the ones that were captured"""
+    import hashlib
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    h = hashlib.sha256()
+    for name in bench.SOLVER_SOURCES:
+        with open(os.path.join(ROOT, "paper_0710_0066_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    t, d = bench.solver_traffic()
+    if h.hexdigest() == bench.SOLVER_TRAFFIC["src_sha256"]:
+        assert t == bench.SOLVER_TRAFFIC["block_series"] and d["global_solve_bicgstab"] == bench.SOLVER_TRAFFIC["glob"]
+    else:
+        assert t is None and d is None
+    monkeypatch.setitem(bench.SOLVER_TRAFFIC, "src_sha256", "0" * 64)
+    assert bench.solver_traffic() == (None, None)
