@@ -48,7 +48,11 @@
  * Precision argument: LQCD_PREC_F64 runs everything in double precision;
  *   LQCD_PREC_F32 / LQCD_PREC_F16 run stencils and inner Krylov iterations
  *   with single- / half-precision storage (FP32 arithmetic) and keep
- *   double-precision residuals, dot products and outer defect correction.
+ *   double-precision residuals, dot products and outer defect correction;
+ *   there the double hopping sweeps of the outer residual and of the
+ *   even-odd source / reconstruction read the double fields and links and
+ *   compute in double-float arithmetic (pairs of floats, ~2^-46 relative),
+ *   because GB300's FP64 rate would bound them.
  */
 #ifndef LQCD_H
 #define LQCD_H
