@@ -121,6 +121,18 @@ def test_solve_wilson(setup, prec):
             assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(b), (it, rs)
 
 
+@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16])
+def test_zero_source_solves(setup, prec):
+    """the degenerate system b = 0: every slab system and the global solve
+    return x = 0 exactly, without an inner iteration"""
+    lat, olat, U, kappa, seed = setup
+    z = torch.zeros((olat.V, 4, 3), dtype=torch.complex128, device="cuda")
+    x, it, rs = lat.block_solve(z, kappa, -1, 0, prec, tol=1e-10)
+    assert x.abs().max().item() == 0.0 and max(it[:olat.nb]) == 0
+    x, it, rs = lat.solve(z, kappa, 1, prec, tol=1e-10)
+    assert x.abs().max().item() == 0.0 and it == 0
+
+
 @pytest.mark.parametrize("op", [lqcd.SCHUR_R, lqcd.SCHUR_RDAG, lqcd.SCHUR_RINV, lqcd.SCHUR_RINVDAG])
 def test_schur(setup, op):
     lat, olat, U, kappa, seed = setup
