@@ -18,7 +18,7 @@
  *   T_U, T_P, LF, SW      Sec. 2, eqs. (4)-(7)
  *   recursive levels      Sec. 2, eqs. (iterateLF), (iterateSW)
  *   x0 shift              end of Sec. 2
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent (each one restated at its function):
  *   chiral gamma basis; fermion phase bc_t on the x0 wrap; the boundary
  *   operator R = Pi (1 - C A^-1 B D^-1) Pi obtained by block LU of eq. (2)
  *   (the paper cites Luscher's eqs. (3.12)-(3.13) without restating them);

@@ -9,8 +9,10 @@ calls the library's force kernel, which recomputes the solver solutions
 instead of keeping them from the forward pass.  The gradient is the force
 dS/domega^a at the rotated links, i.e. the exact gradient at omega = 0 (the
 point where the molecular dynamics uses it) and the left-trivialised
-derivative elsewhere.  Argument marshalling only: every step runs in the
-library's kernels.
+derivative elsewhere.  Both passes leave the lattice handle holding the
+caller's links U again (they install the rotated links only while they
+evaluate).  Argument marshalling only: every step runs in the library's
+kernels.
 """
 import torch
 
@@ -34,7 +36,8 @@ class PseudoFermionAction(torch.autograd.Function):
                 rho=0.0):
         Uw = lat.link_update(U, omega.detach().contiguous(), 1.0)
         S, _ = _evaluate(lat, term, phi, kappa, rho, precision, tol, max_iter, False)
-        ctx.lat, ctx.Uw, ctx.phi = lat, Uw, phi
+        lat.set_gauge(U)
+        ctx.lat, ctx.U, ctx.Uw, ctx.phi = lat, U, Uw, phi
         ctx.args = (kappa, term, precision, tol, max_iter, rho)
         return torch.tensor(S, dtype=torch.float64, device=omega.device)
 
@@ -43,6 +46,7 @@ class PseudoFermionAction(torch.autograd.Function):
         kappa, term, precision, tol, max_iter, rho = ctx.args
         ctx.lat.set_gauge(ctx.Uw)
         _, F = _evaluate(ctx.lat, term, ctx.phi, kappa, rho, precision, tol, max_iter, True)
+        ctx.lat.set_gauge(ctx.U)
         return (grad_out * F,) + (None,) * 9
 
 

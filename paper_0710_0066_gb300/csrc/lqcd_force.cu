@@ -701,11 +701,16 @@ int static_partials(double** out)
 extern "C" int lqcd_gauge_action_static(const int L[4], const double* U, double beta, double* out, void* stream)
 {
     if (!L || !U || !out) return LQCD_ERR_ARG;
-    for (int mu = 0; mu < 4; ++mu)
-        if (L[mu] < 2 || (L[mu] & 1)) return LQCD_ERR_GEOM;
-    const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+    // every extent and every partial product stays within the site bound
+    // before the next multiplication, so the volume cannot overflow
+    const int64_t max_sites = (int64_t)STATIC_MAX_BLOCKS * STATIC_SITES_PER_BLOCK;
+    int64_t V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (L[mu] < 2 || (L[mu] & 1) || L[mu] > max_sites) return LQCD_ERR_GEOM;
+        V *= L[mu];
+        if (V > max_sites) return LQCD_ERR_GEOM;
+    }
     const int64_t nblocks = (V + STATIC_SITES_PER_BLOCK - 1) / STATIC_SITES_PER_BLOCK;
-    if (nblocks > STATIC_MAX_BLOCKS) return LQCD_ERR_GEOM;
     double* part = nullptr;
     const int st = static_partials(&part);
     if (st != LQCD_OK) return st;

@@ -74,6 +74,12 @@ def test_static_gauge_action_validates_on_the_host(lib):
     assert f(ctypes.byref((ctypes.c_int * 4)(4, 3, 4, 4)), dummy, 5.6, dummy, None) == -2
     # more than 2,097,152 sites: beyond the fixed partial-sum array
     assert f(ctypes.byref((ctypes.c_int * 4)(128, 32, 32, 32)), dummy, 5.6, dummy, None) == -2
+    # extents whose 64-bit product would overflow (2^30 each: 2^120 sites)
+    # or wrap to a small value are rejected before any multiplication
+    big = 1 << 30
+    assert f(ctypes.byref((ctypes.c_int * 4)(big, big, big, big)), dummy, 5.6, dummy, None) == -2
+    assert f(ctypes.byref((ctypes.c_int * 4)(2, 2, 2, 2147483646)), dummy, 5.6, dummy, None) == -2
+    assert f(ctypes.byref((ctypes.c_int * 4)(4194304, 2, 2, 2)), dummy, 5.6, dummy, None) == -2
 
 
 def test_null_handle_is_an_argument_error(lib):
