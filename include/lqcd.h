@@ -406,6 +406,16 @@ int lqcd_profile_times(lqcd_t h, int kernel_id, float* ms_out, int64_t cap, int6
 int lqcd_autotune(lqcd_t h, int what, double kappa);
 int lqcd_tune_read(lqcd_t h, int* out);
 
+/* Limit of one barrier wait inside the persistent solver, in GPU clock
+ * cycles (clock64): a CTA that has waited that long for the other CTAs of
+ * its system gives up, the solve ends with LQCD_ERR_TIMEOUT and every CTA
+ * returns at its next barrier; the handle stays usable.  cycles <= 0
+ * restores the default, 4e9 cycles (about two seconds).  A diagnostic for
+ * exercising the bounded-wait path (the paper has no counterpart); it
+ * applies to solves launched after the call (a recorded MD graph is
+ * recorded again).  Host only, never fails on a valid handle. */
+int lqcd_set_wait_limit(lqcd_t h, int64_t cycles);
+
 /* Number of kernels this handle has launched since lqcd_create (host
  * counter; *count is a host int64). */
 int lqcd_launch_count(lqcd_t h, int64_t* count);

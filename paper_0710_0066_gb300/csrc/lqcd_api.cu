@@ -593,7 +593,7 @@ std::vector<unsigned char> md_key(const lqcd_ctx* h, const lqcd_hmc_params& p)
                              (double)p.level_s2, (double)p.level_s1, p.rho, (double)p.precision, p.tol,
                              (double)p.max_iter, (double)p.eo_solver, (double)p.block_solver,
                              (double)p.step_scheme, (double)p.chrono,
-                             (double)h->prof.on, (double)h->g1.l0s};
+                             (double)h->prof.on, (double)h->g1.l0s, (double)h->wait_limit};
     for (int q = 0; q < 3; ++q) {
         k.push_back((double)h->tune.hop_bs[q]);
         k.push_back((double)h->tune.solve_spt[q][0]);
@@ -665,7 +665,12 @@ int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const do
         h->md_nforce = nf;
         h->md_solves = ns;
     }
-    LQ_TRY(solver_collect(h, nullptr, nullptr));  // clears what eager solves left
+    {
+        // clears what eager solves left in the sticky word; each of them has
+        // already reported its own status, so only a failed read counts
+        const int st0 = solver_collect(h, nullptr, nullptr);
+        if (st0 == LQCD_ERR_CUDA) return st0;
+    }
     LQ_CUDA(h, cudaGraphLaunch(h->md_exec, h->stream));
     h->launches += h->md_launches;
     h->solve_count += h->md_solves;
@@ -1634,6 +1639,13 @@ int lqcd_force_profile(lqcd_t h, const double* F, double* out)
     CHECK_H(h);
     NEED(F && out, "null force / output pointer");
     return force_profile(h, F, out);
+}
+
+int lqcd_set_wait_limit(lqcd_t h, int64_t cycles)
+{
+    CHECK_H(h);
+    h->wait_limit = cycles > 0 ? (long long)cycles : lqcd_ctx::WAIT_LIMIT_DEFAULT;
+    return LQCD_OK;
 }
 
 int lqcd_launch_count(lqcd_t h, int64_t* count)

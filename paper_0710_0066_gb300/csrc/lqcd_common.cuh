@@ -771,6 +771,10 @@ struct lqcd_ctx {
     int64_t site_iters = 0;  // inner iterations x even sites of the system
     int64_t hop_sites = 0;   // half-lattice hopping site updates of those iterations
     int solve_count = 0;
+    // clock64 cycles a CTA of the persistent solver waits at a barrier
+    // before the solve gives up with LQCD_ERR_TIMEOUT (lqcd_set_wait_limit)
+    static constexpr long long WAIT_LIMIT_DEFAULT = 4000000000LL;  // ~2 s
+    long long wait_limit = WAIT_LIMIT_DEFAULT;
 };
 
 // switches the handle to another geometry for the lifetime of the scope

@@ -15,8 +15,9 @@
 // The systems never wait for one another: a group meets only at its own
 // software barrier (one counter per system), loops until its own system has
 // converged and returns; the kernel ends when every group has.  The barrier
-// wait is bounded (about two seconds): on time-out the kernel records
-// LQCD_ERR_TIMEOUT and every CTA returns.
+// wait is bounded (about two seconds unless lqcd_set_wait_limit says
+// otherwise): on time-out the kernel records LQCD_ERR_TIMEOUT and every CTA
+// returns at its next barrier.
 #include <stdio.h>
 
 #include <algorithm>
@@ -28,7 +29,6 @@ namespace {
 constexpr int SBS = 256;
 constexpr int NSYS_MAX = 64;
 constexpr int NQ = 3;
-constexpr long long SPIN_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
 
 // per-system state codes in the flag arrays
 enum { F_ACTIVE = 0, F_DONE = 1, F_NAN = 2, F_MAXIT = 3 };
@@ -60,6 +60,7 @@ struct SolveArgs {
     int* iters;         // [nsys]
     double* resid;      // [nsys]
     int* outer_out;
+    long long spin_limit;  // clock64 cycles of one barrier wait before LQCD_ERR_TIMEOUT
 };
 
 struct SysSt {  // the CTA's own system
@@ -79,7 +80,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 }
 
 // barrier over the cps CTAs of one system (the systems are independent and
-// never wait for one another); bounded: gives up after SPIN_LIMIT cycles
+// never wait for one another); bounded: gives up after A.spin_limit cycles
 __device__ bool sys_sync(const SolveArgs& A, int sys, unsigned& epoch)
 {
     __shared__ int s_bad;
@@ -94,7 +95,7 @@ __device__ bool sys_sync(const SolveArgs& A, int sys, unsigned& epoch)
         int bad = 0;
         while (ld_acquire(bar) < target) {
             if (*(volatile int*)A.status == LQCD_ERR_TIMEOUT) { bad = 1; break; }
-            if (clock64() - t0 > SPIN_LIMIT) {
+            if (clock64() - t0 > A.spin_limit) {
                 atomicExch(A.status, LQCD_ERR_TIMEOUT);
                 atomicCAS(A.sticky, 0, LQCD_ERR_TIMEOUT);
                 bad = 1;
@@ -932,6 +933,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.iters = w->iters;
     A.resid = w->resid;
     A.outer_out = w->outer;
+    A.spin_limit = h->wait_limit;
     LQ_CUDA(h, cudaMemsetAsync(w->bar, 0, sizeof(unsigned) * BAR_STRIDE * A.nsys, h->stream));
     LQ_CUDA(h, cudaMemsetAsync(w->status, 0, sizeof(int) * 4, h->stream));
     void* args[] = {&A};

@@ -38,7 +38,7 @@ EXPORTS = [
     "lqcd_profile_enable", "lqcd_profile_reset", "lqcd_profile_read", "lqcd_launch_count",
     "lqcd_gauge_action_static", "lqcd_force_profile", "lqcd_set_subslabs", "lqcd_subblock_dslash",
     "lqcd_subblock_solve_batched", "lqcd_subblock_eo", "lqcd_pf_force_eo", "lqcd_link_update",
-    "lqcd_autotune", "lqcd_tune_read", "lqcd_profile_times",
+    "lqcd_autotune", "lqcd_tune_read", "lqcd_profile_times", "lqcd_set_wait_limit",
 ]
 
 
@@ -134,6 +134,7 @@ def load():
         "lqcd_launch_count": [vp, vp],
         "lqcd_gauge_action_static": [C.POINTER(C.c_int * 4), vp, d, vp, vp],
         "lqcd_force_profile": [vp, vp, vp],
+        "lqcd_set_wait_limit": [vp, i64],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -238,6 +239,10 @@ def lqcd_tune_read(h):
     return {"hop_block_size": dict(zip(("f64", "f32", "f16"), v[0:3])),
             "slab_solve_sites_per_thread": dict(zip(("f64", "f32", "f16"), v[3:6])),
             "global_solve_sites_per_thread": dict(zip(("f64", "f32", "f16"), v[6:9]))}
+
+
+def lqcd_set_wait_limit(h, cycles):
+    return _check(h, load().lqcd_set_wait_limit(h, int(cycles)))
 
 
 def lqcd_link_update(h, U, P, dt):

@@ -150,7 +150,7 @@ def test_gauge_force_and_action(setup):
     assert rel(F, olat.gauge_force(U, 5.6)) < 1e-12
 
 
-@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F16])
+@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16])
 def test_pf_force_w1(setup, prec):
     lat, olat, U, kappa, seed = setup
     phi = syn.gaussian_spinor(olat.V, seed + 6)
