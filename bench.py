@@ -39,6 +39,8 @@ WORKLOAD_NAME = ("Schwarz-HMC trajectory 16^3x32, l0=4 (8 x0-slabs, red/black), 
                  "Schur force, n=(2,4,8); links exp(i 0.6 H) thermalised by 40 pure-gauge HMC "
                  "trajectories at beta=5.6")
 DSLASH_L = (64, 32, 32, 32)
+# the one metric both arms print (the precision is in dtype / config)
+METRIC = "s/HMC trajectory (16^3x32 Schwarz HMC)"
 
 
 def thermalise(lat, U, beta, ntraj, seed):
@@ -54,6 +56,26 @@ def thermalise(lat, U, beta, ntraj, seed):
         prm.metropolis = 1 if t >= min(20, ntraj // 2) else 0
         U, res = lat.hmc_trajectory(U, prm, seed, 1000000 + t)
     return U, res
+
+
+def thermalise_dynamical(lat, U, prm, ntraj, seed):
+    """input preparation, continued: full trajectories with the fermion
+    action (the timed schedule at a looser solver tolerance) from the
+    pure-gauge start, so that the plaquette and the solver work are
+    stationary over the timed trajectories; returns the field and the
+    plaquettes seen"""
+    tol, graph = prm.tol, prm.use_graph
+    prm.tol, prm.use_graph = 1e-8, 0
+    plaq = []
+    try:
+        for t in range(ntraj):
+            U, res = lat.hmc_trajectory(U, prm, seed, 2000000 + t)
+            plaq.append(res.plaq)
+    finally:
+        prm.tol, prm.use_graph = tol, graph
+    return U, plaq
+
+
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 # DRAM bytes per k_solve launch from the ncu capture summarised in
@@ -148,16 +170,22 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # oracle timing (host cores)
 # ---------------------------------------------------------------------------
-def oracle_M_seconds(budget_s, L, l0, eps, seed):
-    """seconds per application of the oracle's full-lattice Wilson matrix"""
-    import numpy as np
-
+def oracle_problem(L, l0, eps, seed):
+    """the oracle lattice, links and a source of the workload (built once)"""
     from oracle import oracle as O
     from paper_0710_0066_gb300 import synthetic as syn
 
     lat = O.Lattice(L, l0, -1)
     U = syn.random_links(L, eps, seed)
     x = syn.gaussian_spinor(lat.V, seed + 1)
+    return lat, U, x
+
+
+def oracle_M_seconds(budget_s, L, l0, eps, seed, problem=None):
+    """seconds per application of the oracle's full-lattice Wilson matrix"""
+    import numpy as np
+
+    lat, U, x = problem if problem is not None else oracle_problem(L, l0, eps, seed)
     lat.M(U, 0.1575, x)
     n, t0 = 0, time.perf_counter()
     while True:
@@ -173,14 +201,17 @@ def oracle_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
-# Wilson-matrix applications in one trajectory of this workload: the
-# library counts the half-lattice hopping site updates of every inner
-# iteration (hop_sites; a full application is V of them); the value below is
-# that count for the 16^3x32 run with every solve started from zero, as
-# the oracle solves (geometric series for W1, BiCGstab elsewhere,
-# single-precision inner storage), used by the reference arm, which runs
-# without a GPU.  The GPU's chronological guesses bring it to ~17.2 k.
-M_APPS_PER_TRAJ_DEFAULT = 25187.0
+# Wilson-matrix applications in one trajectory of this workload, the count
+# both oracle figures (the reference arm and cpu_baseline) scale the
+# oracle's measured time per application by: the library counts the
+# half-lattice hopping site updates of every inner iteration (hop_sites; a
+# full application is V of them), and this is that count for the 16^3x32
+# trajectory with every solve started from zero (the method's own work:
+# geometric series for W1, BiCGstab elsewhere).  The oracle's own solver,
+# CG on the normal equations, needs several times more applications (about
+# 500 for one slab solve of a thermalised 16x4^3 field to 1e-10), so the
+# figure is a lower bound on the oracle's time.
+M_APPS_PER_TRAJ = 25187.0
 
 
 def job_time(rank_ms, steps, dist=None, device="cpu"):
@@ -205,21 +236,32 @@ def run_reference(args):
     if rank != 0:
         return
     L, l0 = WL["L"], WL["l0"]
-    times = []
+    times, wall, napp = [], [], 0
+    problem = oracle_problem(L, l0, WL["eps"], WL["seed"])
     for k in range(args.warmup + args.steps):
-        t_M, n = oracle_M_seconds(8.0, L, l0, WL["eps"], WL["seed"])
+        w0 = time.perf_counter()
+        t_M, n = oracle_M_seconds(args.ref_sample_seconds, L, l0, WL["eps"], WL["seed"], problem)
         if k >= args.warmup:
-            times.append(t_M * M_APPS_PER_TRAJ_DEFAULT)
+            times.append(t_M * M_APPS_PER_TRAJ)
+            wall.append(time.perf_counter() - w0)
+            napp += n
     v = statistics.mean(times)
+    sample = ("per step %.1f s of wall time: applications of the oracle's FP64 Wilson matrix at 16^3x32 "
+              "(%.1f ms each), the seconds per application scaled by %d applications per trajectory (the "
+              "method's count with every solve from zero; the oracle's CGNR needs more, so this is a lower "
+              "bound)" % (statistics.mean(wall), 1e3 * statistics.mean(times) / M_APPS_PER_TRAJ,
+                          M_APPS_PER_TRAJ))
     line = {
-        "impl": "reference", "metric": "s/HMC trajectory (16^3x32 Schwarz HMC)", "value": v,
+        "impl": "reference", "metric": METRIC, "value": v,
         "unit": "s/trajectory", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD_NAME},
+        "ms_per_step": 1e3 * statistics.mean(wall), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD_NAME},
+        "extrapolated": {"model": "oracle seconds per Wilson-matrix application x %d applications per trajectory"
+                                  % M_APPS_PER_TRAJ,
+                         "measured_wall_s_per_step": statistics.mean(wall),
+                         "applications_timed": napp},
         "cpu_baseline": {"value": v, "unit": "s/trajectory", "cores": oracle_threads(), "kind": "oracle",
-                         "sample": "per step ~8 s of oracle Wilson-matrix applications (FP64, 16^3x32), "
-                                   "scaled by %d applications per trajectory (every solve from zero, as the "
-                                   "oracle solves)" % M_APPS_PER_TRAJ_DEFAULT},
+                         "sample": sample},
         "e2e": {"value": v, "unit": "s/trajectory", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -254,6 +296,8 @@ def run_ours(args):
     lat.set_gauge(U0)
     lqcd.lqcd_autotune(lat.h, 3, WL["kappa"])
     tune = lqcd.lqcd_tune_read(lat.h)
+    if args.global_solver == "sap":
+        lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP, args.sap_terms)
 
     def params(prec):
         return lqcd.hmc_params(WL["beta"], WL["kappa"], WL["tau"], WL["nlevels"], WL["scheme"], WL["nsteps"],
@@ -265,25 +309,32 @@ def run_ours(args):
 
     prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     prm = params(prec)
+    block_solver = args.block_solver
+
+    def run_or_fall_back(fn):
+        # the geometric series needs its spectral radius below one; if a slab
+        # of this field does not satisfy that, the W1 solves fall back to
+        # BiCGstab for the whole measurement (reported)
+        nonlocal prm, block_solver
+        try:
+            return fn()
+        except lqcd.LqcdError as e:
+            if e.status != lqcd.ERR_NOCONVERGE or args.block_solver != "series":
+                raise
+            block_solver = "bicgstab (the series did not converge on this field)"
+            args.block_solver = "bicgstab"
+            prm = params(prec)
+            return fn()
+
+    U0, plaq_dyn = run_or_fall_back(lambda: thermalise_dynamical(lat, U0, prm, args.therm_fermion,
+                                                                 WL["seed"] + rank))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     stream = torch.cuda.current_stream()
 
     U = U0.clone()
     traj = 0
-    block_solver = args.block_solver
     for _ in range(args.warmup):
-        try:
-            U, res = lat.hmc_trajectory(U, prm, WL["seed"], traj)
-        except lqcd.LqcdError as e:
-            # the geometric series needs its spectral radius below one; if a
-            # slab of this field does not satisfy that, the W1 solves fall
-            # back to BiCGstab for the whole measurement (reported)
-            if e.status != lqcd.ERR_NOCONVERGE or block_solver != "series":
-                raise
-            block_solver = "bicgstab (the series did not converge on this field)"
-            args.block_solver = "bicgstab"
-            prm = params(prec)
-            U, res = lat.hmc_trajectory(U, prm, WL["seed"], traj)
+        U, res = run_or_fall_back(lambda: lat.hmc_trajectory(U, prm, WL["seed"], traj))
         traj += 1
     torch.cuda.synchronize()
 
@@ -315,28 +366,37 @@ def run_ours(args):
     lqcd.lqcd_profile_enable(lat.h, 0)
     total_ms, value = job_time(sum(step_ms), args.steps, dist, "cuda")
 
-    # ---- plain double-precision GPU form on the first timed input
+    # ---- plain double-precision GPU form on the inputs of the first timed
+    # trajectories (one untimed trajectory first records its MD graph)
     fp64 = None
     if not args.no_fp64 and prec != lqcd.PREC_F64:
-        Uk, tk = U_in[0]
         prm64 = params(lqcd.PREC_F64)
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, r64 = lat.hmc_trajectory(Uk, prm64, WL["seed"], tk)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        fp64 = {"s_per_traj": t64, "dH": r64.dH, "dH_mixed": results[0].dH,
-                "abs_dH_diff": abs(r64.dH - results[0].dH),
-                "speedup_mixed_vs_fp64": t64 / (step_ms[0] / 1e3),
-                "solver_iters": r64.solver_iters}
+        lat.hmc_trajectory(U_in[0][0], prm64, WL["seed"], U_in[0][1])
+        t64, d64 = [], []
+        nf = min(args.fp64_steps, len(U_in))
+        for k in range(nf):
+            Uk, tk = U_in[k]
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, r64 = lat.hmc_trajectory(Uk, prm64, WL["seed"], tk)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t64.append(a.elapsed_time(b) / 1e3)
+            d64.append(abs(r64.dH - results[k].dH))
+        mixed = statistics.mean(step_ms[:nf]) / 1e3
+        fp64 = {"s_per_traj": statistics.mean(t64), "trajectories": nf,
+                "mixed_s_per_traj_same_inputs": mixed, "speedup_mixed_vs_fp64": statistics.mean(t64) / mixed,
+                "max_abs_dH_diff": max(d64)}
 
     # ---- end to end through the C-ABI with host buffers
     Uh = torch.empty_like(U, device="cpu").pin_memory()
     Uh.copy_(U)
     Ud = torch.empty_like(U)
     e2e_ms = []
-    for k in range(2):
+    for k in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Ud.copy_(Uh, non_blocking=True)
@@ -345,10 +405,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         traj += 1
-    e2e_value = e2e_ms[-1] / 1e3
+    e2e_value = statistics.mean(e2e_ms[1:]) / 1e3
     ubytes = U.numel() * 16
 
     # ---- Dslash (even-odd hopping sweep) bandwidth at 32^3 x 64 (> L2)
+    peak, peak_kind = hbm_peak()
     dslash = {}
     if not args.no_dslash:
         latd = lqcd.Lattice(DSLASH_L, 8, -1)
@@ -373,16 +434,15 @@ def run_ours(args):
             per = lqcd.lqcd_profile_times(latd.h, lqcd.KERNEL_HOP)
             lqcd.lqcd_profile_enable(latd.h, 0)
             med = statistics.median(per)
-            dslash[name] = {"gbs": by / n / med / 1e6, "ms_median": med, "ms_min": min(per),
-                            "bytes_per_launch": by / n, "launches": len(per),
-                            "frac_of_peak": by / n / med / 1e6 / hbm_peak()[0]}
-        dslash["hop_block_size"] = lqcd.lqcd_tune_read(latd.h)["hop_block_size"]
+            dslash[name] = {"gbs": round(by / n / med / 1e6, 1), "frac": round(by / n / med / 1e6 / peak, 4),
+                            "ms_median": round(med, 4), "bytes_per_launch": by / n}
         latd.close()
 
-    # ---- force-profile diagnostic (Sec. 3, Fig. 1) on the thermalised field:
-    # mean |F| on space-like links per time slice for each action term
-    profile = {}
-    if not args.no_dslash:
+    # ---- force-profile diagnostic (Sec. 3, Fig. 1) on the thermalised field
+    # (--force-profile): mean |F| on space-like links per time slice
+    profile = None
+    if args.force_profile:
+        profile = {}
         lat.set_gauge(U)
         g = torch.Generator(device="cuda")
         g.manual_seed(WL["seed"] + 11)
@@ -396,53 +456,67 @@ def run_ours(args):
         for name, F in (("gauge", Fg), ("w1", Fw), ("schur", Fs)):
             profile[name] = [round(v, 5) for v in lat.force_profile(F)[0].tolist()]
 
-    # ---- oracle on the host cores (bounded sample)
-    # Wilson-matrix applications of one trajectory's inner iterations (a
-    # full application is two half-lattice sweeps, V site updates)
+    # ---- oracle on the host cores (bounded sample), scaled by the same
+    # application count as the reference arm
     m_apps = statistics.mean(r.hop_sites for r in results) / lat.V
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         t_M, n = oracle_M_seconds(args.cpu_seconds, L, l0, WL["eps"], WL["seed"])
-        cpu = {"value": t_M * m_apps, "unit": "s/trajectory", "cores": oracle_threads(), "kind": "oracle",
-               "sample": "%d applications of the oracle's FP64 Wilson matrix at 16^3x32 (%.2f s each), "
-                         "scaled by the %.0f matrix applications of one GPU trajectory" % (n, t_M, m_apps)}
+        cpu = {"value": t_M * M_APPS_PER_TRAJ, "unit": "s/trajectory", "cores": oracle_threads(), "kind": "oracle",
+               "sample": "%d applications of the oracle's FP64 Wilson matrix at 16^3x32 (%.1f ms each) x %d "
+                         "applications per trajectory (solves from zero; a lower bound for the oracle's CGNR)"
+                         % (n, 1e3 * t_M, M_APPS_PER_TRAJ)}
 
-    peak, peak_kind = hbm_peak()
     achieved = by_sol / ms_sol / 1e6 if ms_sol > 0 else None
     traffic, traffic_detail = solver_traffic() if prec == lqcd.PREC_F32 else (None, None)
+    sm = step_ms
+    half = max(1, len(sm) // 2)
     line = {
-        "metric": "s/HMC trajectory (16^3x32 Schwarz HMC, mixed precision batched)",
+        "metric": METRIC,
         "value": value, "unit": "s/trajectory", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "lattice": "x".join(map(str, L)), "l0": l0,
                    "inner_precision": args.precision, "l2": "flushed between timed trajectories",
-                   "parallelism": "replicas" if world > 1 else "1 GPU", "autotune": tune,
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
                    "md_as_cuda_graph": not args.no_graph, "w1_block_solver": block_solver,
-                   "chronological_guesses": not args.no_chrono},
+                   "chronological_guesses": not args.no_chrono,
+                   "global_solver": ("Schwarz-preconditioned BiCGstab, %d series terms per slab solve"
+                                     % args.sap_terms) if args.global_solver == "sap"
+                                    else "even-odd BiCGstab",
+                   "dynamical_thermalisation": args.therm_fermion},
         "roofline": {"bound": "hbm", "kernel": "persistent batched solver (k_solve)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "traffic_per_launch": traffic_detail,
-                     "alg_bytes_per_launch": by_sol / n_sol if n_sol else None,
                      "peak_kind": peak_kind, "launches": n_sol,
-                     "kernel_share_of_step": ms_sol / total_ms if total_ms else None},
-        "dslash": dslash,
-        "force_profile_spatial": profile,
+                     "kernel_share_of_step": ms_sol / total_ms if total_ms else None,
+                     "dslash_64x32x32x32": dslash},
         "fp64_form": fp64,
-        "thermalisation": {"trajectories": WL["therm"], "plaq": rth.plaq if rth else None},
-        "trajectory": {"dH": [r.dH for r in results], "accepted": [r.accepted for r in results],
-                       "plaq": results[-1].plaq, "solver_iters": [r.solver_iters for r in results],
-                       "n_solves": results[-1].n_solves, "n_force": results[-1].n_force,
-                       "step_ms": step_ms},
-        "e2e": {"value": e2e_value, "unit": "s/trajectory", "h2d_bytes_per_step": ubytes,
-                "d2h_bytes_per_step": ubytes},
+        "trajectory": {"step_ms_first_half_mean": statistics.mean(sm[:half]),
+                       "step_ms_second_half_mean": statistics.mean(sm[half:]) if len(sm) > 1 else sm[0],
+                       "step_ms_min": min(sm), "step_ms_max": max(sm),
+                       "solver_iters_first": results[0].solver_iters, "solver_iters_last": results[-1].solver_iters,
+                       "plaq_first": results[0].plaq, "plaq_last": results[-1].plaq,
+                       "acceptance": sum(r.accepted for r in results) / len(results),
+                       "dH_rms": math.sqrt(statistics.mean(r.dH ** 2 for r in results)),
+                       "n_solves": results[-1].n_solves, "n_force": results[-1].n_force},
         "m_apps_per_traj": m_apps,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "s/trajectory", "h2d_bytes_per_step": ubytes,
+                "d2h_bytes_per_step": ubytes},
     }
+    if profile is not None:
+        line["force_profile_spatial"] = profile
+    if args.detail and rank == 0:
+        with open(args.detail, "w") as f:
+            json.dump({"step_ms": step_ms, "solver_iters": [r.solver_iters for r in results],
+                       "plaq": [r.plaq for r in results], "dH": [r.dH for r in results],
+                       "accepted": [r.accepted for r in results], "plaq_dynamical_thermalisation": plaq_dyn,
+                       "pure_gauge_plaq": rth.plaq if rth else None, "autotune": tune,
+                       "solver_traffic": traffic_detail, "fp64": fp64, "e2e_ms": e2e_ms}, f)
     if rank == 0:
         print(json.dumps(line), flush=True)
     lat.close()
@@ -625,11 +699,19 @@ def run_case(args):
     if args.case == "table1":
         return run_iterated(args, WL_TABLE1)
     if args.case == "solver":
-        # the batched slab solve (8 slabs) and the global solve of the workload
+        # the batched slab solve (8 slabs) and the global solve of the
+        # workload, on the field the timed trajectories start from (pure-
+        # gauge, then dynamical thermalisation)
         L, l0 = WL["L"], WL["l0"]
         lat = lqcd.Lattice(L, l0, -1)
         U = syn.random_links_torch(L, WL["eps"], WL["seed"], "cuda").contiguous()
-        U, _ = thermalise(lat, U, WL["beta"], 20, WL["seed"])
+        U, _ = thermalise(lat, U, WL["beta"], WL["therm"], WL["seed"])
+        if args.therm_fermion:
+            prm = lqcd.hmc_params(WL["beta"], WL["kappa"], WL["tau"], WL["nlevels"], WL["scheme"], WL["nsteps"],
+                                  WL["level_gauge"], WL["level_w1"], WL["level_schur"], lam=WL["lam"], roll=1,
+                                  metropolis=1, precision=lqcd.PREC_F32, tol=WL["tol"], max_iter=WL["max_iter"],
+                                  chrono=1, block_solver=lqcd.SOLVER_SERIES)
+            U, _ = thermalise_dynamical(lat, U, prm, args.therm_fermion, WL["seed"])
         lat.set_gauge(U)
         b = torch.randn((lat.V, 4, 3), dtype=torch.complex128, device="cuda", generator=g)
         lqcd.lqcd_profile_enable(lat.h, 1 << lqcd.KERNEL_SOLVER)
@@ -655,6 +737,19 @@ def run_case(args):
                 x, it, rs = lat.solve(b, WL["kappa"], 0, prec, tol=WL["tol"])
             n, ms, by = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
             out[name] = {"iters": it, "resid": rs, "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6}
+        # the global solve with the Schwarz preconditioner (Sec. 3, S4
+        # solver) for several series lengths of its slab solves; each timed
+        # after one untimed solve
+        if hasattr(lqcd, "SOLVER_SAP"):
+            for nsap in args.sap_sweep:
+                lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP, nsap)
+                lat.solve(b, WL["kappa"], 0, prec, tol=WL["tol"])
+                lqcd.lqcd_profile_reset(lat.h)
+                x, it, rs = lat.solve(b, WL["kappa"], 0, prec, tol=WL["tol"])
+                n, ms, by = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
+                out["global_sap%d" % nsap] = {"iters": it, "resid": rs, "ms": ms, "alg_bytes": by,
+                                              "gbs": by / ms / 1e6}
+            lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_BICGSTAB, 0)
         print(json.dumps({"case": "solver", "lattice": "x".join(map(str, L)), "precision": args.precision,
                           **out}), flush=True)
         lat.close()
@@ -695,6 +790,23 @@ def main():
                          "geometric series by default)")
     ap.add_argument("--eo-solver", default="bicgstab", choices=["bicgstab", "series"],
                     help="inner iteration of the S2 / S1 solves (--case production)")
+    ap.add_argument("--therm-fermion", type=int, default=80,
+                    help="trajectories with the fermion action after the pure-gauge thermalisation "
+                         "(input preparation, untimed)")
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="trajectories of the plain double form timed on the first timed inputs")
+    ap.add_argument("--ref-sample-seconds", type=float, default=5.0,
+                    help="--impl reference: wall seconds of oracle work per step")
+    ap.add_argument("--force-profile", action="store_true",
+                    help="add the per-time-slice force profile of each term to the line")
+    ap.add_argument("--detail", default=None, help="write per-trajectory records to this JSON file")
+    ap.add_argument("--global-solver", default="bicgstab", choices=["bicgstab", "sap"],
+                    help="inner iteration of the whole-lattice solves: even-odd BiCGstab, or BiCGstab "
+                         "with the Schwarz preconditioner over the x0-slabs (Sec. 3, S4 solver)")
+    ap.add_argument("--sap-terms", type=int, default=4,
+                    help="geometric-series terms of every slab solve of the Schwarz preconditioner")
+    ap.add_argument("--sap-sweep", type=int, nargs="*", default=[1, 2, 4, 8],
+                    help="--case solver: series lengths of the Schwarz-preconditioned global solves timed")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
