@@ -83,7 +83,7 @@ enum { LQCD_SCHUR_R = 0, LQCD_SCHUR_RDAG = 1, LQCD_SCHUR_RINV = 2, LQCD_SCHUR_RI
 enum { LQCD_TERM_W1 = 0, LQCD_TERM_SCHUR = 1, LQCD_TERM_W2 = 2, LQCD_TERM_SCHUR2 = 3,
        LQCD_TERM_S2 = 4, LQCD_TERM_S1 = 5 };
 enum { LQCD_EO_APPLY = 0, LQCD_EO_SOLVE = 1 };
-enum { LQCD_SOLVER_BICGSTAB = 0, LQCD_SOLVER_SERIES = 1 };
+enum { LQCD_SOLVER_BICGSTAB = 0, LQCD_SOLVER_SERIES = 1, LQCD_SOLVER_SAP = 2 };
 enum { LQCD_MAX_LEVELS = 5 };
 enum { LQCD_LF = 0, LQCD_SW = 1 };
 
@@ -191,9 +191,10 @@ int lqcd_subblock_eo(lqcd_t h, double* out, const double* in, double kappa, doub
                      int* iters_out);
 
 /* Solve M x = b (dagger: M^dag x = b) on the full lattice: even-odd reduced
- * BiCGstab, inner iterations in `precision`, double precision defect
- * correction to |b - M x| <= tol |b|.  iters_out / resid_out: host scalars
- * (may be NULL).  Synchronous.  (Sec. 3: the S4 solver.) */
+ * system, double precision defect correction to |b - M x| <= tol |b|, inner
+ * iterations in `precision` by the handle's global solver
+ * (lqcd_set_global_solver).  iters_out / resid_out: host scalars (may be
+ * NULL).  Synchronous.  (Sec. 3: the S4 solver.) */
 int lqcd_solve_wilson(lqcd_t h, double* x, const double* b, double kappa, int dagger,
                       int precision, double tol, int max_iter, int* iters_out,
                       double* resid_out);
@@ -405,6 +406,24 @@ int lqcd_profile_times(lqcd_t h, int kernel_id, float* ms_out, int64_t cap, int6
  * per thread [F64, F32, F16]. */
 int lqcd_autotune(lqcd_t h, int what, double kappa);
 int lqcd_tune_read(lqcd_t h, int* out);
+
+/* Inner iteration of every whole-lattice solve of the handle (the S4
+ * solver of Sec. 3: lqcd_solve_wilson, R^-1 / R^-dag and the boundary-term
+ * force, and the trajectory's), inside the same double defect correction:
+ *   LQCD_SOLVER_BICGSTAB (default): BiCGstab on the even-odd reduced
+ *     matrix 1 - kappa^2 H_eo H_oe;
+ *   LQCD_SOLVER_SAP: the paper's "BiCGstab with even-odd and Schwarz
+ *     preconditioning": BiCGstab on M with right preconditioner K^-1, one
+ *     multiplicative Schwarz cycle over the x0-slabs (all red slabs, then
+ *     all black slabs with the source corrected by the hops from the red
+ *     faces), each slab solve the geometric series of its even-odd reduced
+ *     operator truncated after sap_terms terms (0..64), so that K^-1 is a
+ *     fixed linear map; the inner system M y = (r, 0) gives the even-odd
+ *     reduced correction y_e.  The series needs the slab operator's
+ *     spectral radius below one to precondition well (it always gives a
+ *     valid, if weaker, preconditioner).
+ * Errors: LQCD_ERR_ARG (other methods, sap_terms out of range).  Host only. */
+int lqcd_set_global_solver(lqcd_t h, int method, int sap_terms);
 
 /* Limit of one barrier wait inside the persistent solver, in GPU clock
  * cycles (clock64): a CTA that has waited that long for the other CTAs of

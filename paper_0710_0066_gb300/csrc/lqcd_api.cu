@@ -119,8 +119,10 @@ int solve_full(lqcd_ctx* h, int mode, int colour, int dagger, int prec, double k
     const int hp = prec == PREC64 ? PREC64 : PRECDF;
     LQ_TRY(hop_sweep(h, hp, mode, 0, 0, col, sp64(fld(h, F_T2), 0, Vh), sp64((double2*)bb, 1, Vh), 1.0,
                      sp64((double2*)bb, 0, Vh), kappa));
-    LQ_TRY(eo_solve(h, mode, col, prec, kappa, x, fld(h, F_T2), tol, max_iter, iters, resid, 1.0, method,
-                    guess));
+    // whole-lattice solves take the handle's global solver (plain or
+    // Schwarz-preconditioned BiCGstab), block solves the caller's method
+    LQ_TRY(eo_solve(h, mode, col, prec, kappa, x, fld(h, F_T2), tol, max_iter, iters, resid, 1.0,
+                    mode == MODE_ALL ? h->global_method : method, guess));
     // x_o = b_o + kappa H_oe x_e
     LQ_TRY(hop_sweep(h, hp, mode, 0, 1, col, sp64(x, 1, Vh), sp64(x, 0, Vh), 1.0, sp64((double2*)bb, 1, Vh),
                      kappa));
@@ -593,7 +595,8 @@ std::vector<unsigned char> md_key(const lqcd_ctx* h, const lqcd_hmc_params& p)
                              (double)p.level_s2, (double)p.level_s1, p.rho, (double)p.precision, p.tol,
                              (double)p.max_iter, (double)p.eo_solver, (double)p.block_solver,
                              (double)p.step_scheme, (double)p.chrono,
-                             (double)h->prof.on, (double)h->g1.l0s, (double)h->wait_limit};
+                             (double)h->prof.on, (double)h->g1.l0s, (double)h->wait_limit,
+                             (double)h->global_method, (double)h->sap_terms};
     for (int q = 0; q < 3; ++q) {
         k.push_back((double)h->tune.hop_bs[q]);
         k.push_back((double)h->tune.solve_spt[q][0]);
@@ -675,11 +678,12 @@ int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const do
     h->launches += h->md_launches;
     h->solve_count += h->md_solves;
     *nforce += h->md_nforce;
-    int64_t it = 0, sit = 0, osit = 0, ssit = 0;
-    const int st = solver_collect(h, &it, &sit, &osit, &ssit);
+    int64_t it = 0, sit = 0, osit = 0, ssit = 0, asit = 0;
+    const int st = solver_collect(h, &it, &sit, &osit, &ssit, &asit);
     h->iter_count += it;
-    h->site_iters += sit + ssit;
-    h->hop_sites += 4 * sit + 2 * ssit;
+    h->site_iters += sit + ssit + asit;
+    h->hop_sites += solver_hops_per_iter(SOLVER_BICGSTAB, 0) * sit + solver_hops_per_iter(SOLVER_SERIES, 0) * ssit +
+                    (int64_t)solver_hops_per_iter(SOLVER_SAP, h->sap_terms) * asit;
     // kernel times of this replay (the stream is synchronised); the solver's
     // algorithmic bytes follow from the replay's iteration sums
     if (!h->prof.graph_recs.empty()) {
@@ -692,9 +696,11 @@ int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const do
             if (h->prof.hist[r.id].size() < 65536) h->prof.hist[r.id].push_back(ms);
         }
         double bi, bo, bs;
+        double ba;
         solver_site_bytes(p.precision, SOLVER_BICGSTAB, &bi, &bo);
         solver_site_bytes(p.precision, SOLVER_SERIES, &bs, &bo);
-        h->prof.bytes[1] += (double)sit * bi + (double)ssit * bs + (double)osit * bo;
+        solver_site_bytes(p.precision, SOLVER_SAP, &ba, &bo, h->sap_terms);
+        h->prof.bytes[1] += (double)sit * bi + (double)ssit * bs + (double)asit * ba + (double)osit * bo;
     }
     return st;
 }
@@ -1639,6 +1645,22 @@ int lqcd_force_profile(lqcd_t h, const double* F, double* out)
     CHECK_H(h);
     NEED(F && out, "null force / output pointer");
     return force_profile(h, F, out);
+}
+
+int lqcd_set_global_solver(lqcd_t h, int method, int sap_terms)
+{
+    CHECK_H(h);
+    if (method != LQCD_SOLVER_BICGSTAB && method != LQCD_SOLVER_SAP) {
+        h->err = "global solver: LQCD_SOLVER_BICGSTAB or LQCD_SOLVER_SAP";
+        return LQCD_ERR_ARG;
+    }
+    if (method == LQCD_SOLVER_SAP && (sap_terms < 0 || sap_terms > 64)) {
+        h->err = "global solver: 0 <= sap_terms <= 64";
+        return LQCD_ERR_ARG;
+    }
+    h->global_method = method == LQCD_SOLVER_SAP ? SOLVER_SAP : SOLVER_BICGSTAB;
+    if (method == LQCD_SOLVER_SAP) h->sap_terms = sap_terms;
+    return LQCD_OK;
 }
 
 int lqcd_set_wait_limit(lqcd_t h, int64_t cycles)

@@ -775,6 +775,11 @@ struct lqcd_ctx {
     // before the solve gives up with LQCD_ERR_TIMEOUT (lqcd_set_wait_limit)
     static constexpr long long WAIT_LIMIT_DEFAULT = 4000000000LL;  // ~2 s
     long long wait_limit = WAIT_LIMIT_DEFAULT;
+    // inner iteration of every whole-lattice solve (M^-1 of the boundary
+    // term, lqcd_solve_wilson): SOLVER_BICGSTAB or SOLVER_SAP with sap_terms
+    // series terms per slab solve (lqcd_set_global_solver)
+    int global_method = 0;
+    int sap_terms = 4;
 };
 
 // switches the handle to another geometry for the lifetime of the scope
@@ -854,15 +859,26 @@ void solver_free(lqcd_ctx* h);
 // (site_iters: BiCGstab iterations x system sites; series_sites: the same
 // for geometric-series iterations)
 int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* outer_sites = nullptr,
-                   int64_t* series_sites = nullptr);
+                   int64_t* series_sites = nullptr, int64_t* sap_sites = nullptr);
 // algorithmic bytes per system site of one inner iteration / outer cycle
-void solver_site_bytes(int prec, int method, double* inner, double* outer);
+// (nsap: series terms of the Schwarz preconditioner, SOLVER_SAP only)
+void solver_site_bytes(int prec, int method, double* inner, double* outer, int nsap = 0);
 // even-odd reduced solve (1 - kappa^2 H_eo H_oe) x_e = b_e on the slabs of
 // `colour` (block mode) or globally; x_e, b_e: double parity-0 views
 // `diag` replaces the 1 of the system: diag - kappa^2 H_eo H_oe (W3,eo = W2,eo + rho)
 // `method`: inner iteration, BiCGstab or the geometric series (which needs
 // the spectral radius of kappa^2 H_eo H_oe / diag below one)
-enum { SOLVER_BICGSTAB = 0, SOLVER_SERIES = 1 };
+// SOLVER_SAP (whole-lattice solves only): BiCGstab on M preconditioned by
+// one multiplicative Schwarz cycle over the red / black x0-slabs
+enum { SOLVER_BICGSTAB = 0, SOLVER_SERIES = 1, SOLVER_SAP = 2 };
+// half-lattice hopping site updates per inner iteration and even site of
+// the system: BiCGstab 4, series 2, Schwarz-preconditioned BiCGstab two
+// applications of (red and black slab solves of nsap series terms, 2 + 2
+// nsap half sweeps, and M, 2 half sweeps)
+inline int solver_hops_per_iter(int method, int nsap)
+{
+    return method == SOLVER_SERIES ? 2 : method == SOLVER_SAP ? 4 * (2 + nsap) : 4;
+}
 // `guess`: 1 if x_e holds an initial guess (its residual is computed in
 // double before the first inner cycle), 0 to start from x = 0
 int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e,

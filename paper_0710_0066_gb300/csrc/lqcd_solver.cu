@@ -29,6 +29,7 @@ namespace {
 constexpr int SBS = 256;
 constexpr int NSYS_MAX = 64;
 constexpr int NQ = 3;
+constexpr int NACC = 5;  // iteration sums kept beside the sticky status
 
 // per-system state codes in the flag arrays
 enum { F_ACTIVE = 0, F_DONE = 1, F_NAN = 2, F_MAXIT = 3 };
@@ -55,12 +56,20 @@ struct SolveArgs {
     unsigned* bar;      // one barrier counter per system, BAR_STRIDE apart
     int* status;
     int* sticky;        // first failure of any solve since the host last read it
-    unsigned long long* acc;  // [4] inner iterations, BiCGstab iterations x sites,
-                              // outer cycles x sites, series iterations x sites
+    unsigned long long* acc;  // [5] inner iterations, BiCGstab iterations x sites,
+                              // outer cycles x sites, series iterations x sites,
+                              // Schwarz-preconditioned iterations x sites
     int* iters;         // [nsys]
     double* resid;      // [nsys]
     int* outer_out;
     long long spin_limit;  // clock64 cycles of one barrier wait before LQCD_ERR_TIMEOUT
+    // Schwarz-preconditioned inner solve of the whole lattice (SOLVER_SAP):
+    // full-lattice vectors in the inner precision, [0] the even, [1] the odd
+    // parity block; fy (the inner solution) in the precision of e, whose
+    // even block it is
+    double kappa;
+    int nsap;  // geometric-series terms of every slab solve of the preconditioner
+    SpinorF fr[2], frh[2], fp[2], fv[2], fs[2], ft[2], fzp[2], fzs[2], fw1[2], fw2[2], fy[2];
 };
 
 struct SysSt {  // the CTA's own system
@@ -215,7 +224,332 @@ __device__ __forceinline__ void cdot2(float4 a, float4 b, double& re, double& im
 }
 __device__ __forceinline__ double nrm2w(float4 a) { return (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w); }
 
+template <class T>
+__device__ __forceinline__ void sp_axpy(Spinor<T>& y, T a, const Spinor<T>& x)  // y <- x + a y
+{
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) y.c[s][c] = x.c[s][c] + a * y.c[s][c];
+}
+template <class T>
+__device__ __forceinline__ void sp_zero(Spinor<T>& y)
+{
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) y.c[s][c] = mk(T(0), T(0));
+}
+
+// eo index of the t-th site of one parity in the slabs of colour c
+// (t < Vh / 2): slab 2k + c holds eo indices [(2k + c) Sh, (2k + c + 1) Sh)
+__device__ __forceinline__ int colour_site(const Geo& g, int c, int t)
+{
+    const int k = t / g.Sh;
+    return (c + 2 * k) * g.Sh + (t - k * g.Sh);
+}
+
+#define SAP_SYNC \
+    if (!sys_sync(A, sys, epoch)) return false
+#define FOR_COLOUR_SITES(c) \
+    for (int t_ = cin * SBS + (int)threadIdx.x, i = 0; t_ < A.g.Vh / 2 && ((i = colour_site(A.g, (c), t_)), true); \
+         t_ += A.cps * SBS)
+
+// z = K^-1 q, the Schwarz preconditioner of the global solve (Sec. 3, S4
+// solver): one multiplicative cycle over the x0-slabs, first the red slabs
+// (z_r = A^-1 q_r), then the black ones with the source corrected by the
+// hops from the red faces (z_b = D^-1 (q_b + kappa H_cross z_r)).  Every slab
+// solve is the even-odd reduced slab operator 1 - kappa^2 H_eo H_oe inverted
+// by nsap terms of its geometric series (the paper's block solver), so K^-1
+// is a fixed polynomial in the operators: a linear preconditioner, as
+// BiCGstab needs.  Full-lattice vectors in P; 4 nsap + 5 barriers.
 template <int P>
+__device__ bool sap_apply(const SolveArgs& A, int sys, int cin, unsigned& epoch, const SpinorF* q, const SpinorF* z)
+{
+    typedef typename Real<P>::T T;
+    const T kap = (T)A.kappa, k2 = (T)A.k2;
+    for (int c = 0; c < 2; ++c) {
+        const SpinorF* src = c == 0 ? q : A.fw2;
+        // be_e = src_e + kappa H_eo src_o on the slabs of colour c; u_0 = be
+        FOR_COLOUR_SITES(c)
+        {
+            Spinor<T> a, b;
+            hop_site<P, false>(A.g, MODE_INTRA, 0, 0, i, src[1], A.UP, a);
+            load_spinor<P, false>(src[0], i, b);
+            sp_axpy(a, kap, b);
+            store_spinor<P>(A.fw1[0], i, a);
+            store_spinor<P>(z[0], i, a);
+        }
+        SAP_SYNC;
+        for (int n = 0; n < A.nsap; ++n) {
+            // w1_o = H_oe u_e
+            FOR_COLOUR_SITES(c)
+            {
+                Spinor<T> a;
+                hop_site<P, false>(A.g, MODE_INTRA, 0, 1, i, z[0], A.UP, a);
+                store_spinor<P>(A.fw1[1], i, a);
+            }
+            SAP_SYNC;
+            // u_e = be_e + kappa^2 H_eo w1_o
+            FOR_COLOUR_SITES(c)
+            {
+                Spinor<T> a, b;
+                hop_site<P, false>(A.g, MODE_INTRA, 0, 0, i, A.fw1[1], A.UP, a);
+                load_spinor<P, false>(A.fw1[0], i, b);
+                sp_axpy(a, k2, b);
+                store_spinor<P>(z[0], i, a);
+            }
+            SAP_SYNC;
+        }
+        // z_o = src_o + kappa H_oe u_e
+        FOR_COLOUR_SITES(c)
+        {
+            Spinor<T> a, b;
+            hop_site<P, false>(A.g, MODE_INTRA, 0, 1, i, z[0], A.UP, a);
+            load_spinor<P, false>(src[1], i, b);
+            sp_axpy(a, kap, b);
+            store_spinor<P>(z[1], i, a);
+        }
+        SAP_SYNC;
+        if (c == 0) {
+            // black source: w2 = q + kappa H_cross z_r (non-zero hops only on
+            // the slab faces), both parities
+            for (int t_ = cin * SBS + (int)threadIdx.x; t_ < A.g.Vh; t_ += A.cps * SBS) {
+                const int par = t_ >= A.g.Vh / 2 ? 1 : 0;
+                const int i = colour_site(A.g, 1, t_ - par * (A.g.Vh / 2));
+                Spinor<T> a, b;
+                hop_site<P, false>(A.g, MODE_CROSS, 0, par, i, z[1 - par], A.UP, a);
+                load_spinor<P, false>(q[par], i, b);
+                sp_axpy(a, kap, b);
+                store_spinor<P>(A.fw2[par], i, a);
+            }
+            SAP_SYNC;
+        }
+    }
+    return true;
+}
+
+#define FOR_FULL_SITES \
+    for (int t_ = cin * SBS + (int)threadIdx.x; t_ < 2 * A.g.Vh; t_ += A.cps * SBS)
+
+// Schwarz-preconditioned BiCGstab (right preconditioning, K^-1 = sap_apply)
+// on the full lattice for M y = (r64 / |r64|, 0) in P: M y = (r, 0) makes
+// y_e the solution of the even-odd reduced system (1 - kappa^2 H_eo H_oe)
+// y_e = r, so the caller's double defect correction on that system is
+// unchanged (fy[0] is the caller's e).  Returns false when a barrier wait
+// gave up.
+template <int P>
+__device__ bool sap_bicgstab(const SolveArgs& A, int sys, int cin, unsigned& epoch, SysSt& S, double* red, int& rb)
+{
+    typedef typename Real<P>::T T;
+    constexpr int PE = (P == PREC64) ? PREC64 : PREC32;
+    typedef typename Real<PE>::T TE;
+    const int tid = threadIdx.x;
+    const T kap = (T)A.kappa;
+    // ---- start: r = rh = p = (r64 / |r64|, 0), y = 0
+    {
+        double q = 0.0;
+        if (S.active) {
+            const double sc = 1.0 / sqrt(S.rn2);
+            FOR_FULL_SITES
+            {
+                const int par = t_ >= A.g.Vh ? 1 : 0, i = t_ - par * A.g.Vh;
+                Spinor<T> r;
+                Spinor<TE> z;
+                sp_zero(z);
+                sp_zero(r);
+                if (par == 0) {
+                    Spinor<double> r6;
+                    load_spinor<PREC64, false>(A.r64, i, r6);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) r.c[s][c] = mk((T)(sc * r6.c[s][c].re), (T)(sc * r6.c[s][c].im));
+                }
+                store_spinor<P>(A.fr[par], i, r);
+                load_spinor<P, false>(A.fr[par], i, r);  // the stored (rounded) vector
+                store_spinor<P>(A.frh[par], i, r);
+                store_spinor<P>(A.fp[par], i, r);
+                store_spinor<PE>(A.fy[par], i, z);
+                q += nrm_acc(r);
+            }
+        }
+        reduce_put(A, q, 0.0, 0.0, 1, rb);
+        SAP_SYNC;
+        gather_own(A, sys, 1, red, rb);
+        if (tid == 0) {
+            S.rho = make_double2(red[0], 0.0);
+            S.idone = !S.active;
+            S.itc = 0;
+            const double need = 0.5 * A.tol * sqrt(S.bn2 / fmax(S.rn2, 1e-300));
+            const double it = fmax(A.inner_tol, need);
+            S.itol2 = it * it;
+        }
+        __syncthreads();
+    }
+    for (;;) {
+        if (S.idone) break;
+        // zp = K^-1 p ; v = M zp ; <rh, v>
+        if (!sap_apply<P>(A, sys, cin, epoch, A.fp, A.fzp)) return false;
+        {
+            double qr = 0.0, qi = 0.0;
+            FOR_FULL_SITES
+            {
+                const int par = t_ >= A.g.Vh ? 1 : 0, i = t_ - par * A.g.Vh;
+                Spinor<T> a, z, rh;
+                hop_site<P, false>(A.g, MODE_ALL, 0, par, i, A.fzp[1 - par], A.UP, a);
+                load_spinor<P, false>(A.fzp[par], i, z);
+                sp_axpy(a, -kap, z);
+                store_spinor<P>(A.fv[par], i, a);
+                if (P == PREC16) load_spinor<P, false>(A.fv[par], i, a);
+                load_spinor<P, false>(A.frh[par], i, rh);
+                cdot_acc(rh, a, qr, qi);
+            }
+            reduce_put(A, qr, qi, 0.0, 2, rb);
+            SAP_SYNC;
+            gather_own(A, sys, 2, red, rb);
+            if (tid == 0) {
+                const double2 d = make_double2(red[0], red[1]);
+                const double2 al = cdiv(S.rho, d);
+                if (!finite2(al) || (d.x == 0.0 && d.y == 0.0)) {
+                    S.idone = 1;
+                    S.alpha = make_double2(0.0, 0.0);
+                } else {
+                    S.alpha = al;
+                }
+            }
+            __syncthreads();
+        }
+        if (S.idone) break;
+        // s = r - alpha v
+        {
+            const cx<T> al = mk((T)S.alpha.x, (T)S.alpha.y);
+            FOR_FULL_SITES
+            {
+                const int par = t_ >= A.g.Vh ? 1 : 0, i = t_ - par * A.g.Vh;
+                Spinor<T> r, v;
+                load_spinor<P, false>(A.fr[par], i, r);
+                load_spinor<P, false>(A.fv[par], i, v);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) r.c[s][c] = r.c[s][c] - al * v.c[s][c];
+                store_spinor<P>(A.fs[par], i, r);
+            }
+            SAP_SYNC;
+        }
+        // zs = K^-1 s ; t = M zs ; <t, s>, <t, t>
+        if (!sap_apply<P>(A, sys, cin, epoch, A.fs, A.fzs)) return false;
+        {
+            double qr = 0.0, qi = 0.0, qt = 0.0;
+            FOR_FULL_SITES
+            {
+                const int par = t_ >= A.g.Vh ? 1 : 0, i = t_ - par * A.g.Vh;
+                Spinor<T> a, z, ss;
+                hop_site<P, false>(A.g, MODE_ALL, 0, par, i, A.fzs[1 - par], A.UP, a);
+                load_spinor<P, false>(A.fzs[par], i, z);
+                sp_axpy(a, -kap, z);
+                store_spinor<P>(A.ft[par], i, a);
+                if (P == PREC16) load_spinor<P, false>(A.ft[par], i, a);
+                load_spinor<P, false>(A.fs[par], i, ss);
+                cdot_acc(a, ss, qr, qi);
+                qt += nrm_acc(a);
+            }
+            reduce_put(A, qr, qi, qt, 3, rb);
+            SAP_SYNC;
+            gather_own(A, sys, 3, red, rb);
+            if (tid == 0) {
+                const double tt = red[2];
+                const double2 om = make_double2(red[0] / tt, red[1] / tt);
+                if (!(tt > 0.0) || !finite2(om)) {
+                    S.omega = make_double2(0.0, 0.0);
+                    S.idone = 2;  // keep alpha zp, stop afterwards
+                } else {
+                    S.omega = om;
+                }
+            }
+            __syncthreads();
+        }
+        // y += alpha zp + omega zs ; r = s - omega t ; <rh, r>, |r|^2
+        {
+            double qr = 0.0, qi = 0.0, qn = 0.0;
+            const cx<T> al = mk((T)S.alpha.x, (T)S.alpha.y);
+            const cx<T> om = mk((T)S.omega.x, (T)S.omega.y);
+            FOR_FULL_SITES
+            {
+                const int par = t_ >= A.g.Vh ? 1 : 0, i = t_ - par * A.g.Vh;
+                Spinor<T> zp, zs, ss, tt, rh;
+                Spinor<TE> yy;
+                load_spinor<PE, false>(A.fy[par], i, yy);
+                load_spinor<P, false>(A.fzp[par], i, zp);
+                load_spinor<P, false>(A.fzs[par], i, zs);
+                load_spinor<P, false>(A.fs[par], i, ss);
+                load_spinor<P, false>(A.ft[par], i, tt);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const cx<T> d = al * zp.c[s][c] + om * zs.c[s][c];
+                        yy.c[s][c] = yy.c[s][c] + mk((TE)d.re, (TE)d.im);
+                        ss.c[s][c] = ss.c[s][c] - om * tt.c[s][c];
+                    }
+                store_spinor<PE>(A.fy[par], i, yy);
+                store_spinor<P>(A.fr[par], i, ss);
+                if (P == PREC16) load_spinor<P, false>(A.fr[par], i, ss);
+                load_spinor<P, false>(A.frh[par], i, rh);
+                cdot_acc(rh, ss, qr, qi);
+                qn += nrm_acc(ss);
+            }
+            reduce_put(A, qr, qi, qn, 3, rb);
+            SAP_SYNC;
+            gather_own(A, sys, 3, red, rb);
+            if (tid == 0) {
+                S.it += 1;
+                S.itc += 1;
+                const double2 rn = make_double2(red[0], red[1]);
+                S.rr = red[2];
+                if (S.idone == 2 || S.itc >= A.max_inner || S.it >= A.max_iter || !(S.rr > S.itol2) ||
+                    !finite2(rn)) {
+                    S.idone = 1;
+                } else {
+                    S.beta = cmul(cdiv(rn, S.rho), cdiv(S.alpha, S.omega));
+                    if (!finite2(S.beta)) S.idone = 1;
+                    S.rho = rn;
+                }
+            }
+            if (tid == 0 && S.idone) S.idone = 1;
+            __syncthreads();
+        }
+        if (S.idone) break;
+        // p = r + beta (p - omega v)
+        {
+            const cx<T> be = mk((T)S.beta.x, (T)S.beta.y);
+            const cx<T> om = mk((T)S.omega.x, (T)S.omega.y);
+            FOR_FULL_SITES
+            {
+                const int par = t_ >= A.g.Vh ? 1 : 0, i = t_ - par * A.g.Vh;
+                Spinor<T> r, pp, v;
+                load_spinor<P, false>(A.fr[par], i, r);
+                load_spinor<P, false>(A.fp[par], i, pp);
+                load_spinor<P, false>(A.fv[par], i, v);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) r.c[s][c] = r.c[s][c] + be * (pp.c[s][c] - om * v.c[s][c]);
+                store_spinor<P>(A.fp[par], i, r);
+            }
+            SAP_SYNC;
+        }
+    }
+    SAP_SYNC;
+    return true;
+}
+
+#undef SAP_SYNC
+#undef FOR_COLOUR_SITES
+#undef FOR_FULL_SITES
+
+template <int P, bool SAP>
 __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 {
     typedef typename Real<P>::T T;
@@ -326,6 +660,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
         }
         ++outer;
 
+        if constexpr (SAP) {
+            if (!sap_bicgstab<P>(A, sys, cin, epoch, S, red, rb)) return;
+        } else {
         // ---- inner start: r = rh = p = r64 / |r64|, e = 0
         {
             double q = 0.0;
@@ -663,6 +1000,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             }
             SYNC_OR_RETURN;
         }
+        }  // inner solve (not SAP)
 
         // ---- x += |r64| e (double)
         if (S.active && WORDS) {
@@ -745,7 +1083,8 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
         if (final_flag == F_NAN) atomicCAS(A.sticky, 0, LQCD_ERR_NAN);
         if (final_flag == F_MAXIT) atomicCAS(A.sticky, 0, LQCD_ERR_NOCONVERGE);
         atomicAdd(A.acc, (unsigned long long)S.it);
-        atomicAdd(A.acc + (A.method == SOLVER_SERIES ? 3 : 1), (unsigned long long)S.it * (unsigned long long)A.nsite);
+        atomicAdd(A.acc + (A.method == SOLVER_SERIES ? 3 : A.method == SOLVER_SAP ? 4 : 1),
+                  (unsigned long long)S.it * (unsigned long long)A.nsite);
         atomicAdd(A.acc + 2, (unsigned long long)outer * (unsigned long long)A.nsite);
     }
 }
@@ -768,14 +1107,36 @@ struct Work {
     double* part = nullptr;       // [2][NQ][grid] double-buffered partial sums
     unsigned* bar = nullptr;      // [NSYS_MAX][BAR_STRIDE] barrier counters
     int* status = nullptr;
-    int* sticky = nullptr;  // int[4] then unsigned long long[4] (sticky status, iteration sums)
+    int* sticky = nullptr;  // int[4] then unsigned long long[NACC] (sticky status, iteration sums)
     int* iters = nullptr;
     double* resid = nullptr;
     int* outer = nullptr;
     int* h_status = nullptr;  // pinned mirror: status, outer, iters[NSYS_MAX]
     double* h_resid = nullptr;
     int gmax[3] = {0, 0, 0};  // co-resident CTAs per precision
+    // the Schwarz-preconditioned global solve: 11 full-lattice vectors, each
+    // sized for a double full field (allocated on first use)
+    static constexpr int NSAP = 11;
+    double2* sap[NSAP] = {nullptr};
 };
+
+// parity block `par` of a full-lattice vector in precision prec (parity 0
+// block, parity 1 block; for half storage the two scale arrays follow)
+static SpinorF full_view(double2* buf, int prec, int par, int Vh)
+{
+    SpinorF f;
+    f.N = Vh;
+    f.nrm = nullptr;
+    if (prec == PREC64) {
+        f.v = buf + (size_t)par * 12 * Vh;
+    } else if (prec == PREC32) {
+        f.v = (float4*)buf + (size_t)par * 6 * Vh;
+    } else {
+        f.v = (uint4*)buf + (size_t)par * 3 * Vh;
+        f.nrm = (float*)((uint4*)buf + (size_t)6 * Vh) + (size_t)par * Vh;
+    }
+    return f;
+}
 
 static SpinorF inner_view(double2* buf, int prec, int Vh)
 {
@@ -795,20 +1156,25 @@ int solver_init(lqcd_ctx* h)
     for (int k = 0; k < 8; ++k) LQ_CUDA(h, cudaMalloc(&w->vec[k], sizeof(double2) * 12 * (size_t)Vh));
     LQ_CUDA(h, cudaMalloc(&w->r64, sizeof(double2) * 12 * (size_t)Vh));
     LQ_CUDA(h, cudaMalloc(&w->t64, sizeof(double2) * 12 * (size_t)Vh));
-    int occ[3];
-    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_solve<PREC64>, SBS, 0));
-    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_solve<PREC32>, SBS, 0));
-    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_solve<PREC16>, SBS, 0));
+    // co-resident CTAs of a cooperative launch: the smaller occupancy of the
+    // two variants of each precision
+    int occ[3], occs[3];
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_solve<PREC64, false>, SBS, 0));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_solve<PREC32, false>, SBS, 0));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_solve<PREC16, false>, SBS, 0));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[0], k_solve<PREC64, true>, SBS, 0));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[1], k_solve<PREC32, true>, SBS, 0));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[2], k_solve<PREC16, true>, SBS, 0));
     int gm = 0;
     for (int k = 0; k < 3; ++k) {
-        w->gmax[k] = std::max(1, occ[k]) * h->num_sms;
+        w->gmax[k] = std::max(1, std::min(occ[k], occs[k])) * h->num_sms;
         gm = std::max(gm, w->gmax[k]);
     }
     LQ_CUDA(h, cudaMalloc(&w->part, sizeof(double) * 2 * NQ * (size_t)gm));
     LQ_CUDA(h, cudaMalloc(&w->bar, sizeof(unsigned) * BAR_STRIDE * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->status, sizeof(int) * 4));
-    LQ_CUDA(h, cudaMalloc(&w->sticky, sizeof(int) * 4 + sizeof(unsigned long long) * 4));
-    LQ_CUDA(h, cudaMemset(w->sticky, 0, sizeof(int) * 4 + sizeof(unsigned long long) * 4));
+    LQ_CUDA(h, cudaMalloc(&w->sticky, sizeof(int) * 4 + sizeof(unsigned long long) * NACC));
+    LQ_CUDA(h, cudaMemset(w->sticky, 0, sizeof(int) * 4 + sizeof(unsigned long long) * NACC));
     LQ_CUDA(h, cudaMalloc(&w->iters, sizeof(int) * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->resid, sizeof(double) * NSYS_MAX));
     LQ_CUDA(h, cudaMalloc(&w->outer, sizeof(int) * 4));
@@ -820,11 +1186,11 @@ int solver_init(lqcd_ctx* h)
 // reads and clears the sticky status and the iteration sums of the solves
 // run since the last call (synchronises the stream)
 int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* outer_sites,
-                   int64_t* series_sites)
+                   int64_t* series_sites, int64_t* sap_sites)
 {
     Work* w = h->work;
     int hs[4];
-    unsigned long long acc[4];
+    unsigned long long acc[NACC];
     LQ_CUDA(h, cudaMemcpyAsync(hs, w->sticky, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
     LQ_CUDA(h, cudaMemcpyAsync(acc, w->sticky + 4, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
     LQ_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -833,6 +1199,7 @@ int solver_collect(lqcd_ctx* h, int64_t* iters, int64_t* site_iters, int64_t* ou
     if (site_iters) *site_iters = (int64_t)acc[1];
     if (outer_sites) *outer_sites = (int64_t)acc[2];
     if (series_sites) *series_sites = (int64_t)acc[3];
+    if (sap_sites) *sap_sites = (int64_t)acc[4];
     if (hs[0] != 0) {
         h->err = hs[0] == LQCD_ERR_TIMEOUT ? "solver: grid barrier wait timed out"
                  : hs[0] == LQCD_ERR_NAN   ? "solver: non-finite residual"
@@ -849,6 +1216,7 @@ void solver_free(lqcd_ctx* h)
     for (int k = 0; k < 8; ++k) cudaFree(w->vec[k]);
     cudaFree(w->r64);
     cudaFree(w->t64);
+    for (int k = 0; k < Work::NSAP; ++k) cudaFree(w->sap[k]);
     cudaFree(w->part);
     cudaFree(w->bar);
     cudaFree(w->status);
@@ -864,14 +1232,22 @@ void solver_free(lqcd_ctx* h)
 
 // algorithmic DRAM bytes per system site: one inner iteration and one outer
 // cycle (each vector and the eight links moved once per phase)
-void solver_site_bytes(int prec, int method, double* inner, double* outer)
+void solver_site_bytes(int prec, int method, double* inner, double* outer, int nsap)
 {
     const double sp = prec == PREC64 ? 192.0 : prec == PREC32 ? 96.0 : 52.0;
     const double lk = prec == PREC64 ? 1152.0 : prec == PREC32 ? 384.0 : 192.0;
     const double se = prec == PREC64 ? 192.0 : 96.0;
     // BiCGstab: 24 spinor passes, 4 half sweeps of links, solution r/w;
-    // series: p, tmp, tmp, r, p, p (6 passes), 2 half sweeps of links
-    *inner = method == SOLVER_SERIES ? 6.0 * sp + 2.0 * lk : 24.0 * sp + 4.0 * lk + 2.0 * se;
+    // series: p, tmp, tmp, r, p, p (6 passes), 2 half sweeps of links;
+    // Schwarz-preconditioned BiCGstab (per even site of the lattice, nsap
+    // series terms): two preconditioner applications of (17 + 5 nsap)
+    // spinor passes and (4 + 2 nsap) half sweeps of links each (slab solves
+    // of both colours, the face update, the Wilson matrix), plus 28 passes
+    // of vector updates and the solution r/w of both parities
+    if (method == SOLVER_SAP)
+        *inner = 2.0 * (17.0 + 5.0 * nsap) * sp + 28.0 * sp + 2.0 * (4.0 + 2.0 * nsap) * lk + 4.0 * se;
+    else
+        *inner = method == SOLVER_SERIES ? 6.0 * sp + 2.0 * lk : 24.0 * sp + 4.0 * lk + 2.0 * se;
     *outer = (192.0 + 3.0 * sp + se) + (2.0 * 192.0 + se) + (2.0 * 192.0 + 1152.0) + (4.0 * 192.0 + 1152.0);
 }
 
@@ -887,6 +1263,13 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.diag = diag;
     A.method = method;
     A.guess = guess;
+    A.kappa = kappa;
+    const bool sap = method == SOLVER_SAP;
+    if (sap && (mode != MODE_ALL || diag != 1.0)) {
+        h->err = "the Schwarz-preconditioned solve is a whole-lattice solve of M";
+        return LQCD_ERR_ARG;
+    }
+    A.nsap = h->sap_terms;
     if (mode == MODE_INTRA) {
         A.nsys = colour < 0 ? g.nb : g.nb / 2;
         A.slab0 = colour < 0 ? 0 : colour;
@@ -920,6 +1303,16 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.t = inner_view(w->vec[5], prec, g.Vh);
     A.tmp = inner_view(w->vec[6], prec, g.Vh);
     A.e = inner_view(w->vec[7], prec == PREC64 ? PREC64 : PREC32, g.Vh);
+    if (sap) {
+        for (int k = 0; k < Work::NSAP; ++k)
+            if (!w->sap[k]) LQ_CUDA(h, cudaMalloc(&w->sap[k], sizeof(double2) * 24 * (size_t)g.Vh));
+        SpinorF* fv[Work::NSAP] = {A.fr, A.frh, A.fp, A.fv, A.fs, A.ft, A.fzp, A.fzs, A.fw1, A.fw2, A.fy};
+        for (int k = 0; k < Work::NSAP; ++k)
+            for (int par = 0; par < 2; ++par)
+                fv[k][par] = full_view(w->sap[k], k == Work::NSAP - 1 ? (prec == PREC64 ? PREC64 : PREC32) : prec,
+                                       par, g.Vh);
+        A.e = A.fy[0];  // the inner solution's even block
+    }
     A.tol = tol;
     A.inner_tol = prec == PREC64 ? 0.0 : prec == PREC32 ? 1e-5 : 2e-3;
     A.max_iter = max_iter;
@@ -937,9 +1330,9 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     LQ_CUDA(h, cudaMemsetAsync(w->bar, 0, sizeof(unsigned) * BAR_STRIDE * A.nsys, h->stream));
     LQ_CUDA(h, cudaMemsetAsync(w->status, 0, sizeof(int) * 4, h->stream));
     void* args[] = {&A};
-    const void* fn = prec == PREC64 ? (const void*)k_solve<PREC64>
-                     : prec == PREC32 ? (const void*)k_solve<PREC32>
-                                      : (const void*)k_solve<PREC16>;
+    const void* fn = prec == PREC64 ? (sap ? (const void*)k_solve<PREC64, true> : (const void*)k_solve<PREC64, false>)
+                     : prec == PREC32 ? (sap ? (const void*)k_solve<PREC32, true> : (const void*)k_solve<PREC32, false>)
+                                      : (sap ? (const void*)k_solve<PREC16, true> : (const void*)k_solve<PREC16, false>);
     cudaEvent_t ev;
     prof_begin(h, 1, &ev);
     // cooperative launch (every CTA resident), expressed as a launch
@@ -971,7 +1364,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     const int st = w->h_status[0];
     const int nouter = w->h_status[1];
     double bi, bo;
-    solver_site_bytes(prec, method, &bi, &bo);
+    solver_site_bytes(prec, method, &bi, &bo, A.nsap);
     int64_t itsum = 0;
     for (int s = 0; s < A.nsys; ++s) {
         itsum += w->h_status[4 + s];
@@ -982,7 +1375,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
         h->prof.recs[rec - 1].bytes = (double)A.nsite * ((double)itsum * bi + (double)nouter * A.nsys * bo);
     h->iter_count += itsum;
     h->site_iters += itsum * (int64_t)A.nsite;
-    h->hop_sites += itsum * (int64_t)A.nsite * (method == SOLVER_SERIES ? 2 : 4);
+    h->hop_sites += itsum * (int64_t)A.nsite * solver_hops_per_iter(method, A.nsap);
     if (st == LQCD_ERR_TIMEOUT) {
         h->err = "solver: grid barrier wait timed out";
         return LQCD_ERR_TIMEOUT;

@@ -25,7 +25,7 @@ SCHUR_R, SCHUR_RDAG, SCHUR_RINV, SCHUR_RINVDAG = 0, 1, 2, 3
 SCHUR2_R, SCHUR2_RDAG, SCHUR2_RINV, SCHUR2_RINVDAG = 4, 5, 6, 7
 TERM_W1, TERM_SCHUR, TERM_W2, TERM_SCHUR2, TERM_S2, TERM_S1 = 0, 1, 2, 3, 4, 5
 EO_APPLY, EO_SOLVE = 0, 1
-SOLVER_BICGSTAB, SOLVER_SERIES = 0, 1
+SOLVER_BICGSTAB, SOLVER_SERIES, SOLVER_SAP = 0, 1, 2
 MAX_LEVELS = 5
 LF, SW = 0, 1
 KERNEL_HOP, KERNEL_SOLVER, KERNEL_FORCE, KERNEL_GAUGE, KERNEL_BLAS = 0, 1, 2, 3, 4
@@ -39,6 +39,7 @@ EXPORTS = [
     "lqcd_gauge_action_static", "lqcd_force_profile", "lqcd_set_subslabs", "lqcd_subblock_dslash",
     "lqcd_subblock_solve_batched", "lqcd_subblock_eo", "lqcd_pf_force_eo", "lqcd_link_update",
     "lqcd_autotune", "lqcd_tune_read", "lqcd_profile_times", "lqcd_set_wait_limit",
+    "lqcd_set_global_solver",
 ]
 
 
@@ -135,6 +136,7 @@ def load():
         "lqcd_gauge_action_static": [C.POINTER(C.c_int * 4), vp, d, vp, vp],
         "lqcd_force_profile": [vp, vp, vp],
         "lqcd_set_wait_limit": [vp, i64],
+        "lqcd_set_global_solver": [vp, i, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -239,6 +241,10 @@ def lqcd_tune_read(h):
     return {"hop_block_size": dict(zip(("f64", "f32", "f16"), v[0:3])),
             "slab_solve_sites_per_thread": dict(zip(("f64", "f32", "f16"), v[3:6])),
             "global_solve_sites_per_thread": dict(zip(("f64", "f32", "f16"), v[6:9]))}
+
+
+def lqcd_set_global_solver(h, method, sap_terms=4):
+    return _check(h, load().lqcd_set_global_solver(h, int(method), int(sap_terms)))
 
 
 def lqcd_set_wait_limit(h, cycles):
