@@ -422,7 +422,11 @@ int lqcd_tune_read(lqcd_t h, int* out);
  *     reduced correction y_e.  The series needs the slab operator's
  *     spectral radius below one to precondition well (it always gives a
  *     valid, if weaker, preconditioner).
- * Errors: LQCD_ERR_ARG (other methods, sap_terms out of range).  Host only. */
+ * Selecting LQCD_SOLVER_SAP allocates its workspace (11 full-lattice
+ * vectors, 2.1 KB per lattice site) on the current device; it is kept
+ * until lqcd_destroy.
+ * Errors: LQCD_ERR_ARG (other methods, sap_terms out of range),
+ * LQCD_ERR_CUDA (allocation). */
 int lqcd_set_global_solver(lqcd_t h, int method, int sap_terms);
 
 /* Limit of one barrier wait inside the persistent solver, in GPU clock

@@ -1658,6 +1658,7 @@ int lqcd_set_global_solver(lqcd_t h, int method, int sap_terms)
         h->err = "global solver: 0 <= sap_terms <= 64";
         return LQCD_ERR_ARG;
     }
+    if (method == LQCD_SOLVER_SAP) LQ_TRY(solver_sap_alloc(h));
     h->global_method = method == LQCD_SOLVER_SAP ? SOLVER_SAP : SOLVER_BICGSTAB;
     if (method == LQCD_SOLVER_SAP) h->sap_terms = sap_terms;
     return LQCD_OK;

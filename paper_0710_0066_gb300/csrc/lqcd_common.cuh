@@ -854,6 +854,9 @@ int hop_sweep(lqcd_ctx* h, int prec, int mode, int dag, int pout, int colour, Sp
 
 // solver.cu
 int solver_init(lqcd_ctx* h);
+// the Schwarz-preconditioned solve's workspace (11 full-lattice vectors),
+// allocated once, outside any graph capture
+int solver_sap_alloc(lqcd_ctx* h);
 void solver_free(lqcd_ctx* h);
 // sticky status and iteration sums of the solves since the last call
 // (site_iters: BiCGstab iterations x system sites; series_sites: the same

@@ -1251,6 +1251,20 @@ void solver_site_bytes(int prec, int method, double* inner, double* outer, int n
     *outer = (192.0 + 3.0 * sp + se) + (2.0 * 192.0 + se) + (2.0 * 192.0 + 1152.0) + (4.0 * 192.0 + 1152.0);
 }
 
+int solver_sap_alloc(lqcd_ctx* h)
+{
+    Work* w = h->work;
+    for (int k = 0; k < Work::NSAP; ++k)
+        if (!w->sap[k]) {
+            if (h->capturing) {
+                h->err = "the Schwarz-preconditioned solve's workspace must exist before a graph is recorded";
+                return LQCD_ERR_STATE;
+            }
+            LQ_CUDA(h, cudaMalloc(&w->sap[k], sizeof(double2) * 24 * (size_t)h->g.Vh));
+        }
+    return LQCD_OK;
+}
+
 int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e, const double2* b_e,
              double tol, int max_iter, int* iters_sys, double* resid_sys, double diag, int method, int guess)
 {
@@ -1304,8 +1318,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.tmp = inner_view(w->vec[6], prec, g.Vh);
     A.e = inner_view(w->vec[7], prec == PREC64 ? PREC64 : PREC32, g.Vh);
     if (sap) {
-        for (int k = 0; k < Work::NSAP; ++k)
-            if (!w->sap[k]) LQ_CUDA(h, cudaMalloc(&w->sap[k], sizeof(double2) * 24 * (size_t)g.Vh));
+        LQ_TRY(solver_sap_alloc(h));
         SpinorF* fv[Work::NSAP] = {A.fr, A.frh, A.fp, A.fv, A.fs, A.ft, A.fzp, A.fzs, A.fw1, A.fw2, A.fy};
         for (int k = 0; k < Work::NSAP; ++k)
             for (int par = 0; par < 2; ++par)
