@@ -303,7 +303,7 @@ def run_ours(args):
         return lqcd.hmc_params(WL["beta"], WL["kappa"], WL["tau"], WL["nlevels"], WL["scheme"], WL["nsteps"],
                                WL["level_gauge"], WL["level_w1"], WL["level_schur"], lam=WL["lam"], roll=1,
                                metropolis=1, precision=prec, tol=WL["tol"], max_iter=WL["max_iter"],
-                               use_graph=0 if args.no_graph else 1, chrono=0 if args.no_chrono else 1,
+                               use_graph=0 if args.no_graph else 1, chrono=0 if args.no_chrono else args.chrono,
                                block_solver=lqcd.SOLVER_SERIES if args.block_solver == "series"
                                else lqcd.SOLVER_BICGSTAB)
 
@@ -363,6 +363,7 @@ def run_ours(args):
     clk = clocks.stop()
     launches = lqcd.lqcd_launch_count(lat.h) - l0_launch
     n_sol, ms_sol, by_sol = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
+    sol_ms = lqcd.lqcd_profile_times(lat.h, lqcd.KERNEL_SOLVER)[:max(1, n_sol // max(1, args.steps))]
     lqcd.lqcd_profile_enable(lat.h, 0)
     total_ms, value = job_time(sum(step_ms), args.steps, dist, "cuda")
 
@@ -481,7 +482,7 @@ def run_ours(args):
                    "inner_precision": args.precision, "l2": "flushed between timed trajectories",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "md_as_cuda_graph": not args.no_graph, "w1_block_solver": block_solver,
-                   "chronological_guesses": not args.no_chrono,
+                   "chronological_guesses": 0 if args.no_chrono else args.chrono,
                    "global_solver": ("Schwarz-preconditioned BiCGstab, %d series terms per slab solve"
                                      % args.sap_terms) if args.global_solver == "sap"
                                     else "even-odd BiCGstab",
@@ -516,7 +517,8 @@ def run_ours(args):
                        "plaq": [r.plaq for r in results], "dH": [r.dH for r in results],
                        "accepted": [r.accepted for r in results], "plaq_dynamical_thermalisation": plaq_dyn,
                        "pure_gauge_plaq": rth.plaq if rth else None, "autotune": tune,
-                       "solver_traffic": traffic_detail, "fp64": fp64, "e2e_ms": e2e_ms}, f)
+                       "solver_traffic": traffic_detail, "fp64": fp64, "e2e_ms": e2e_ms,
+                       "solver_launch_ms_one_trajectory": sol_ms}, f)
     if rank == 0:
         print(json.dumps(line), flush=True)
     lat.close()
@@ -663,7 +665,7 @@ def run_iterated(args, W=WL_ITER):
         "config": {"lattice": "x".join(map(str, L)), "l0": W["l0"], "l0s": W["l0s"], "kappa": W["kappa"],
                    "beta": W["beta"], "nsteps": W["nsteps"], "levels": W["levels"], "rho": W.get("rho"),
                    "step_scheme": W.get("step_scheme", 0), "scheme": W["scheme"], "eo_solver": args.eo_solver,
-                   "chronological_guesses": not args.no_chrono,
+                   "chronological_guesses": 0 if args.no_chrono else args.chrono,
                    "thermalisation": "%d pure-gauge trajectories from exp(i %.1f H)" % (W["therm"], W["eps"]),
                    "autotune": tune,
                    "l2": "flushed between timed trajectories"},
@@ -810,6 +812,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--chrono", type=int, default=1, choices=[1, 2],
+                    help="order of the chronological guesses: 1 linear (two solutions), 2 quadratic (three)")
     ap.add_argument("--no-chrono", action="store_true",
                     help="start every force solve from zero instead of the previous solution of its term")
     ap.add_argument("--no-graph", action="store_true",

@@ -325,11 +325,13 @@ typedef struct {
                            extrapolation in MD time of its solutions at the
                            two previous force evaluations of its term (one
                            kept: that one; the first solve of a trajectory
-                           starts from zero).  The solves still run to tol,
+                           starts from zero); 2: the quadratic extrapolation
+                           through the three previous solutions (fewer kept:
+                           the lower orders).  The solves still run to tol,
                            so the forces agree with chrono = 0 to the solver
                            tolerance, and reversibility holds to it.  Needs
-                           24 extra even-site double fields on the device
-                           (allocated on first use). */
+                           12 (chrono + 1) extra even-site double fields on
+                           the device (allocated on first use). */
 } lqcd_hmc_params;
 
 /* Pseudo-fermion fields of lqcd_md (device pointers, NULL where the term

@@ -61,39 +61,51 @@ int hop_full(lqcd_ctx* h, int mode, int dag, int colour, double2* out, const dou
 }
 
 // Chronological initial guess of slot k for a solve on the links at MD
-// time h->md_time (even half of x): nothing kept, zero (*guess = 0); one
-// solution, that solution; two, their linear extrapolation in MD time
-// (Brower, Ivanenko, Levi, Orginos, Nucl. Phys. B 484 (1997) 353: the
-// chronological inverter with two vectors).  dag: the unknown of the
-// adjoint system is gamma5 x.
+// time h->md_time (even half of x): the Lagrange extrapolation in MD time of
+// the solutions kept (Brower, Ivanenko, Levi, Orginos, Nucl. Phys. B 484
+// (1997) 353: the chronological inverter): nothing kept, zero (*guess = 0);
+// one, that solution; two, the straight line through them; three (chrono =
+// 2), the parabola.  Solutions at coinciding times drop to the lower
+// order.  dag: the unknown of the adjoint system is gamma5 x.
 int chrono_guess(lqcd_ctx* h, int k, double2* x, int dag, int* guess)
 {
+    constexpr int D = lqcd_ctx::CHRONO_MAX;
     *guess = 0;
-    if (k < 0 || !h->chrono_buf[2 * k] || h->chrono_n[k] == 0) return LQCD_OK;
-    const double2* x1 = h->chrono_buf[2 * k + h->chrono_cur[k]];
-    const double2* x0 = h->chrono_buf[2 * k + 1 - h->chrono_cur[k]];
-    const double t0 = h->chrono_t[k][0], t1 = h->chrono_t[k][1];
-    double a = 1.0, b = 0.0;
-    if (h->chrono_n[k] == 2 && t1 != t0) {
-        const double s = (h->md_time - t1) / (t1 - t0);
-        a = 1.0 + s;
-        b = -s;
+    if (k < 0 || !h->chrono_buf[D * k] || h->chrono_n[k] == 0) return LQCD_OK;
+    const int depth = h->chrono_depth;
+    // newest first: buffers cur, cur - 1, cur - 2 (mod depth)
+    const int j2 = h->chrono_cur[k], j1 = (j2 + depth - 1) % depth, j0 = (j2 + depth - 2) % depth;
+    const double t = h->md_time, t2 = h->chrono_t[k][j2], t1 = h->chrono_t[k][j1], t0 = h->chrono_t[k][j0];
+    const double2 *x2 = h->chrono_buf[D * k + j2], *x1 = h->chrono_buf[D * k + j1], *x0 = h->chrono_buf[D * k + j0];
+    int n = h->chrono_n[k];
+    if (n >= 2 && t1 == t2) n = 1;
+    if (n >= 3 && (t0 == t1 || t0 == t2)) n = 2;
+    if (n == 3) {
+        const double w2 = (t - t0) * (t - t1) / ((t2 - t0) * (t2 - t1));
+        const double w1 = (t - t0) * (t - t2) / ((t1 - t0) * (t1 - t2));
+        const double w0 = (t - t1) * (t - t2) / ((t0 - t1) * (t0 - t2));
+        LQ_TRY(lincomb3_even(h, x, w2, x2, w1, x1, w0, x0, dag));
+    } else if (n == 2) {
+        const double s = (t - t2) / (t2 - t1);
+        LQ_TRY(lincomb_even(h, x, 1.0 + s, x2, -s, x1, dag));
+    } else {
+        LQ_TRY(lincomb_even(h, x, 1.0, x2, 0.0, x2, dag));
     }
-    LQ_TRY(lincomb_even(h, x, a, x1, b, x0, dag));
     *guess = 1;
     return LQCD_OK;
 }
 
-// keep the even half of the solution x of slot k (the older one is dropped)
+// keep the even half of the solution x of slot k (the oldest one is dropped)
 int chrono_store(lqcd_ctx* h, int k, const double2* x)
 {
-    if (k < 0 || !h->chrono_buf[2 * k] || h->chrono_frozen) return LQCD_OK;
-    h->chrono_cur[k] ^= 1;
-    LQ_CUDA(h, cudaMemcpyAsync(h->chrono_buf[2 * k + h->chrono_cur[k]], x, sizeof(double2) * 12 * (size_t)h->g.Vh,
+    constexpr int D = lqcd_ctx::CHRONO_MAX;
+    if (k < 0 || !h->chrono_buf[D * k] || h->chrono_frozen) return LQCD_OK;
+    const int depth = h->chrono_depth;
+    h->chrono_cur[k] = (h->chrono_cur[k] + 1) % depth;
+    LQ_CUDA(h, cudaMemcpyAsync(h->chrono_buf[D * k + h->chrono_cur[k]], x, sizeof(double2) * 12 * (size_t)h->g.Vh,
                                cudaMemcpyDeviceToDevice, h->stream));
-    h->chrono_t[k][0] = h->chrono_t[k][1];
-    h->chrono_t[k][1] = h->md_time;
-    h->chrono_n[k] = h->chrono_n[k] < 2 ? h->chrono_n[k] + 1 : 2;
+    h->chrono_t[k][h->chrono_cur[k]] = h->md_time;
+    h->chrono_n[k] = h->chrono_n[k] < depth ? h->chrono_n[k] + 1 : depth;
     return LQCD_OK;
 }
 
@@ -427,17 +439,20 @@ void build_step(const lqcd_hmc_params& p, int j, double dt, std::vector<Op>& v)
     }
 }
 
-// the chronological slots of the force solves (two even-half double fields
-// each), allocated before any capture
+// the chronological slots of the force solves (chrono + 1 even-half double
+// fields each), allocated before any capture
 int chrono_alloc(lqcd_ctx* h, const lqcd_hmc_params* p)
 {
     if (!p->chrono) return LQCD_OK;
+    constexpr int D = lqcd_ctx::CHRONO_MAX;
     const size_t bytes = sizeof(double2) * 12 * (size_t)h->g.Vh;
-    for (int k = 0; k < 2 * lqcd_ctx::NCHRONO; ++k) {
-        if (h->chrono_buf[k]) continue;
-        LQ_CUDA(h, cudaMalloc(&h->chrono_buf[k], bytes));
-        LQ_CUDA(h, cudaMemsetAsync(h->chrono_buf[k], 0, bytes, h->stream));
-    }
+    for (int k = 0; k < lqcd_ctx::NCHRONO; ++k)
+        for (int j = 0; j < p->chrono + 1; ++j) {
+            double2*& b = h->chrono_buf[D * k + j];
+            if (b) continue;
+            LQ_CUDA(h, cudaMalloc(&b, bytes));
+            LQ_CUDA(h, cudaMemsetAsync(b, 0, bytes, h->stream));
+        }
     return LQCD_OK;
 }
 
@@ -472,8 +487,8 @@ int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
         h->err = "hmc params: use_graph must be 0 or 1";
         return LQCD_ERR_ARG;
     }
-    if (p->chrono != 0 && p->chrono != 1) {
-        h->err = "hmc params: chrono must be 0 or 1";
+    if (p->chrono < 0 || p->chrono > 2) {
+        h->err = "hmc params: chrono must be 0, 1 or 2";
         return LQCD_ERR_ARG;
     }
     if ((p->eo_solver != LQCD_SOLVER_BICGSTAB && p->eo_solver != LQCD_SOLVER_SERIES) ||
@@ -551,6 +566,7 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
     const SolveCfg cs2{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 8 : -1};
     const SolveCfg cs1{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 10 : -1};
     for (int k = 0; k < lqcd_ctx::NCHRONO; ++k) h->chrono_n[k] = h->chrono_cur[k] = 0;
+    h->chrono_depth = p.chrono + 1;
     h->md_time = 0.0;
     for (const Op& o : ops) {
         if (o.kind == 1) {

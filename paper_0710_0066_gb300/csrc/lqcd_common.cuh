@@ -755,14 +755,16 @@ struct lqcd_ctx {
     std::vector<unsigned char> md_key;  // parameters the graph was recorded for
     int64_t md_launches = 0;            // kernels per replay
     // chronological initial guesses of the MD's solves: per solve site of
-    // the force terms the even halves of its last two solutions (buffers
-    // 2k, 2k + 1; chrono_cur[k] names the newer) and the MD times of the
-    // links they were solved on
+    // the force terms the even halves of its last chrono_depth solutions
+    // (buffers CHRONO_MAX k + j, a ring; chrono_cur[k] names the newest)
+    // and the MD times of the links each buffer's solution was solved on
     static constexpr int NCHRONO = 12;
-    double2* chrono_buf[2 * NCHRONO] = {};
-    int chrono_n[NCHRONO] = {};    // solutions kept (0, 1, 2)
+    static constexpr int CHRONO_MAX = 3;
+    double2* chrono_buf[CHRONO_MAX * NCHRONO] = {};
+    int chrono_n[NCHRONO] = {};    // solutions kept (0 .. chrono_depth)
     int chrono_cur[NCHRONO] = {};
-    double chrono_t[NCHRONO][2] = {};  // [older, newer]
+    double chrono_t[NCHRONO][CHRONO_MAX] = {};  // MD time of each buffer
+    int chrono_depth = 2;                        // solutions the guess uses (chrono + 1)
     double md_time = 0.0;              // MD time of the links in do_md
     bool chrono_frozen = false;        // guesses are read but not replaced
     int md_nforce = 0;                  // force evaluations per replay
@@ -839,6 +841,9 @@ int axpby_full(lqcd_ctx* h, double2* y, double a, const double2* x, double b, in
 int gamma5_full(lqcd_ctx* h, double2* y, const double2* x);
 // even half: y = gamma5^g5 (a x1 + b x0); x0 not read when b = 0
 int lincomb_even(lqcd_ctx* h, double2* y, double a, const double2* x1, double b, const double2* x0, int g5);
+// even half: y = gamma5^g5 (a x2 + b x1 + c x0)
+int lincomb3_even(lqcd_ctx* h, double2* y, double a, const double2* x2, double b, const double2* x1, double c,
+                  const double2* x0, int g5);
 int keep_colour(lqcd_ctx* h, double2* y, int colour);
 int norm2_dev(lqcd_ctx* h, const double* x, int64_t n, double* dev_out);
 int rng_normals(lqcd_ctx* h, double* out, int64_t n, uint64_t seed, uint32_t stream, uint32_t traj,

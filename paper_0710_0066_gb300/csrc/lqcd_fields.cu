@@ -257,6 +257,16 @@ __global__ void k_lincomb_even(double2* y, double a, const double2* x1, double b
     y[t] = make_double2(s * (a * u.x + b * v.x), s * (a * u.y + b * v.y));
 }
 
+__global__ void k_lincomb3_even(double2* y, double a, const double2* x2, double b, const double2* x1, double c,
+                                const double2* x0, int Vh, int g5)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)12 * Vh) return;
+    const double s = (g5 && (int)(t / Vh) >= 6) ? -1.0 : 1.0;  // spins 2, 3
+    const double2 u = x2[t], v = x1[t], w = x0[t];
+    y[t] = make_double2(s * (a * u.x + b * v.x + c * w.x), s * (a * u.y + b * v.y + c * w.y));
+}
+
 // ---------------------------------------------------------------------------
 // deterministic two-stage sums of squares
 // ---------------------------------------------------------------------------
@@ -479,6 +489,14 @@ int gamma5_full(lqcd_ctx* h, double2* y, const double2* x)
 int lincomb_even(lqcd_ctx* h, double2* y, double a, const double2* x1, double b, const double2* x0, int g5)
 {
     k_lincomb_even<<<nblk((int64_t)12 * h->g.Vh), BS, 0, h->stream>>>(y, a, x1, b, x0, h->g.Vh, g5);
+    LAUNCH_CHECK(h);
+    return LQCD_OK;
+}
+
+int lincomb3_even(lqcd_ctx* h, double2* y, double a, const double2* x2, double b, const double2* x1, double c,
+                  const double2* x0, int g5)
+{
+    k_lincomb3_even<<<nblk((int64_t)12 * h->g.Vh), BS, 0, h->stream>>>(y, a, x2, b, x1, c, x0, h->g.Vh, g5);
     LAUNCH_CHECK(h);
     return LQCD_OK;
 }

@@ -724,10 +724,13 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             // ---- geometric series (Sec. 3, the solver of the block terms):
             // p <- (r + k2 H_eo H_oe p) / diag from p = r; before an update
             // the inner residual is r - A p = diag (p_new - p).  Two
-            // barriers per iteration.
+            // barriers per iteration; the residual is reduced every second
+            // iteration only (and at the iteration limits), which costs at
+            // most one extra iteration per inner solve.
             const T k2 = (T)A.k2, dinv = (T)(1.0 / A.diag);
             for (;;) {
                 if (S.idone) break;
+                const bool chk = (S.itc & 1) || S.itc + 1 >= A.max_inner || S.it + 1 >= A.max_iter;
                 FOR_SITES
                 {
                     const int i = base + j_;
@@ -749,13 +752,24 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 #pragma unroll
                             for (int c = 0; c < 3; ++c) a.c[s][c] = dinv * (rr.c[s][c] + k2 * a.c[s][c]);
                         store_spinor<P>(A.p, i, a);
-                        if (P == PREC16) load_spinor<P, false>(A.p, i, a);
+                        if (chk) {
+                            if (P == PREC16) load_spinor<P, false>(A.p, i, a);
 #pragma unroll
-                        for (int s = 0; s < 4; ++s)
+                            for (int s = 0; s < 4; ++s)
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) pp.c[s][c] = a.c[s][c] - pp.c[s][c];
-                        q += nrm_acc(pp);
+                                for (int c = 0; c < 3; ++c) pp.c[s][c] = a.c[s][c] - pp.c[s][c];
+                            q += nrm_acc(pp);
+                        }
                     }
+                if (!chk) {
+                    SYNC_OR_RETURN;
+                    if (tid == 0) {
+                        S.it += 1;
+                        S.itc += 1;
+                    }
+                    __syncthreads();
+                    continue;
+                }
                 reduce_put(A, q, 0.0, 0.0, 1, rb);
                 SYNC_OR_RETURN;
                 gather_own(A, sys, 1, red, rb);

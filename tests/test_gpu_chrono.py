@@ -1,7 +1,8 @@
 """Chronological initial guesses of the molecular-dynamics force solves
-(lqcd_hmc_params.chrono): each solve starts from the linear extrapolation
-in MD time of its solutions at the two previous force evaluations of its
-term (Brower et al.'s chronological inverter).  The solves still run
+(lqcd_hmc_params.chrono): each solve starts from the linear (chrono = 1)
+or quadratic (chrono = 2) extrapolation in MD time of its solutions at the
+two or three previous force evaluations of its term (Brower et al.'s
+chronological inverter).  The solves still run
 to the requested residual, so trajectories agree with the FP64 oracle (which
 always starts from zero) to the tolerances of the other trajectory tests;
 a solve whose guess already meets the residual takes no iteration; the
@@ -87,16 +88,19 @@ def test_repeated_solves_take_no_iterations(case):
     lat.close()
 
 
-@pytest.mark.parametrize("case,method", [("two_part", lqcd.SOLVER_BICGSTAB), ("four_part", lqcd.SOLVER_BICGSTAB),
-                                         ("four_part", lqcd.SOLVER_SERIES)])
-def test_chrono_trajectory_matches_oracle(case, method):
+@pytest.mark.parametrize("case,method,chrono", [("two_part", lqcd.SOLVER_BICGSTAB, 1),
+                                                ("four_part", lqcd.SOLVER_BICGSTAB, 1),
+                                                ("four_part", lqcd.SOLVER_SERIES, 1),
+                                                ("two_part", lqcd.SOLVER_BICGSTAB, 2),
+                                                ("four_part", lqcd.SOLVER_SERIES, 2)])
+def test_chrono_trajectory_matches_oracle(case, method, chrono):
     """the mixed-precision trajectory with chronological guesses against
     the oracle's, which solves every system from zero"""
     L, l0 = (8, 4, 4, 4), 4
     Un = syn.random_links(L, 0.3, 51)
     lat = lqcd.Lattice(L, l0, -1, l0s=2)
     olat = O.Lattice(L, l0, -1, l0s=2)
-    U1, res = lat.hmc_trajectory(cuda(Un), _prm(case, 0.4, 3, 1, method=method), 2011, 6)
+    U1, res = lat.hmc_trajectory(cuda(Un), _prm(case, 0.4, 3, chrono, method=method), 2011, 6)
     U0, res0 = lat.hmc_trajectory(cuda(Un), _prm(case, 0.4, 3, 0, method=method), 2011, 6)
     Uo, ores, st = olat.hmc_trajectory(Un, _prm(case, 0.4, 3, 0, mod=O), 2011, 6)
     assert st == 0
@@ -109,15 +113,16 @@ def test_chrono_trajectory_matches_oracle(case, method):
     lat.close()
 
 
-def test_chrono_graph_equals_eager():
+@pytest.mark.parametrize("chrono", [1, 2])
+def test_chrono_graph_equals_eager(chrono):
     L, l0 = (16, 8, 8, 8), 4
     U0 = cuda(syn.random_links(L, 0.6, 17))
     lat_e = lqcd.Lattice(L, l0, -1, l0s=2)
     lat_g = lqcd.Lattice(L, l0, -1, l0s=2)
     Ue, Ug = U0.clone(), U0.clone()
     for t in range(3):
-        Ue, re = lat_e.hmc_trajectory(Ue, _prm("four_part", 0.5, 2, 1, graph=0), 99, t)
-        Ug, rg = lat_g.hmc_trajectory(Ug, _prm("four_part", 0.5, 2, 1, graph=1), 99, t)
+        Ue, re = lat_e.hmc_trajectory(Ue, _prm("four_part", 0.5, 2, chrono, graph=0), 99, t)
+        Ug, rg = lat_g.hmc_trajectory(Ug, _prm("four_part", 0.5, 2, chrono, graph=1), 99, t)
         assert torch.equal(Ue, Ug), t
         assert re.dH == rg.dH and re.accepted == rg.accepted
         assert re.solver_iters == rg.solver_iters
@@ -125,7 +130,8 @@ def test_chrono_graph_equals_eager():
     lat_g.close()
 
 
-def test_chrono_md_reversible():
+@pytest.mark.parametrize("chrono", [1, 2])
+def test_chrono_md_reversible(chrono):
     """forward then backward with the momenta negated returns to the start
     up to the solver tolerance (the guesses differ between the two legs)"""
     L, l0 = (8, 4, 4, 4), 4
@@ -137,7 +143,7 @@ def test_chrono_md_reversible():
     ps2 = syn.gaussian_spinor(olat.Vh, 75)
     ps1 = syn.gaussian_spinor(olat.Vh, 76)
     lat = lqcd.Lattice(L, l0, -1, l0s=2)
-    prm = _prm("four_part", 0.3, 2, 1)
+    prm = _prm("four_part", 0.3, 2, chrono)
     fields = (None, cuda(phi2), prm, None, cuda(phi4), cuda(ps2), cuda(ps1))
     U1, P1 = lat.md(cuda(Un), cuda(P), *fields)
     U2, P2 = lat.md(U1, -P1, *fields)
