@@ -327,11 +327,19 @@ typedef struct {
                            kept: that one; the first solve of a trajectory
                            starts from zero); 2: the quadratic extrapolation
                            through the three previous solutions (fewer kept:
-                           the lower orders).  The solves still run to tol,
+                           the lower orders); 3: as 2, except that the whole-
+                           lattice solves of the boundary term start from the
+                           combination of their last (up to) six solutions
+                           that minimises the residual under the current
+                           links (minimal residual extrapolation: the
+                           solutions' images under the even-odd matrix in
+                           single precision, the small normal equations
+                           solved on the device).  The solves still run to tol,
                            so the forces agree with chrono = 0 to the solver
                            tolerance, and reversibility holds to it.  Needs
                            12 (chrono + 1) extra even-site double fields on
-                           the device (allocated on first use). */
+                           the device (chrono = 3: 42, and six single-
+                           precision ones; allocated on first use). */
 } lqcd_hmc_params;
 
 /* Pseudo-fermion fields of lqcd_md (device pointers, NULL where the term

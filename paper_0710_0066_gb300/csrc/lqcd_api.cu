@@ -72,12 +72,12 @@ int chrono_guess(lqcd_ctx* h, int k, double2* x, int dag, int* guess)
     constexpr int D = lqcd_ctx::CHRONO_MAX;
     *guess = 0;
     if (k < 0 || !h->chrono_buf[D * k] || h->chrono_n[k] == 0) return LQCD_OK;
-    const int depth = h->chrono_depth;
+    const int depth = std::max(1, h->chrono_depth[k]);
     // newest first: buffers cur, cur - 1, cur - 2 (mod depth)
     const int j2 = h->chrono_cur[k], j1 = (j2 + depth - 1) % depth, j0 = (j2 + depth - 2) % depth;
     const double t = h->md_time, t2 = h->chrono_t[k][j2], t1 = h->chrono_t[k][j1], t0 = h->chrono_t[k][j0];
     const double2 *x2 = h->chrono_buf[D * k + j2], *x1 = h->chrono_buf[D * k + j1], *x0 = h->chrono_buf[D * k + j0];
-    int n = h->chrono_n[k];
+    int n = std::min(h->chrono_n[k], 3);
     if (n >= 2 && t1 == t2) n = 1;
     if (n >= 3 && (t0 == t1 || t0 == t2)) n = 2;
     if (n == 3) {
@@ -100,12 +100,28 @@ int chrono_store(lqcd_ctx* h, int k, const double2* x)
 {
     constexpr int D = lqcd_ctx::CHRONO_MAX;
     if (k < 0 || !h->chrono_buf[D * k] || h->chrono_frozen) return LQCD_OK;
-    const int depth = h->chrono_depth;
+    const int depth = std::max(1, h->chrono_depth[k]);
     h->chrono_cur[k] = (h->chrono_cur[k] + 1) % depth;
     LQ_CUDA(h, cudaMemcpyAsync(h->chrono_buf[D * k + h->chrono_cur[k]], x, sizeof(double2) * 12 * (size_t)h->g.Vh,
                                cudaMemcpyDeviceToDevice, h->stream));
     h->chrono_t[k][h->chrono_cur[k]] = h->md_time;
     h->chrono_n[k] = h->chrono_n[k] < depth ? h->chrono_n[k] + 1 : depth;
+    return LQCD_OK;
+}
+
+// minimal-residual guess of slot k for the whole-lattice even-odd system
+// with source b_e (the solve's b_e' = b_e + kappa H_eo b_o): over all kept
+// solutions of the slot (chrono = 3, lqcd_chrono.cu)
+int chrono_mre(lqcd_ctx* h, int k, double2* x, const double2* b_e, double kappa, int dag, int* guess)
+{
+    *guess = 0;
+    constexpr int D = lqcd_ctx::CHRONO_MAX;
+    if (k < 0 || !h->chrono_buf[D * k] || h->chrono_n[k] == 0) return LQCD_OK;
+    const double2* sol[lqcd_ctx::NMRE];
+    const int n = std::min(h->chrono_n[k], (int)lqcd_ctx::NMRE);
+    for (int i = 0; i < n; ++i) sol[i] = h->chrono_buf[D * k + i];
+    LQ_TRY(chrono_mre_guess(h, sol, n, x, b_e, kappa, dag));
+    *guess = 1;
     return LQCD_OK;
 }
 
@@ -124,13 +140,16 @@ int solve_full(lqcd_ctx* h, int mode, int colour, int dagger, int prec, double k
         bb = fld(h, F_T1);
     }
     const int col = mode == MODE_ALL ? -1 : colour;
-    int guess = 0;
-    LQ_TRY(chrono_guess(h, slot, x, dagger, &guess));
     // b_e' = b_e + kappa H_eo b_o (double fields; double-float arithmetic
     // around a mixed-precision solve)
     const int hp = prec == PREC64 ? PREC64 : PRECDF;
     LQ_TRY(hop_sweep(h, hp, mode, 0, 0, col, sp64(fld(h, F_T2), 0, Vh), sp64((double2*)bb, 1, Vh), 1.0,
                      sp64((double2*)bb, 0, Vh), kappa));
+    int guess = 0;
+    if (mode == MODE_ALL && h->chrono_mre && slot >= 0)
+        LQ_TRY(chrono_mre(h, slot, x, fld(h, F_T2), kappa, dagger, &guess));
+    else
+        LQ_TRY(chrono_guess(h, slot, x, dagger, &guess));
     // whole-lattice solves take the handle's global solver (plain or
     // Schwarz-preconditioned BiCGstab), block solves the caller's method
     LQ_TRY(eo_solve(h, mode, col, prec, kappa, x, fld(h, F_T2), tol, max_iter, iters, resid, 1.0,
@@ -439,15 +458,35 @@ void build_step(const lqcd_hmc_params& p, int j, double dt, std::vector<Op>& v)
     }
 }
 
-// the chronological slots of the force solves (chrono + 1 even-half double
-// fields each), allocated before any capture
+// chronological slots of the force solves: the solve of a term and its
+// adjoint solve; the boundary term's are the whole-lattice solves
+enum { SLOT_W1 = 0, SLOT_SCHUR = 2, SLOT_W2 = 4, SLOT_SCHUR2 = 6, SLOT_S2 = 8, SLOT_S1 = 10 };
+
+// solutions kept per slot: chrono + 1 (polynomial extrapolation, at most
+// three), all NMRE for the whole-lattice slots with chrono = 3
+int chrono_slot_depth(const lqcd_hmc_params& p, int k)
+{
+    if (p.chrono == 3 && (k == SLOT_SCHUR || k == SLOT_SCHUR + 1)) return lqcd_ctx::NMRE;
+    return std::min(p.chrono, 2) + 1;
+}
+
+void chrono_configure(lqcd_ctx* h, const lqcd_hmc_params& p)
+{
+    for (int k = 0; k < lqcd_ctx::NCHRONO; ++k) h->chrono_depth[k] = chrono_slot_depth(p, k);
+    h->chrono_mre = p.chrono == 3;
+}
+
+// the chronological slots of the force solves (chrono_slot_depth even-half
+// double fields each) and the minimal-residual workspace, allocated before
+// any capture
 int chrono_alloc(lqcd_ctx* h, const lqcd_hmc_params* p)
 {
     if (!p->chrono) return LQCD_OK;
+    if (p->chrono == 3) LQ_TRY(chrono_mre_alloc(h));
     constexpr int D = lqcd_ctx::CHRONO_MAX;
     const size_t bytes = sizeof(double2) * 12 * (size_t)h->g.Vh;
     for (int k = 0; k < lqcd_ctx::NCHRONO; ++k)
-        for (int j = 0; j < p->chrono + 1; ++j) {
+        for (int j = 0; j < chrono_slot_depth(*p, k); ++j) {
             double2*& b = h->chrono_buf[D * k + j];
             if (b) continue;
             LQ_CUDA(h, cudaMalloc(&b, bytes));
@@ -487,8 +526,8 @@ int check_params(lqcd_ctx* h, const lqcd_hmc_params* p)
         h->err = "hmc params: use_graph must be 0 or 1";
         return LQCD_ERR_ARG;
     }
-    if (p->chrono < 0 || p->chrono > 2) {
-        h->err = "hmc params: chrono must be 0, 1 or 2";
+    if (p->chrono < 0 || p->chrono > 3) {
+        h->err = "hmc params: chrono must be 0, 1, 2 or 3";
         return LQCD_ERR_ARG;
     }
     if ((p->eo_solver != LQCD_SOLVER_BICGSTAB && p->eo_solver != LQCD_SOLVER_SERIES) ||
@@ -559,14 +598,14 @@ int do_md(lqcd_ctx* h, const lqcd_hmc_params& p, double* P, const PfFields& pf, 
     for (int i = 0; i < p.nsteps[top]; ++i) build_step(p, top, dt, ops);
     // chronological slots (two per term: the solve and its adjoint)
     const bool ch = p.chrono != 0;
-    const SolveCfg cw1{p.precision, p.tol, p.max_iter, p.block_solver, ch ? 0 : -1};
-    const SolveCfg csch{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? 2 : -1};
-    const SolveCfg cw2{p.precision, p.tol, p.max_iter, p.block_solver, ch ? 4 : -1};
-    const SolveCfg csch2{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? 6 : -1};
-    const SolveCfg cs2{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 8 : -1};
-    const SolveCfg cs1{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 10 : -1};
+    const SolveCfg cw1{p.precision, p.tol, p.max_iter, p.block_solver, ch ? SLOT_W1 : -1};
+    const SolveCfg csch{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? SLOT_SCHUR : -1};
+    const SolveCfg cw2{p.precision, p.tol, p.max_iter, p.block_solver, ch ? SLOT_W2 : -1};
+    const SolveCfg csch2{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? SLOT_SCHUR2 : -1};
+    const SolveCfg cs2{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? SLOT_S2 : -1};
+    const SolveCfg cs1{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? SLOT_S1 : -1};
     for (int k = 0; k < lqcd_ctx::NCHRONO; ++k) h->chrono_n[k] = h->chrono_cur[k] = 0;
-    h->chrono_depth = p.chrono + 1;
+    chrono_configure(h, p);
     h->md_time = 0.0;
     for (const Op& o : ops) {
         if (o.kind == 1) {
@@ -755,16 +794,17 @@ struct ChronoFreeze {
 int energy(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, int base)
 {
     const bool ch = p.chrono != 0;
+    chrono_configure(h, p);
     ChronoFreeze freeze(h);
     double* e = h->red_out + base;
     LQ_TRY(kinetic_sum(h, h->P, e));
     if (p.level_gauge >= 0) LQ_TRY(plaquette_sum(h, e + 1));
-    const SolveCfg cw1{p.precision, p.tol, p.max_iter, p.block_solver, ch ? 0 : -1};
-    const SolveCfg csch{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? 2 : -1};
-    const SolveCfg cw2{p.precision, p.tol, p.max_iter, p.block_solver, ch ? 4 : -1};
-    const SolveCfg csch2{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? 6 : -1};
-    const SolveCfg cs2{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 8 : -1};
-    const SolveCfg cs1{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? 10 : -1};
+    const SolveCfg cw1{p.precision, p.tol, p.max_iter, p.block_solver, ch ? SLOT_W1 : -1};
+    const SolveCfg csch{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? SLOT_SCHUR : -1};
+    const SolveCfg cw2{p.precision, p.tol, p.max_iter, p.block_solver, ch ? SLOT_W2 : -1};
+    const SolveCfg csch2{p.precision, p.tol, p.max_iter, SOLVER_BICGSTAB, ch ? SLOT_SCHUR2 : -1};
+    const SolveCfg cs2{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? SLOT_S2 : -1};
+    const SolveCfg cs1{p.precision, p.tol, p.max_iter, p.eo_solver, ch ? SLOT_S1 : -1};
     if (p.level_w1 >= 0) LQ_TRY(pf_w1(h, nullptr, pf.phi1, p.kappa, 0.0, cw1, e + 2));
     if (p.level_schur >= 0) LQ_TRY(pf_schur(h, nullptr, pf.phi2, p.kappa, 0.0, csch, e + 3));
     if (p.level_w2 >= 0) LQ_TRY(pf_w2(h, nullptr, pf.phi3, p.kappa, 0.0, cw2, e + 4));
@@ -958,6 +998,7 @@ int lqcd_destroy(lqcd_t h)
     cudaFree(h->U64);
     cudaFree(h->U64_save);
     for (double2* f : h->chrono_buf) cudaFree(f);
+    chrono_mre_free(h);
     cudaFree(h->U32);
     cudaFree(h->U16);
     for (double2* f : h->f64) cudaFree(f);

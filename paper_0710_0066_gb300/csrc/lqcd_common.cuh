@@ -759,12 +759,21 @@ struct lqcd_ctx {
     // (buffers CHRONO_MAX k + j, a ring; chrono_cur[k] names the newest)
     // and the MD times of the links each buffer's solution was solved on
     static constexpr int NCHRONO = 12;
-    static constexpr int CHRONO_MAX = 3;
+    static constexpr int NMRE = 6;        // solutions of a minimal-residual guess
+    static constexpr int CHRONO_MAX = NMRE;
     double2* chrono_buf[CHRONO_MAX * NCHRONO] = {};
-    int chrono_n[NCHRONO] = {};    // solutions kept (0 .. chrono_depth)
+    int chrono_n[NCHRONO] = {};    // solutions kept (0 .. chrono_depth[k])
     int chrono_cur[NCHRONO] = {};
     double chrono_t[NCHRONO][CHRONO_MAX] = {};  // MD time of each buffer
-    int chrono_depth = 2;                        // solutions the guess uses (chrono + 1)
+    int chrono_depth[NCHRONO] = {};  // solutions kept per slot: chrono + 1 (at most 3), NMRE for
+                                     // the minimal-residual slots of the whole-lattice solves
+    bool chrono_mre = false;         // chrono = 3: whole-lattice solves guess by minimal residual
+    // workspace of the minimal-residual guess (lqcd_chrono.cu)
+    float4* mre_w[NMRE] = {};
+    float4* mre_v = nullptr;
+    float4* mre_o = nullptr;
+    double2* mre_c = nullptr;
+    double* mre_part = nullptr;
     double md_time = 0.0;              // MD time of the links in do_md
     bool chrono_frozen = false;        // guesses are read but not replaced
     int md_nforce = 0;                  // force evaluations per replay
@@ -841,6 +850,13 @@ int axpby_full(lqcd_ctx* h, double2* y, double a, const double2* x, double b, in
 int gamma5_full(lqcd_ctx* h, double2* y, const double2* x);
 // even half: y = gamma5^g5 (a x1 + b x0); x0 not read when b = 0
 int lincomb_even(lqcd_ctx* h, double2* y, double a, const double2* x1, double b, const double2* x0, int g5);
+// chrono.cu: minimal-residual guess x_e for (1 - kappa^2 H_eo H_oe) x_e = b_e
+// from the n solutions sol[i] (double even halves, gamma5^dag applied to
+// them), its workspace
+int chrono_mre_guess(lqcd_ctx* h, const double2* const* sol, int n, double2* x_e, const double2* b_e, double kappa,
+                     int dag);
+int chrono_mre_alloc(lqcd_ctx* h);
+void chrono_mre_free(lqcd_ctx* h);
 // even half: y = gamma5^g5 (a x2 + b x1 + c x0)
 int lincomb3_even(lqcd_ctx* h, double2* y, double a, const double2* x2, double b, const double2* x1, double c,
                   const double2* x0, int g5);

@@ -1,8 +1,10 @@
 """Chronological initial guesses of the molecular-dynamics force solves
 (lqcd_hmc_params.chrono): each solve starts from the linear (chrono = 1)
 or quadratic (chrono = 2) extrapolation in MD time of its solutions at the
-two or three previous force evaluations of its term (Brower et al.'s
-chronological inverter).  The solves still run
+two or three previous force evaluations of its term, or (chrono = 3, the
+whole-lattice solves of the boundary term) from the combination of its last
+six solutions with the smallest residual (Brower et al.'s chronological
+inverter).  The solves still run
 to the requested residual, so trajectories agree with the FP64 oracle (which
 always starts from zero) to the tolerances of the other trajectory tests;
 a solve whose guess already meets the residual takes no iteration; the
@@ -63,7 +65,8 @@ def _prm(case, tau, top, chrono, graph=0, prec=lqcd.PREC_F32, method=lqcd.SOLVER
 
 
 @pytest.mark.parametrize("case", list(CASES))
-def test_repeated_solves_take_no_iterations(case):
+@pytest.mark.parametrize("order", [1, 3])
+def test_repeated_solves_take_no_iterations(case, order):
     """tau = 1e-14: every force evaluation of a term solves the same systems
     up to 1e-14, so with chrono = 1 only the first evaluation of each term
     iterates and more integration steps cost (almost) no more iterations;
@@ -72,11 +75,11 @@ def test_repeated_solves_take_no_iterations(case):
     U = cuda(syn.random_links(L, 0.3, 61))
     lat = lqcd.Lattice(L, l0, -1, l0s=2)
     it = {}
-    for chrono in (0, 1):
+    for chrono in (0, order):
         for top in (1, 3):
             _, r = lat.hmc_trajectory(U, _prm(case, 1e-14, top, chrono), 7, 0)
             assert abs(r.dH) < 1e-8
-            it[chrono, top] = (r.solver_iters, r.n_force)
+            it[min(chrono, 1), top] = (r.solver_iters, r.n_force)
     assert it[0, 3][1] == it[1, 3][1] > it[0, 1][1] == it[1, 1][1]
     extra_plain = it[0, 3][0] - it[0, 1][0]
     extra_chrono = it[1, 3][0] - it[1, 1][0]
@@ -92,7 +95,9 @@ def test_repeated_solves_take_no_iterations(case):
                                                 ("four_part", lqcd.SOLVER_BICGSTAB, 1),
                                                 ("four_part", lqcd.SOLVER_SERIES, 1),
                                                 ("two_part", lqcd.SOLVER_BICGSTAB, 2),
-                                                ("four_part", lqcd.SOLVER_SERIES, 2)])
+                                                ("four_part", lqcd.SOLVER_SERIES, 2),
+                                                ("two_part", lqcd.SOLVER_BICGSTAB, 3),
+                                                ("four_part", lqcd.SOLVER_SERIES, 3)])
 def test_chrono_trajectory_matches_oracle(case, method, chrono):
     """the mixed-precision trajectory with chronological guesses against
     the oracle's, which solves every system from zero"""
@@ -113,7 +118,7 @@ def test_chrono_trajectory_matches_oracle(case, method, chrono):
     lat.close()
 
 
-@pytest.mark.parametrize("chrono", [1, 2])
+@pytest.mark.parametrize("chrono", [1, 2, 3])
 def test_chrono_graph_equals_eager(chrono):
     L, l0 = (16, 8, 8, 8), 4
     U0 = cuda(syn.random_links(L, 0.6, 17))
@@ -130,7 +135,7 @@ def test_chrono_graph_equals_eager(chrono):
     lat_g.close()
 
 
-@pytest.mark.parametrize("chrono", [1, 2])
+@pytest.mark.parametrize("chrono", [1, 2, 3])
 def test_chrono_md_reversible(chrono):
     """forward then backward with the momenta negated returns to the start
     up to the solver tolerance (the guesses differ between the two legs)"""
