@@ -812,8 +812,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--chrono", type=int, default=1, choices=[1, 2],
-                    help="order of the chronological guesses: 1 linear (two solutions), 2 quadratic (three)")
+    ap.add_argument("--chrono", type=int, default=1, choices=[1, 2, 3],
+                    help="chronological guesses: 1 linear (two solutions), 2 quadratic (three), 3 quadratic "
+                         "with minimal-residual guesses (six solutions) for the whole-lattice solves")
     ap.add_argument("--no-chrono", action="store_true",
                     help="start every force solve from zero instead of the previous solution of its term")
     ap.add_argument("--no-graph", action="store_true",
