@@ -812,7 +812,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--chrono", type=int, default=1, choices=[1, 2, 3],
+    ap.add_argument("--chrono", type=int, default=2, choices=[1, 2, 3],
                     help="chronological guesses: 1 linear (two solutions), 2 quadratic (three), 3 quadratic "
                          "with minimal-residual guesses (six solutions) for the whole-lattice solves")
     ap.add_argument("--no-chrono", action="store_true",

@@ -224,6 +224,35 @@ __device__ __forceinline__ void cdot2(float4 a, float4 b, double& re, double& im
 }
 __device__ __forceinline__ double nrm2w(float4 a) { return (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w); }
 
+// single-precision spinor at site j of the combination y + a x of two
+// inner vectors (word by word, as the element-wise phases form it), and of
+// y + b (z + a x) of three
+__device__ __forceinline__ void load_axpy32(const SpinorF& x, const SpinorF& y, float2 a, int j, Spinor<float>& s)
+{
+    const float4* xp = (const float4*)x.v;
+    const float4* yp = (const float4*)y.v;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float4 w = caxpy2(a, xp[(size_t)k * x.N + j], yp[(size_t)k * y.N + j]);
+        s.c[(2 * k) / 3][(2 * k) % 3] = mk(w.x, w.y);
+        s.c[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(w.z, w.w);
+    }
+}
+__device__ __forceinline__ void load_axpypz32(const SpinorF& x, const SpinorF& z, const SpinorF& y, float2 a, float2 b,
+                                              int j, Spinor<float>& s)
+{
+    const float4* xp = (const float4*)x.v;
+    const float4* zp = (const float4*)z.v;
+    const float4* yp = (const float4*)y.v;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const size_t o = (size_t)k * x.N + j;
+        const float4 w = caxpy2(b, caxpy2(a, xp[o], zp[o]), yp[o]);
+        s.c[(2 * k) / 3][(2 * k) % 3] = mk(w.x, w.y);
+        s.c[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(w.z, w.w);
+    }
+}
+
 template <class T>
 __device__ __forceinline__ void sp_axpy(Spinor<T>& y, T a, const Spinor<T>& x)  // y <- x + a y
 {
@@ -801,6 +830,163 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                     store_spinor<PE>(A.e, i, ee);
                 }
             SYNC_OR_RETURN;
+        } else {
+        if constexpr (P == PREC32) {
+            // ---- BiCGstab with the vector updates folded into the hopping
+            // phases: s = r - alpha v is formed where H_oe s reads it (at the
+            // neighbours) and where the next phase keeps it; the update
+            // p = r + beta (p - omega v) waits for the next iteration, whose
+            // H_oe p forms it at the neighbours and whose second phase keeps
+            // it.  Five barriers per iteration (seven unfolded); the same
+            // word-wise single-precision operations as the unfolded form.
+            bool pend = false;  // p = r + beta (p - omega v) not yet formed
+            const T k2 = (T)A.k2, dg = (T)A.diag;
+            for (;;) {
+                if (S.idone) break;
+                const float2 pbe = make_float2((float)S.beta.x, (float)S.beta.y);
+                const float2 pmom = make_float2(-(float)S.omega.x, -(float)S.omega.y);
+                // tmp = H_oe p'
+                if (pend) {
+                    FOR_SITES
+                    {
+                        const int i = base + j_;
+                        Spinor<T> a;
+                        hop_site_ld<P>(A.g, A.mode, 0, 1, i,
+                                       [&](int j, Spinor<T>& sp) { load_axpypz32(A.v, A.p, A.r, pmom, pbe, j, sp); },
+                                       A.UP, a);
+                        store_spinor<P>(A.tmp, i, a);
+                    }
+                } else {
+                    FOR_SITES
+                    {
+                        const int i = base + j_;
+                        Spinor<T> a;
+                        hop_site<P, false>(A.g, A.mode, 0, 1, i, A.p, A.UP, a);
+                        store_spinor<P>(A.tmp, i, a);
+                    }
+                }
+                SYNC_OR_RETURN;
+                // p = p' ; v = dg p - k2 H_eo tmp ; <rh, v>
+                {
+                    double qr = 0.0, qi = 0.0;
+                    FOR_SITES
+                    {
+                        const int i = base + j_;
+                        Spinor<T> a, pp, rh;
+                        hop_site<P, false>(A.g, A.mode, 0, 0, i, A.tmp, A.UP, a);
+                        if (pend) {
+                            load_axpypz32(A.v, A.p, A.r, pmom, pbe, i, pp);
+                            store_spinor<P>(A.p, i, pp);
+                        } else {
+                            load_spinor<P, false>(A.p, i, pp);
+                        }
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) a.c[s][c] = dg * pp.c[s][c] - k2 * a.c[s][c];
+                        store_spinor<P>(A.v, i, a);
+                        load_spinor<P, false>(A.rh, i, rh);
+                        cdot_acc(rh, a, qr, qi);
+                    }
+                    reduce_put(A, qr, qi, 0.0, 2, rb);
+                    SYNC_OR_RETURN;
+                    gather_own(A, sys, 2, red, rb);
+                    if (tid == 0) {
+                        const double2 d = make_double2(red[0], red[1]);
+                        const double2 al = cdiv(S.rho, d);
+                        if (!finite2(al) || (d.x == 0.0 && d.y == 0.0)) {
+                            S.idone = 1;
+                            S.alpha = make_double2(0.0, 0.0);
+                        } else {
+                            S.alpha = al;
+                        }
+                    }
+                    __syncthreads();
+                }
+                pend = false;
+                if (S.idone) break;
+                const float2 mal = make_float2(-(float)S.alpha.x, -(float)S.alpha.y);
+                // tmp = H_oe s, s = r - alpha v formed at the neighbours
+                FOR_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<T> a;
+                    hop_site_ld<P>(A.g, A.mode, 0, 1, i,
+                                   [&](int j, Spinor<T>& sp) { load_axpy32(A.v, A.r, mal, j, sp); }, A.UP, a);
+                    store_spinor<P>(A.tmp, i, a);
+                }
+                SYNC_OR_RETURN;
+                // s = r - alpha v (kept) ; t = dg s - k2 H_eo tmp ; <t, s>, <t, t>
+                {
+                    double qr = 0.0, qi = 0.0, qt = 0.0;
+                    FOR_SITES
+                    {
+                        const int i = base + j_;
+                        Spinor<T> a, ss;
+                        hop_site<P, false>(A.g, A.mode, 0, 0, i, A.tmp, A.UP, a);
+                        load_axpy32(A.v, A.r, mal, i, ss);
+                        store_spinor<P>(A.s, i, ss);
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) a.c[s][c] = dg * ss.c[s][c] - k2 * a.c[s][c];
+                        store_spinor<P>(A.t, i, a);
+                        cdot_acc(a, ss, qr, qi);
+                        qt += nrm_acc(a);
+                    }
+                    reduce_put(A, qr, qi, qt, 3, rb);
+                    SYNC_OR_RETURN;
+                    gather_own(A, sys, 3, red, rb);
+                    if (tid == 0) {
+                        const double tt = red[2];
+                        const double2 om = make_double2(red[0] / tt, red[1] / tt);
+                        if (!(tt > 0.0) || !finite2(om)) {
+                            S.omega = make_double2(0.0, 0.0);
+                            S.idone = 2;  // keep alpha p, stop afterwards
+                        } else {
+                            S.omega = om;
+                        }
+                    }
+                    __syncthreads();
+                }
+                // e += alpha p + omega s ; r = s - omega t ; <rh, r>, |r|^2
+                {
+                    double qr = 0.0, qi = 0.0, qn = 0.0;
+                    const float2 al = make_float2((float)S.alpha.x, (float)S.alpha.y);
+                    const float2 om = make_float2((float)S.omega.x, (float)S.omega.y);
+                    const float2 mom = make_float2(-om.x, -om.y);
+                    FOR_WORDS
+                    {
+                        WORD_ADDR;
+                        const float4 ss = W4(A.s)[a];
+                        W4(A.e)[a] = caxpy2(om, ss, caxpy2(al, W4(A.p)[a], W4(A.e)[a]));
+                        const float4 rr = caxpy2(mom, W4(A.t)[a], ss);
+                        W4(A.r)[a] = rr;
+                        cdot2(W4(A.rh)[a], rr, qr, qi);
+                        qn += nrm2w(rr);
+                    }
+                    reduce_put(A, qr, qi, qn, 3, rb);
+                    SYNC_OR_RETURN;
+                    gather_own(A, sys, 3, red, rb);
+                    if (tid == 0) {
+                        S.it += 1;
+                        S.itc += 1;
+                        const double2 rn = make_double2(red[0], red[1]);
+                        S.rr = red[2];
+                        if (S.idone == 2 || S.itc >= A.max_inner || S.it >= A.max_iter || !(S.rr > S.itol2) ||
+                            !finite2(rn)) {
+                            S.idone = 1;
+                        } else {
+                            S.beta = cmul(cdiv(rn, S.rho), cdiv(S.alpha, S.omega));
+                            if (!finite2(S.beta)) S.idone = 1;
+                            S.rho = rn;
+                        }
+                    }
+                    if (tid == 0 && S.idone) S.idone = 1;
+                    __syncthreads();
+                }
+                pend = !S.idone;
+            }
         } else
         // ---- BiCGstab: seven barriers per iteration
         for (;;) {
@@ -1014,6 +1200,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             }
             SYNC_OR_RETURN;
         }
+        }  // BiCGstab
         }  // inner solve (not SAP)
 
         // ---- x += |r64| e (double)
