@@ -514,28 +514,33 @@ LQ_HD bool t_hop_kept(const Geo& g, int mode, int xf)
     return sub_face && !slab_face;
 }
 
-// ld(j, spinor) provides the input spinor at eo index j of parity 1-pout
-template <int P, class Loader>
+// ld(j, spinor) provides the input spinor at eo index j of parity 1-pout.
+// UNR: unrolling of the loop over the four directions (4: every hop
+// specialised at compile time, the fastest code for a kernel that runs one
+// sweep; 1: one copy of the hop code, four times smaller, for the large
+// persistent kernels whose many phases would otherwise not fit the
+// instruction cache)
+template <int P, int UNR = 4, class Loader>
 __device__ __forceinline__ void hop_site_ld(const Geo& g, int mode, int dag, int pout, int i, Loader ld,
                                             const GaugeF& U, Spinor<typename Real<P>::T>& acc);
 
-template <int P, bool RO>
+template <int P, bool RO, int UNR = 4>
 __device__ __forceinline__ void hop_site_df(const Geo& g, int mode, int dag, int pout, int i, const SpinorF& in,
                                             const GaugeF& U, Spinor<df>& acc);
 
-template <int P, bool RO = true>
+template <int P, bool RO = true, int UNR = 4>
 __device__ __forceinline__ void hop_site(const Geo& g, int mode, int dag, int pout, int i,
                                          const SpinorF& in, const GaugeF& U,
                                          Spinor<typename Real<P>::T>& acc)
 {
     if constexpr (P == PRECDF || P == PRECDS)
-        hop_site_df<P, RO>(g, mode, dag, pout, i, in, U, acc);
+        hop_site_df<P, RO, UNR>(g, mode, dag, pout, i, in, U, acc);
     else
-        hop_site_ld<P>(g, mode, dag, pout, i,
-                       [&](int j, Spinor<typename Real<P>::T>& s) { load_spinor<P, RO>(in, j, s); }, U, acc);
+        hop_site_ld<P, UNR>(g, mode, dag, pout, i,
+                            [&](int j, Spinor<typename Real<P>::T>& s) { load_spinor<P, RO>(in, j, s); }, U, acc);
 }
 
-template <int P, class Loader>
+template <int P, int UNR, class Loader>
 __device__ __forceinline__ void hop_site_ld(const Geo& g, int mode, int dag, int pout, int i, Loader ld,
                                             const GaugeF& U, Spinor<typename Real<P>::T>& acc)
 {
@@ -549,7 +554,7 @@ __device__ __forceinline__ void hop_site_ld(const Geo& g, int mode, int dag, int
     const int lex = lex_of(g, x);
     int stride = 1;
     const int pin = 1 - pout;
-#pragma unroll
+#pragma unroll(UNR)
     for (int mu = 3; mu >= 0; --mu) {
         // forward hop x -> x + mu
         {
@@ -630,7 +635,7 @@ __device__ __forceinline__ cx<df> df_link(const double2* p, int k, int Vh, int i
     return mk(df_split(d.x), df_split(d.y));
 }
 
-template <int P, bool RO>
+template <int P, bool RO, int UNR>
 __device__ __forceinline__ void hop_site_df(const Geo& g, int mode, int dag, int pout, int i, const SpinorF& in,
                                             const GaugeF& U, Spinor<df>& acc)
 {
@@ -643,7 +648,7 @@ __device__ __forceinline__ void hop_site_df(const Geo& g, int mode, int dag, int
     const int lex = lex_of(g, x);
     int stride = 1;
     const int pin = 1 - pout;
-#pragma unroll
+#pragma unroll(UNR)
     for (int mu = 3; mu >= 0; --mu) {
 #pragma unroll
         for (int fw = 1; fw >= 0; --fw) {
