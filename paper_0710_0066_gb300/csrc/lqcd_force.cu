@@ -335,13 +335,58 @@ __global__ void k_force_profile(Geo g, const double* F, double* out)
 }
 
 // exp(iQ) for traceless hermitian Q by the Cayley-Hamilton form
-// exp(iQ) = f0 + f1 Q + f2 Q^2 (Morningstar & Peardon, PRD 69 (2004) 054501)
+// exp(iQ) = f0 + f1 Q + f2 Q^2 (Morningstar & Peardon, PRD 69 (2004) 054501).
+// For the molecular dynamics' small steps (c1 = tr Q^2 / 2 <= 1) the
+// coefficients come from the Taylor series of exp(iQ) reduced by
+// Cayley-Hamilton, Q^3 = c1 Q + c0 (c0 = det Q): with Q^n = a0 + a1 Q + a2 Q^2,
+// Q^(n+1) = c0 a2 + (a0 + c1 a2) Q + a1 Q^2, and f_j = sum_n i^n a_j / n!,
+// a scalar recurrence without transcendental functions (terms fall below
+// 1e-17 of the leading ones after about 6 + 3 |Q| steps); larger Q use the
+// closed form with the trigonometric functions.
 __device__ void expiq(const Su3<double>& Q, Su3<double>& E)
 {
     Su3<double> Q2;
     su3_mul(Q, Q, Q2);
     const double c1 = 0.5 * (Q2.m[0][0].re + Q2.m[1][1].re + Q2.m[2][2].re);
     cx<double> f0, f1, f2;
+    if (c1 >= 1e-12 && c1 <= 1.0) {
+        const cx<double> det = Q.m[0][0] * (Q.m[1][1] * Q.m[2][2] - Q.m[1][2] * Q.m[2][1]) -
+                               Q.m[0][1] * (Q.m[1][0] * Q.m[2][2] - Q.m[1][2] * Q.m[2][0]) +
+                               Q.m[0][2] * (Q.m[1][0] * Q.m[2][1] - Q.m[1][1] * Q.m[2][0]);
+        const double c0 = det.re;
+        double a0 = 1.0, a1 = 0.0, a2 = 0.0, w = 1.0;  // Q^n coordinates, 1 / n!
+        double r0 = 1.0, r1 = 0.0, r2 = 0.0, i0 = 0.0, i1 = 0.0, i2 = 0.0;
+        const double qn = sqrt(2.0 * c1);  // Frobenius norm of Q: |Q^n| <= qn^n
+        double bound = 1.0;
+        for (int n = 1; n <= 40; ++n) {
+            const double b0 = c0 * a2, b1 = a0 + c1 * a2, b2 = a1;
+            a0 = b0;
+            a1 = b1;
+            a2 = b2;
+            w /= (double)n;
+            bound *= qn / (double)n;
+            // i^n: 1, i, -1, -i
+            switch (n & 3) {
+                case 0: r0 += w * a0; r1 += w * a1; r2 += w * a2; break;
+                case 1: i0 += w * a0; i1 += w * a1; i2 += w * a2; break;
+                case 2: r0 -= w * a0; r1 -= w * a1; r2 -= w * a2; break;
+                default: i0 -= w * a0; i1 -= w * a1; i2 -= w * a2; break;
+            }
+            if (bound < 1e-18) break;
+        }
+        f0 = mk(r0, i0);
+        f1 = mk(r1, i1);
+        f2 = mk(r2, i2);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cx<double> v = f1 * Q.m[r][c] + f2 * Q2.m[r][c];
+                if (r == c) v = v + f0;
+                E.m[r][c] = v;
+            }
+        return;
+    }
     if (c1 < 1e-12) {
         // |Q| < 1.5e-6: series to fourth order
         Su3<double> Q3, Q4;
