@@ -307,7 +307,7 @@ def run_ours(args):
                                block_solver=lqcd.SOLVER_SERIES if args.block_solver == "series"
                                else lqcd.SOLVER_BICGSTAB)
 
-    prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
+    prec = {"f16": lqcd.PREC_F16, "bf16": lqcd.PREC_BF16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     prm = params(prec)
     block_solver = args.block_solver
 
@@ -419,7 +419,8 @@ def run_ours(args):
         del Ud_
         lqcd.lqcd_autotune(latd.h, 1, 0.0)
         x = torch.randn((latd.Vh, 4, 3), dtype=torch.complex128, device="cuda")
-        for name, pr in (("f32", lqcd.PREC_F32), ("f16", lqcd.PREC_F16), ("f64", lqcd.PREC_F64)):
+        for name, pr in (("f32", lqcd.PREC_F32), ("f16", lqcd.PREC_F16), ("bf16", lqcd.PREC_BF16),
+                         ("f64", lqcd.PREC_F64)):
             # the k_hop launch alone, timed by the library's CUDA events
             # around each of 100 launches queued back to back (the layout
             # conversions of each call run between them); one launch moves
@@ -476,7 +477,8 @@ def run_ours(args):
         "metric": METRIC,
         "value": value, "unit": "s/trajectory", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else ("f32+f64" if args.precision == "f32"
+                                                                  else args.precision + "-storage+f32+f64"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "lattice": "x".join(map(str, L)), "l0": l0,
                    "inner_precision": args.precision, "l2": "flushed between timed trajectories",
@@ -588,7 +590,7 @@ def run_iterated(args, W=WL_ITER):
                                eo_solver=lqcd.SOLVER_SERIES if args.eo_solver == "series" else lqcd.SOLVER_BICGSTAB,
                                use_graph=0 if args.no_graph else 1, chrono=0 if args.no_chrono else 1)
 
-    prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
+    prec = {"f16": lqcd.PREC_F16, "bf16": lqcd.PREC_BF16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     prm = params(prec)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -693,7 +695,7 @@ def run_case(args):
     torch.cuda.set_device(0)
     g = torch.Generator(device="cuda")
     g.manual_seed(WL["seed"])
-    prec = {"f16": lqcd.PREC_F16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
+    prec = {"f16": lqcd.PREC_F16, "bf16": lqcd.PREC_BF16, "f32": lqcd.PREC_F32, "f64": lqcd.PREC_F64}[args.precision]
     if args.case == "iterated":
         return run_iterated(args, WL_ITER)
     if args.case == "production":
@@ -765,7 +767,8 @@ def run_case(args):
         x = torch.randn((lat.Vh, 4, 3), dtype=torch.complex128, device="cuda", generator=g)
         lqcd.lqcd_profile_enable(lat.h, 1 << lqcd.KERNEL_HOP)
         out = {}
-        for name, pr in (("f32", lqcd.PREC_F32), ("f16", lqcd.PREC_F16), ("f64", lqcd.PREC_F64)):
+        for name, pr in (("f32", lqcd.PREC_F32), ("f16", lqcd.PREC_F16), ("bf16", lqcd.PREC_BF16),
+                         ("f64", lqcd.PREC_F64)):
             lat.dslash_eo(x, 0, 0.0, 0, lqcd.OP_HOP, pr)  # warm-up: launch 4k of this precision
             lqcd.lqcd_profile_reset(lat.h)
             for _ in range(3):
@@ -784,7 +787,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32", choices=["f16", "f32", "f64"],
+    ap.add_argument("--precision", default="f32", choices=["f16", "bf16", "f32", "f64"],
                     help="storage of the inner Krylov iterations (outer residuals stay double)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--block-solver", default="series", choices=["bicgstab", "series"],

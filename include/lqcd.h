@@ -46,8 +46,11 @@
  *   gamma_k = [[0,-i sigma_k],[i sigma_k,0]], gamma_5 = diag(1,1,-1,-1).
  * Fermion phase bc_t (+1 / -1) on every x0 hop that wraps L0-1 <-> 0.
  * Precision argument: LQCD_PREC_F64 runs everything in double precision;
- *   LQCD_PREC_F32 / LQCD_PREC_F16 run stencils and inner Krylov iterations
- *   with single- / half-precision storage (FP32 arithmetic) and keep
+ *   LQCD_PREC_F32 / LQCD_PREC_F16 / LQCD_PREC_BF16 run stencils and inner
+ *   Krylov iterations with single-, half- (IEEE fp16, each site scaled by
+ *   its largest component) or bfloat16-precision storage (8 exponent bits,
+ *   no scale; 8 significant bits) of spinors and links, FP32 arithmetic,
+ *   and keep
  *   double-precision residuals, dot products and outer defect correction;
  *   there the double hopping sweeps of the outer residual and of the
  *   even-odd source / reconstruction read the double fields and links and
@@ -76,7 +79,7 @@ enum {
     LQCD_ERR_STATE = -7       /* call order (e.g. no gauge field set) */
 };
 
-enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2 };
+enum { LQCD_PREC_F64 = 0, LQCD_PREC_F32 = 1, LQCD_PREC_F16 = 2, LQCD_PREC_BF16 = 3 };
 enum { LQCD_OP_HOP = 0, LQCD_OP_MHAT = 1 };
 enum { LQCD_SCHUR_R = 0, LQCD_SCHUR_RDAG = 1, LQCD_SCHUR_RINV = 2, LQCD_SCHUR_RINVDAG = 3,
        LQCD_SCHUR2_R = 4, LQCD_SCHUR2_RDAG = 5, LQCD_SCHUR2_RINV = 6, LQCD_SCHUR2_RINVDAG = 7 };
@@ -411,9 +414,9 @@ int lqcd_profile_times(lqcd_t h, int kernel_id, float* ms_out, int64_t cap, int6
  * batched slab solve and the global solve, each candidate timed on a
  * solve at `kappa` to 1e-10.  The choices stay with the handle; results
  * are the same up to rounding for every choice.  Synchronous.
- * lqcd_tune_read fills out (host int[9]) with hop block size [F64, F32,
- * F16], slab-solve sites per thread [F64, F32, F16], global-solve sites
- * per thread [F64, F32, F16]. */
+ * lqcd_tune_read fills out (host int[12]) with hop block size [F64, F32,
+ * F16, BF16], slab-solve sites per thread [F64, F32, F16, BF16], global-
+ * solve sites per thread [F64, F32, F16, BF16]. */
 int lqcd_autotune(lqcd_t h, int what, double kappa);
 int lqcd_tune_read(lqcd_t h, int* out);
 

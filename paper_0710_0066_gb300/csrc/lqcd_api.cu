@@ -36,7 +36,10 @@ int nbnd_of(const Geo& g) { return (g.nb / 2) * 2 * g.V3 * 6; }
 // complex entries of a second-level boundary field (first slices only)
 int nbnd2_of(const Geo& g1) { return g1.l0s ? (g1.L[0] / g1.l0s / 2) * g1.V3 * 6 : 0; }
 
-bool prec_ok(int p) { return p == LQCD_PREC_F64 || p == LQCD_PREC_F32 || p == LQCD_PREC_F16; }
+bool prec_ok(int p)
+{
+    return p == LQCD_PREC_F64 || p == LQCD_PREC_F32 || p == LQCD_PREC_F16 || p == LQCD_PREC_BF16;
+}
 
 SpinorF none()
 {
@@ -652,7 +655,7 @@ std::vector<unsigned char> md_key(const lqcd_ctx* h, const lqcd_hmc_params& p)
                              (double)p.step_scheme, (double)p.chrono,
                              (double)h->prof.on, (double)h->g1.l0s, (double)h->wait_limit,
                              (double)h->global_method, (double)h->sap_terms};
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < NPREC; ++q) {
         k.push_back((double)h->tune.hop_bs[q]);
         k.push_back((double)h->tune.solve_spt[q][0]);
         k.push_back((double)h->tune.solve_spt[q][1]);
@@ -858,7 +861,8 @@ GaugeF gauge_view(lqcd_ctx* h, int prec)
     g.Vh = h->g.Vh;
     g.v = (prec == PREC64 || prec == PRECDF) ? (const void*)h->U64
           : prec == PREC32                     ? (const void*)h->U32
-                                               : (const void*)h->U16;
+          : prec == PREC16                     ? (const void*)h->U16
+                                               : (const void*)(h->U16 + (size_t)24 * h->g.Vh);
     return g;
 }
 
@@ -971,7 +975,7 @@ int lqcd_create(lqcd_t* out, const int L[4], int l0, int bc_t, void* stream)
     LQ_CUDA(h, cudaMalloc(&h->U64, sizeof(double2) * 72 * Vh));
     LQ_CUDA(h, cudaMalloc(&h->U64_save, sizeof(double2) * 72 * Vh));
     LQ_CUDA(h, cudaMalloc(&h->U32, sizeof(float4) * 24 * Vh));
-    LQ_CUDA(h, cudaMalloc(&h->U16, sizeof(uint2) * 24 * Vh));
+    LQ_CUDA(h, cudaMalloc(&h->U16, sizeof(uint2) * 48 * Vh));  // fp16, then bf16
     h->f64.assign(NFIELD, nullptr);
     for (int k = 0; k < NFIELD; ++k) LQ_CUDA(h, cudaMalloc(&h->f64[k], sizeof(double2) * 24 * Vh));
     LQ_CUDA(h, cudaMalloc(&h->P, sizeof(double) * 32 * (size_t)g.V));
@@ -1565,7 +1569,7 @@ int lqcd_autotune(lqcd_t h, int what, double kappa)
     if (what & 1) {
         // k_hop: threads per block, per storage precision, timed on this lattice
         const int cand[3] = {64, 128, 256};
-        for (int prec = 0; prec < 3 && st == LQCD_OK; ++prec) {
+        for (int prec = 0; prec < NPREC && st == LQCD_OK; ++prec) {
             SpinorF in = sp64(A, 1, Vh), out = sp64(B, 0, Vh);
             if (prec != PREC64) {
                 auto lowview = [&](double2* buf, int par) {
@@ -1617,7 +1621,7 @@ int lqcd_autotune(lqcd_t h, int what, double kappa)
         // k_solve: sites per thread (CTAs per system), per precision, for the
         // batched slab solve and the global solve, timed on this lattice
         const int cand[3] = {1, 2, 4};
-        for (int prec = 0; prec < 3 && st == LQCD_OK; ++prec)
+        for (int prec = 0; prec < NPREC && st == LQCD_OK; ++prec)
             for (int kind = 0; kind < 2 && st == LQCD_OK; ++kind) {
                 // candidates interleaved over two rounds, the minimum per
                 // candidate kept; the default stays unless another is 3 % faster
@@ -1668,10 +1672,10 @@ int lqcd_tune_read(lqcd_t h, int* out)
 {
     CHECK_H(h);
     NEED(out, "null output");
-    for (int p = 0; p < 3; ++p) {
+    for (int p = 0; p < NPREC; ++p) {
         out[p] = h->tune.hop_bs[p];
-        out[3 + p] = h->tune.solve_spt[p][0];
-        out[6 + p] = h->tune.solve_spt[p][1];
+        out[NPREC + p] = h->tune.solve_spt[p][0];
+        out[2 * NPREC + p] = h->tune.solve_spt[p][1];
     }
     return LQCD_OK;
 }

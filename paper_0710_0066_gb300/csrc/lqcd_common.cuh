@@ -6,12 +6,15 @@
 //   single spinor  [parity][6][Vh]            float4  (two complex each)
 //   half spinor    [parity][3][Vh]            uint4   (four complex each)
 //                  + [parity][Vh] float scale (max |component| of the site)
+//   bf16 spinor    [parity][3][Vh]            uint4   (four complex each, no scale)
 //   double gauge   [mu][parity][9][Vh]        double2 (full 3x3)
 //   single gauge   [mu][parity][3][Vh]        float4  (rows 0 and 1)
 //   half gauge     [mu][parity][3][Vh]        uint2   (rows 0 and 1)
+//   bf16 gauge     the same, following the half gauge in one allocation
 // Row 2 of a compressed link is rebuilt as conj(row0 x row1) (SU(3)).
 // eo index of a site: lexicographic index / 2 (L3 is even).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -239,7 +242,10 @@ LQ_HD void accum_recon(int mu, int sg, const HalfSp<T>& w, Spinor<T>& acc)
 // on a spinor stored as df pairs (float4 = re.hi, im.hi, re.lo, im.lo per
 // complex, 16 bytes like a double2), for intermediates that never leave
 // the solver.  Internal, not API precisions.
-enum { PREC64 = 0, PREC32 = 1, PREC16 = 2, PRECDF = 3, PRECDS = 4 };
+// PRECBF: bfloat16 storage (FP32 arithmetic), no per-site scale.  The
+// four storage precisions have the ids of the C-ABI's LQCD_PREC_*.
+enum { PREC64 = 0, PREC32 = 1, PREC16 = 2, PRECBF = 3, PRECDF = 4, PRECDS = 5 };
+constexpr int NPREC = 4;
 
 struct SpinorF {  // one parity block of a spinor field in some precision
     void* v;      // double2* / float4* / uint4*
@@ -264,6 +270,10 @@ struct Real<PREC32> {
 };
 template <>
 struct Real<PREC16> {
+    typedef float T;
+};
+template <>
+struct Real<PRECBF> {
     typedef float T;
 };
 template <>
@@ -369,6 +379,40 @@ struct SpIO<PREC16, RO> {
             p[(size_t)k * f.N + i] = make_uint4(w[0], w[1], w[2], w[3]);
         }
         f.nrm[i] = mx;
+    }
+};
+
+template <bool RO>
+struct SpIO<PRECBF, RO> {
+    static __device__ __forceinline__ void load(const SpinorF& f, int i, Spinor<float>& s)
+    {
+        const uint4* p = (const uint4*)f.v;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 d = ldv<uint4, RO>(p + (size_t)k * f.N + i);
+            unsigned w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 v = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w[q]));
+                const int c = 4 * k + q;
+                s.c[c / 3][c % 3] = mk(v.x, v.y);
+            }
+        }
+    }
+    static __device__ __forceinline__ void store(const SpinorF& f, int i, const Spinor<float>& s)
+    {
+        uint4* p = (uint4*)f.v;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            unsigned w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = 4 * k + q;
+                __nv_bfloat162 hv = __floats2bfloat162_rn(s.c[c / 3][c % 3].re, s.c[c / 3][c % 3].im);
+                w[q] = *reinterpret_cast<unsigned*>(&hv);
+            }
+            p[(size_t)k * f.N + i] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
     }
 };
 
@@ -484,6 +528,37 @@ __device__ __forceinline__ void load_link<PREC16>(const GaugeF& g, int mu, int p
         uint2 d = __ldg(p + (size_t)k * g.Vh + i);
         float2 a = __half22float2(*reinterpret_cast<__half2*>(&d.x));
         float2 b = __half22float2(*reinterpret_cast<__half2*>(&d.y));
+        u.m[(2 * k) / 3][(2 * k) % 3] = mk(a.x, a.y);
+        u.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(b.x, b.y);
+    }
+    complete_row2(u);
+}
+
+// word k (elements 2k, 2k + 1 of rows 0-1) of link (mp = mu*2 + parity, i)
+// in the single, half and bfloat16 copies (the bfloat16 copy follows the
+// half one, 24 Vh words further)
+__device__ __forceinline__ void store_low_link_word(float4* U32, uint2* U16, int Vh, int mp, int k, int i, double xr,
+                                                    double xi, double yr, double yi)
+{
+    const size_t o = (size_t)mp * 3 * Vh + (size_t)k * Vh + i;
+    U32[o] = make_float4((float)xr, (float)xi, (float)yr, (float)yi);
+    __half2 hx = __floats2half2_rn((float)xr, (float)xi);
+    __half2 hy = __floats2half2_rn((float)yr, (float)yi);
+    U16[o] = make_uint2(*reinterpret_cast<unsigned*>(&hx), *reinterpret_cast<unsigned*>(&hy));
+    __nv_bfloat162 bx = __floats2bfloat162_rn((float)xr, (float)xi);
+    __nv_bfloat162 by = __floats2bfloat162_rn((float)yr, (float)yi);
+    U16[(size_t)24 * Vh + o] = make_uint2(*reinterpret_cast<unsigned*>(&bx), *reinterpret_cast<unsigned*>(&by));
+}
+
+template <>
+__device__ __forceinline__ void load_link<PRECBF>(const GaugeF& g, int mu, int par, int i, Su3<float>& u)
+{
+    const uint2* p = (const uint2*)g.v + (size_t)(mu * 2 + par) * 3 * g.Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint2 d = __ldg(p + (size_t)k * g.Vh + i);
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&d.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&d.y));
         u.m[(2 * k) / 3][(2 * k) % 3] = mk(a.x, a.y);
         u.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(b.x, b.y);
     }
@@ -718,8 +793,8 @@ struct Work;  // solver workspace (lqcd_solver.cu)
 
 // launch schedules picked by lqcd_autotune (defaults until it runs)
 struct Tune {
-    int hop_bs[3] = {128, 128, 128};           // k_hop threads per block, per precision
-    int solve_spt[3][2] = {{1, 1}, {1, 1}, {1, 1}};  // k_solve sites per thread [prec][block, global]
+    int hop_bs[NPREC] = {128, 128, 128, 128};  // k_hop threads per block, per precision
+    int solve_spt[NPREC][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}};  // k_solve sites per thread [prec][block, global]
 };
 
 struct lqcd_ctx {
@@ -733,7 +808,7 @@ struct lqcd_ctx {
     // internal gauge copies
     double2* U64 = nullptr;  // [4][2][9][Vh]
     float4* U32 = nullptr;   // [4][2][3][Vh]
-    uint2* U16 = nullptr;    // [4][2][3][Vh]
+    uint2* U16 = nullptr;    // [4][2][3][Vh] fp16, then [4][2][3][Vh] bf16
     double2* U64_save = nullptr;
     // double full-lattice spinor scratch fields [2][12][Vh]
     std::vector<double2*> f64;

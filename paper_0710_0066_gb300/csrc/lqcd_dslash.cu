@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(HOP_BS_MAX, 2) k_hop_df(Geo g, int mode, int d
 double hop_site_bytes(int prec, bool with_x)
 {
     const bool dbl = prec == PREC64 || prec == PRECDF;
-    const double sp = dbl ? 192.0 : prec == PREC32 ? 96.0 : 52.0;
+    const double sp = dbl ? 192.0 : prec == PREC32 ? 96.0 : prec == PREC16 ? 52.0 : 48.0;
     const double lk = dbl ? 144.0 : prec == PREC32 ? 48.0 : 24.0;
     return 2.0 * sp + 8.0 * lk + (with_x ? sp : 0.0);
 }
@@ -91,8 +91,10 @@ int hop_sweep(lqcd_ctx* h, int prec, int mode, int dag, int pout, int colour, Sp
         k_hop_df<<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
     else if (prec == PREC32)
         k_hop<PREC32><<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
-    else
+    else if (prec == PREC16)
         k_hop<PREC16><<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
+    else
+        k_hop<PRECBF><<<nb, bs, 0, h->stream>>>(g, mode, dag, pout, colour, out, in, U, a, x, c, nsites);
     h->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -67,15 +67,10 @@ __global__ void k_pack_gauge(double2* U64, float4* U32, uint2* U16, const double
     double2* d64 = U64 + (size_t)mp * 9 * Vh;
 #pragma unroll
     for (int k = 0; k < 9; ++k) d64[(size_t)k * Vh + i] = m[k];
-    float4* d32 = U32 + (size_t)mp * 3 * Vh;
-    uint2* d16 = U16 + (size_t)mp * 3 * Vh;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const double2 x = m[2 * k], y = m[2 * k + 1];
-        d32[(size_t)k * Vh + i] = make_float4((float)x.x, (float)x.y, (float)y.x, (float)y.y);
-        __half2 hx = __floats2half2_rn((float)x.x, (float)x.y);
-        __half2 hy = __floats2half2_rn((float)y.x, (float)y.y);
-        d16[(size_t)k * Vh + i] = make_uint2(*reinterpret_cast<unsigned*>(&hx), *reinterpret_cast<unsigned*>(&hy));
+        store_low_link_word(U32, U16, Vh, mp, k, i, x.x, x.y, y.x, y.y);
     }
 }
 
@@ -85,15 +80,10 @@ __global__ void k_refresh_low(const double2* U64, float4* U32, uint2* U16, int V
     if (t >= (int64_t)8 * Vh) return;
     const int mp = (int)(t / Vh), i = (int)(t % Vh);
     const double2* s64 = U64 + (size_t)mp * 9 * Vh;
-    float4* d32 = U32 + (size_t)mp * 3 * Vh;
-    uint2* d16 = U16 + (size_t)mp * 3 * Vh;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const double2 x = s64[(size_t)(2 * k) * Vh + i], y = s64[(size_t)(2 * k + 1) * Vh + i];
-        d32[(size_t)k * Vh + i] = make_float4((float)x.x, (float)x.y, (float)y.x, (float)y.y);
-        __half2 hx = __floats2half2_rn((float)x.x, (float)x.y);
-        __half2 hy = __floats2half2_rn((float)y.x, (float)y.y);
-        d16[(size_t)k * Vh + i] = make_uint2(*reinterpret_cast<unsigned*>(&hx), *reinterpret_cast<unsigned*>(&hy));
+        store_low_link_word(U32, U16, Vh, mp, k, i, x.x, x.y, y.x, y.y);
     }
 }
 
@@ -412,7 +402,12 @@ int convert_spinor(lqcd_ctx* h, SpinorF dst, int dprec, SpinorF src, int sprec, 
     if (sprec == a && dprec == b) k_convert<a, b><<<nb, BS, 0, h->stream>>>(dst, src, n)
     CV(PREC64, PREC32); else CV(PREC64, PREC16); else CV(PREC32, PREC64); else CV(PREC16, PREC64);
     else CV(PREC64, PREC64); else CV(PREC32, PREC32); else CV(PREC16, PREC16); else CV(PREC32, PREC16);
-    else CV(PREC16, PREC32);
+    else CV(PREC16, PREC32); else CV(PREC64, PRECBF); else CV(PRECBF, PREC64); else CV(PRECBF, PRECBF);
+    else CV(PREC32, PRECBF); else CV(PRECBF, PREC32);
+    else {
+        h->err = "convert_spinor: unsupported precision pair";
+        return LQCD_ERR_ARG;
+    }
 #undef CV
     LAUNCH_CHECK(h);
     return LQCD_OK;

@@ -474,15 +474,10 @@ __device__ void store_link_all(double2* U64, float4* U32, uint2* U16, int Vh, in
     double2* d64 = U64 + (size_t)mp * 9 * Vh;
 #pragma unroll
     for (int k = 0; k < 9; ++k) d64[(size_t)k * Vh + i] = make_double2(u.m[k / 3][k % 3].re, u.m[k / 3][k % 3].im);
-    float4* d32 = U32 + (size_t)mp * 3 * Vh;
-    uint2* d16 = U16 + (size_t)mp * 3 * Vh;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const cx<double> x = u.m[(2 * k) / 3][(2 * k) % 3], y = u.m[(2 * k + 1) / 3][(2 * k + 1) % 3];
-        d32[(size_t)k * Vh + i] = make_float4((float)x.re, (float)x.im, (float)y.re, (float)y.im);
-        __half2 hx = __floats2half2_rn((float)x.re, (float)x.im);
-        __half2 hy = __floats2half2_rn((float)y.re, (float)y.im);
-        d16[(size_t)k * Vh + i] = make_uint2(*reinterpret_cast<unsigned*>(&hx), *reinterpret_cast<unsigned*>(&hy));
+        store_low_link_word(U32, U16, Vh, mp, k, i, x.re, x.im, y.re, y.im);
     }
 }
 

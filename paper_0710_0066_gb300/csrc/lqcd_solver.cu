@@ -442,7 +442,7 @@ __device__ bool sap_bicgstab(const SolveArgs& A, int sys, int cin, unsigned& epo
                 load_spinor<P, false>(A.fzp[par], i, z);
                 sp_axpy(a, -kap, z);
                 store_spinor<P>(A.fv[par], i, a);
-                if (P == PREC16) load_spinor<P, false>(A.fv[par], i, a);
+                if (P == PREC16 || P == PRECBF) load_spinor<P, false>(A.fv[par], i, a);
                 load_spinor<P, false>(A.frh[par], i, rh);
                 cdot_acc(rh, a, qr, qi);
             }
@@ -491,7 +491,7 @@ __device__ bool sap_bicgstab(const SolveArgs& A, int sys, int cin, unsigned& epo
                 load_spinor<P, false>(A.fzs[par], i, z);
                 sp_axpy(a, -kap, z);
                 store_spinor<P>(A.ft[par], i, a);
-                if (P == PREC16) load_spinor<P, false>(A.ft[par], i, a);
+                if (P == PREC16 || P == PRECBF) load_spinor<P, false>(A.ft[par], i, a);
                 load_spinor<P, false>(A.fs[par], i, ss);
                 cdot_acc(a, ss, qr, qi);
                 qt += nrm_acc(a);
@@ -536,7 +536,7 @@ __device__ bool sap_bicgstab(const SolveArgs& A, int sys, int cin, unsigned& epo
                     }
                 store_spinor<PE>(A.fy[par], i, yy);
                 store_spinor<P>(A.fr[par], i, ss);
-                if (P == PREC16) load_spinor<P, false>(A.fr[par], i, ss);
+                if (P == PREC16 || P == PRECBF) load_spinor<P, false>(A.fr[par], i, ss);
                 load_spinor<P, false>(A.frh[par], i, rh);
                 cdot_acc(rh, ss, qr, qi);
                 qn += nrm_acc(ss);
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                             for (int c = 0; c < 3; ++c) a.c[s][c] = dinv * (rr.c[s][c] + k2 * a.c[s][c]);
                         store_spinor<P>(A.p, i, a);
                         if (chk) {
-                            if (P == PREC16) load_spinor<P, false>(A.p, i, a);
+                            if (P == PREC16 || P == PRECBF) load_spinor<P, false>(A.p, i, a);
 #pragma unroll
                             for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -1029,7 +1029,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 #pragma unroll
                             for (int c = 0; c < 3; ++c) a.c[s][c] = dg * pp.c[s][c] - k2 * a.c[s][c];
                         store_spinor<P>(A.v, i, a);
-                        if (P == PREC16) load_spinor<P, false>(A.v, i, a);
+                        if (P == PREC16 || P == PRECBF) load_spinor<P, false>(A.v, i, a);
                         load_spinor<P, false>(A.rh, i, rh);
                         cdot_acc(rh, a, qr, qi);
                     }
@@ -1099,7 +1099,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 #pragma unroll
                             for (int c = 0; c < 3; ++c) a.c[s][c] = dg * ss.c[s][c] - k2 * a.c[s][c];
                         store_spinor<P>(A.t, i, a);
-                        if (P == PREC16) load_spinor<P, false>(A.t, i, a);
+                        if (P == PREC16 || P == PRECBF) load_spinor<P, false>(A.t, i, a);
                         cdot_acc(a, ss, qr, qi);
                         qt += nrm_acc(a);
                     }
@@ -1158,7 +1158,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                             }
                         store_spinor<PE>(A.e, i, ee);
                         store_spinor<P>(A.r, i, ss);
-                        if (P == PREC16) load_spinor<P, false>(A.r, i, ss);
+                        if (P == PREC16 || P == PRECBF) load_spinor<P, false>(A.r, i, ss);
                         load_spinor<P, false>(A.rh, i, rh);
                         cdot_acc(rh, ss, qr, qi);
                         qn += nrm_acc(ss);
@@ -1326,7 +1326,7 @@ struct Work {
     int* outer = nullptr;
     int* h_status = nullptr;  // pinned mirror: status, outer, iters[NSYS_MAX]
     double* h_resid = nullptr;
-    int gmax[3] = {0, 0, 0};  // co-resident CTAs per precision
+    int gmax[NPREC] = {0, 0, 0, 0};  // co-resident CTAs per precision
     // the Schwarz-preconditioned global solve: 11 full-lattice vectors, each
     // sized for a double full field (allocated on first use)
     static constexpr int NSAP = 11;
@@ -1346,7 +1346,7 @@ static SpinorF full_view(double2* buf, int prec, int par, int Vh)
         f.v = (float4*)buf + (size_t)par * 6 * Vh;
     } else {
         f.v = (uint4*)buf + (size_t)par * 3 * Vh;
-        f.nrm = (float*)((uint4*)buf + (size_t)6 * Vh) + (size_t)par * Vh;
+        if (prec == PREC16) f.nrm = (float*)((uint4*)buf + (size_t)6 * Vh) + (size_t)par * Vh;
     }
     return f;
 }
@@ -1371,15 +1371,17 @@ int solver_init(lqcd_ctx* h)
     LQ_CUDA(h, cudaMalloc(&w->t64, sizeof(double2) * 12 * (size_t)Vh));
     // co-resident CTAs of a cooperative launch: the smaller occupancy of the
     // two variants of each precision
-    int occ[3], occs[3];
+    int occ[NPREC], occs[NPREC];
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_solve<PREC64, false>, SBS, 0));
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_solve<PREC32, false>, SBS, 0));
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_solve<PREC16, false>, SBS, 0));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_solve<PRECBF, false>, SBS, 0));
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[0], k_solve<PREC64, true>, SBS, 0));
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[1], k_solve<PREC32, true>, SBS, 0));
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[2], k_solve<PREC16, true>, SBS, 0));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[3], k_solve<PRECBF, true>, SBS, 0));
     int gm = 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < NPREC; ++k) {
         w->gmax[k] = std::max(1, std::min(occ[k], occs[k])) * h->num_sms;
         gm = std::max(gm, w->gmax[k]);
     }
@@ -1447,7 +1449,7 @@ void solver_free(lqcd_ctx* h)
 // cycle (each vector and the eight links moved once per phase)
 void solver_site_bytes(int prec, int method, double* inner, double* outer, int nsap)
 {
-    const double sp = prec == PREC64 ? 192.0 : prec == PREC32 ? 96.0 : 52.0;
+    const double sp = prec == PREC64 ? 192.0 : prec == PREC32 ? 96.0 : prec == PREC16 ? 52.0 : 48.0;
     const double lk = prec == PREC64 ? 1152.0 : prec == PREC32 ? 384.0 : 192.0;
     const double se = prec == PREC64 ? 192.0 : 96.0;
     // BiCGstab: 24 spinor passes, 4 half sweeps of links, solution r/w;
@@ -1540,9 +1542,11 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
         A.e = A.fy[0];  // the inner solution's even block
     }
     A.tol = tol;
-    A.inner_tol = prec == PREC64 ? 0.0 : prec == PREC32 ? 1e-5 : 2e-3;
+    // inner relative residual: a few unit roundoffs of the storage
+    // (bfloat16 keeps 8 significant bits, 2^-9 = 2e-3)
+    A.inner_tol = prec == PREC64 ? 0.0 : prec == PREC32 ? 1e-5 : prec == PREC16 ? 2e-3 : 8e-3;
     A.max_iter = max_iter;
-    A.max_outer = prec == PREC64 ? 8 : 40;
+    A.max_outer = prec == PREC64 ? 8 : prec == PRECBF ? 60 : 40;
     A.max_inner = prec == PREC64 ? max_iter : prec == PREC32 ? 4000 : 600;
     A.part = w->part;
     A.bar = w->bar;
@@ -1558,7 +1562,8 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     void* args[] = {&A};
     const void* fn = prec == PREC64 ? (sap ? (const void*)k_solve<PREC64, true> : (const void*)k_solve<PREC64, false>)
                      : prec == PREC32 ? (sap ? (const void*)k_solve<PREC32, true> : (const void*)k_solve<PREC32, false>)
-                                      : (sap ? (const void*)k_solve<PREC16, true> : (const void*)k_solve<PREC16, false>);
+                     : prec == PREC16 ? (sap ? (const void*)k_solve<PREC16, true> : (const void*)k_solve<PREC16, false>)
+                                      : (sap ? (const void*)k_solve<PRECBF, true> : (const void*)k_solve<PRECBF, false>);
     cudaEvent_t ev;
     prof_begin(h, 1, &ev);
     // cooperative launch (every CTA resident), expressed as a launch

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblqcd.so")
 
 OK, ERR_ARG, ERR_GEOM, ERR_NOCONVERGE, ERR_CUDA, ERR_NAN, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
-PREC_F64, PREC_F32, PREC_F16 = 0, 1, 2
+PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = 0, 1, 2, 3
 OP_HOP, OP_MHAT = 0, 1
 SCHUR_R, SCHUR_RDAG, SCHUR_RINV, SCHUR_RINVDAG = 0, 1, 2, 3
 SCHUR2_R, SCHUR2_RDAG, SCHUR2_RINV, SCHUR2_RINVDAG = 4, 5, 6, 7
@@ -235,12 +235,13 @@ def lqcd_autotune(h, what=3, kappa=0.15):
 
 
 def lqcd_tune_read(h):
-    out = (C.c_int * 9)()
+    out = (C.c_int * 12)()
     _check(h, load().lqcd_tune_read(h, out))
     v = list(out)
-    return {"hop_block_size": dict(zip(("f64", "f32", "f16"), v[0:3])),
-            "slab_solve_sites_per_thread": dict(zip(("f64", "f32", "f16"), v[3:6])),
-            "global_solve_sites_per_thread": dict(zip(("f64", "f32", "f16"), v[6:9]))}
+    names = ("f64", "f32", "f16", "bf16")
+    return {"hop_block_size": dict(zip(names, v[0:4])),
+            "slab_solve_sites_per_thread": dict(zip(names, v[4:8])),
+            "global_solve_sites_per_thread": dict(zip(names, v[8:12]))}
 
 
 def lqcd_set_global_solver(h, method, sap_terms=4):

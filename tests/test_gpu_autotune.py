@@ -25,7 +25,7 @@ def test_autotune_choices_and_results():
     x = syn.gaussian_spinor(olat.Vh, 6)
     b = syn.gaussian_spinor(olat.V, 7)
     before = {p: lat.dslash_eo(torch.from_numpy(x).cuda(), 0, 0.0, 0, lqcd.OP_HOP, p).cpu().numpy()
-              for p in (lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16)}
+              for p in (lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16, lqcd.PREC_BF16)}
     lqcd.lqcd_autotune(lat.h, 3, kappa)
     t = lqcd.lqcd_tune_read(lat.h)
     assert set(t["hop_block_size"].values()) <= {64, 128, 256}
@@ -34,7 +34,7 @@ def test_autotune_choices_and_results():
     for p, ref in before.items():
         out = lat.dslash_eo(torch.from_numpy(x).cuda(), 0, 0.0, 0, lqcd.OP_HOP, p).cpu().numpy()
         assert np.array_equal(out, ref)  # one thread per site: the schedule changes nothing
-    for p in (lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16):
+    for p in (lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16, lqcd.PREC_BF16):
         xs, it, rs = lat.block_solve(torch.from_numpy(b).cuda(), kappa, -1, 0, p, tol=1e-10)
         r = b - olat.W1(U, kappa, xs.cpu().numpy())
         assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(b)

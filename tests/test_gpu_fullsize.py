@@ -21,7 +21,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_0710_0066_gb300 import lqcd  # noqa: E402
 
-TOL = {lqcd.PREC_F64: 1e-13, lqcd.PREC_F32: 1e-6, lqcd.PREC_F16: 5e-3}
+TOL = {lqcd.PREC_F64: 1e-13, lqcd.PREC_F32: 1e-6, lqcd.PREC_F16: 5e-3, lqcd.PREC_BF16: 2e-2}
 
 
 def rel(a, b):
@@ -61,7 +61,7 @@ def test_solves_16x16x16x32():
     olat = O.Lattice(L, 4, -1)
     b = syn.gaussian_spinor(olat.V, 80)
     bd = torch.from_numpy(b).cuda()
-    for p in (lqcd.PREC_F32, lqcd.PREC_F16):
+    for p in (lqcd.PREC_F32, lqcd.PREC_F16, lqcd.PREC_BF16):
         x, it, rs = lat.block_solve(bd, kappa, -1, 0, p, tol=1e-10)
         r = b - olat.W1(Un, kappa, x.cpu().numpy())
         assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(b)

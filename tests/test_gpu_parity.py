@@ -1,7 +1,9 @@
 """GPU path (through the C-ABI) against the FP64 oracle, element by element.
 
 Tolerances (relative to the largest element of the reference):
-  double kernels 1e-12; single-precision stencil 1e-6; half storage 5e-3;
+  double kernels 1e-12; single-precision stencil 1e-6; half storage 5e-3
+  and bfloat16 storage 2e-2 (ten unit roundoffs of the storage: 2^-11 for
+  fp16, 2^-9 for bfloat16);
   solves: |b - W x| / |b| <= 1e-10 checked with the oracle's operator;
   forces 1e-5 (achieved ~1e-9 with double outer residuals); dH 1e-4.
 """
@@ -59,7 +61,8 @@ def test_gauge_roundtrip(setup):
     assert np.array_equal(lat.get_gauge().cpu().numpy(), U)
 
 
-@pytest.mark.parametrize("prec,tol", [(lqcd.PREC_F64, 1e-13), (lqcd.PREC_F32, 1e-6), (lqcd.PREC_F16, 5e-3)])
+@pytest.mark.parametrize("prec,tol", [(lqcd.PREC_F64, 1e-13), (lqcd.PREC_F32, 1e-6), (lqcd.PREC_F16, 5e-3),
+                                      (lqcd.PREC_BF16, 2e-2)])
 def test_dslash_eo(setup, prec, tol):
     lat, olat, U, kappa, seed = setup
     for parity in (0, 1):
@@ -75,7 +78,8 @@ def test_dslash_eo(setup, prec, tol):
         assert rel(out, ref) < tol
 
 
-@pytest.mark.parametrize("prec,tol", [(lqcd.PREC_F64, 1e-13), (lqcd.PREC_F32, 1e-6), (lqcd.PREC_F16, 5e-3)])
+@pytest.mark.parametrize("prec,tol", [(lqcd.PREC_F64, 1e-13), (lqcd.PREC_F32, 1e-6), (lqcd.PREC_F16, 5e-3),
+                                      (lqcd.PREC_BF16, 2e-2)])
 def test_block_dslash(setup, prec, tol):
     lat, olat, U, kappa, seed = setup
     x = syn.gaussian_spinor(olat.V, seed + 3)
@@ -86,7 +90,7 @@ def test_block_dslash(setup, prec, tol):
             assert rel(out, ref) < tol, (colour, dagger, rel(out, ref))
 
 
-@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16])
+@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16, lqcd.PREC_BF16])
 def test_block_solve_batched(setup, prec):
     lat, olat, U, kappa, seed = setup
     b = syn.gaussian_spinor(olat.V, seed + 4)
@@ -109,7 +113,7 @@ def test_block_solve_batched(setup, prec):
             assert rel(x, ref) < 1e-8
 
 
-@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16])
+@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16, lqcd.PREC_BF16])
 def test_solve_wilson(setup, prec):
     lat, olat, U, kappa, seed = setup
     for k in range(3):
@@ -121,7 +125,7 @@ def test_solve_wilson(setup, prec):
             assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(b), (it, rs)
 
 
-@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16])
+@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16, lqcd.PREC_BF16])
 def test_zero_source_solves(setup, prec):
     """the degenerate system b = 0: every slab system and the global solve
     return x = 0 exactly, without an inner iteration"""
@@ -150,7 +154,7 @@ def test_gauge_force_and_action(setup):
     assert rel(F, olat.gauge_force(U, 5.6)) < 1e-12
 
 
-@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16])
+@pytest.mark.parametrize("prec", [lqcd.PREC_F64, lqcd.PREC_F32, lqcd.PREC_F16, lqcd.PREC_BF16])
 def test_pf_force_w1(setup, prec):
     lat, olat, U, kappa, seed = setup
     phi = syn.gaussian_spinor(olat.V, seed + 6)
