@@ -343,10 +343,40 @@ __global__ void k_force_profile(Geo g, const double* F, double* out)
 // a scalar recurrence without transcendental functions (terms fall below
 // 1e-17 of the leading ones after about 6 + 3 |Q| steps); larger Q use the
 // closed form with the trigonometric functions.
+// 1 / n!, n = 0..40, for the series of expiq (constant memory: every
+// thread of a warp reads the same entry)
+constexpr double inv_factorial(int n) { return n <= 1 ? 1.0 : inv_factorial(n - 1) / n; }
+__constant__ double c_invfact[41] = {
+    inv_factorial(0),  inv_factorial(1),  inv_factorial(2),  inv_factorial(3),  inv_factorial(4),  inv_factorial(5),
+    inv_factorial(6),  inv_factorial(7),  inv_factorial(8),  inv_factorial(9),  inv_factorial(10), inv_factorial(11),
+    inv_factorial(12), inv_factorial(13), inv_factorial(14), inv_factorial(15), inv_factorial(16), inv_factorial(17),
+    inv_factorial(18), inv_factorial(19), inv_factorial(20), inv_factorial(21), inv_factorial(22), inv_factorial(23),
+    inv_factorial(24), inv_factorial(25), inv_factorial(26), inv_factorial(27), inv_factorial(28), inv_factorial(29),
+    inv_factorial(30), inv_factorial(31), inv_factorial(32), inv_factorial(33), inv_factorial(34), inv_factorial(35),
+    inv_factorial(36), inv_factorial(37), inv_factorial(38), inv_factorial(39), inv_factorial(40)};
+
+// Q^2 of a hermitian Q from its six distinct entries (real diagonal)
+__device__ __forceinline__ void herm_square(const Su3<double>& Q, Su3<double>& Q2)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        double d = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d += Q.m[i][k].re * Q.m[i][k].re + Q.m[i][k].im * Q.m[i][k].im;
+        Q2.m[i][i] = mk(d, 0.0);
+#pragma unroll
+        for (int j = i + 1; j < 3; ++j) {
+            const cx<double> v = Q.m[i][0] * Q.m[0][j] + Q.m[i][1] * Q.m[1][j] + Q.m[i][2] * Q.m[2][j];
+            Q2.m[i][j] = v;
+            Q2.m[j][i] = conjx(v);
+        }
+    }
+}
+
 __device__ void expiq(const Su3<double>& Q, Su3<double>& E)
 {
     Su3<double> Q2;
-    su3_mul(Q, Q, Q2);
+    herm_square(Q, Q2);
     const double c1 = 0.5 * (Q2.m[0][0].re + Q2.m[1][1].re + Q2.m[2][2].re);
     cx<double> f0, f1, f2;
     if (c1 >= 1e-12 && c1 <= 1.0) {
@@ -354,17 +384,18 @@ __device__ void expiq(const Su3<double>& Q, Su3<double>& E)
                                Q.m[0][1] * (Q.m[1][0] * Q.m[2][2] - Q.m[1][2] * Q.m[2][0]) +
                                Q.m[0][2] * (Q.m[1][0] * Q.m[2][1] - Q.m[1][1] * Q.m[2][0]);
         const double c0 = det.re;
-        double a0 = 1.0, a1 = 0.0, a2 = 0.0, w = 1.0;  // Q^n coordinates, 1 / n!
+        double a0 = 1.0, a1 = 0.0, a2 = 0.0;  // Q^n coordinates
         double r0 = 1.0, r1 = 0.0, r2 = 0.0, i0 = 0.0, i1 = 0.0, i2 = 0.0;
         const double qn = sqrt(2.0 * c1);  // Frobenius norm of Q: |Q^n| <= qn^n
-        double bound = 1.0;
+        double qp = 1.0;                    // qn^n
         for (int n = 1; n <= 40; ++n) {
             const double b0 = c0 * a2, b1 = a0 + c1 * a2, b2 = a1;
             a0 = b0;
             a1 = b1;
             a2 = b2;
-            w /= (double)n;
-            bound *= qn / (double)n;
+            const double w = c_invfact[n];
+            qp *= qn;
+            const double bound = qp * w;
             // i^n: 1, i, -1, -i
             switch (n & 3) {
                 case 0: r0 += w * a0; r1 += w * a1; r2 += w * a2; break;
@@ -452,7 +483,7 @@ __device__ void reunitarise(Su3<double>& u)
     double n0 = 0.0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) n0 += u.m[0][j].re * u.m[0][j].re + u.m[0][j].im * u.m[0][j].im;
-    n0 = 1.0 / sqrt(n0);
+    n0 = rsqrt(n0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) u.m[0][j] = n0 * u.m[0][j];
     cx<double> d = mk(0.0, 0.0);
@@ -463,7 +494,7 @@ __device__ void reunitarise(Su3<double>& u)
     double n1 = 0.0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) n1 += u.m[1][j].re * u.m[1][j].re + u.m[1][j].im * u.m[1][j].im;
-    n1 = 1.0 / sqrt(n1);
+    n1 = rsqrt(n1);
 #pragma unroll
     for (int j = 0; j < 3; ++j) u.m[1][j] = n1 * u.m[1][j];
     complete_row2(u);

@@ -229,12 +229,16 @@ __device__ __forceinline__ float4 caxpy2(float2 a, float4 x, float4 y)
     return make_float4(y.x + a.x * x.x - a.y * x.y, y.y + a.x * x.y + a.y * x.x, y.z + a.x * x.z - a.y * x.w,
                        y.w + a.x * x.w + a.y * x.z);
 }
-__device__ __forceinline__ void cdot2(float4 a, float4 b, double& re, double& im)
+// word-parallel dot products: each thread sums its few words in FP32 and
+// hands the sum to the FP64 reduction once (GB300 issues FP64 at a small
+// fraction of the FP32 rate; the single-precision inner solver's scalars
+// need no more than FP32 accuracy per thread)
+__device__ __forceinline__ void cdot2(float4 a, float4 b, float& re, float& im)
 {
-    re += (double)(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
-    im += (double)(a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z);
+    re += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    im += a.x * b.y - a.y * b.x + a.z * b.w - a.w * b.z;
 }
-__device__ __forceinline__ double nrm2w(float4 a) { return (double)(a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w); }
+__device__ __forceinline__ float nrm2w(float4 a) { return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w; }
 
 // single-precision spinor at site j of the combination y + a x of two
 // inner vectors (word by word, as the element-wise phases form it), and of
@@ -710,6 +714,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
             if (S.active && WORDS) {
                 const double sc = 1.0 / sqrt(S.rn2);
                 const double2* r6 = (const double2*)A.r64.v;
+                float qf = 0.f;
                 FOR_WORDS
                 {
                     const int k = f_ / A.nsite, i = base + (f_ % A.nsite);
@@ -721,8 +726,9 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                     W4(A.rh)[a] = w;
                     W4(A.p)[a] = w;
                     W4(A.e)[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    q += nrm2w(w);
+                    qf += nrm2w(w);
                 }
+                q = qf;
             } else if (S.active) {
                 const double sc = 1.0 / sqrt(S.rn2);
                 FOR_SITES
@@ -967,6 +973,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                     const float2 al = make_float2((float)S.alpha.x, (float)S.alpha.y);
                     const float2 om = make_float2((float)S.omega.x, (float)S.omega.y);
                     const float2 mom = make_float2(-om.x, -om.y);
+                    float fr = 0.f, fi = 0.f, fn = 0.f;
                     FOR_WORDS
                     {
                         WORD_ADDR;
@@ -974,9 +981,12 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                         W4(A.e)[a] = caxpy2(om, ss, caxpy2(al, W4(A.p)[a], W4(A.e)[a]));
                         const float4 rr = caxpy2(mom, W4(A.t)[a], ss);
                         W4(A.r)[a] = rr;
-                        cdot2(W4(A.rh)[a], rr, qr, qi);
-                        qn += nrm2w(rr);
+                        cdot2(W4(A.rh)[a], rr, fr, fi);
+                        fn += nrm2w(rr);
                     }
+                    qr = fr;
+                    qi = fi;
+                    qn = fn;
                     reduce_put(A, qr, qi, qn, 3, rb);
                     SYNC_OR_RETURN;
                     gather_own(A, sys, 3, red, rb);
@@ -1126,6 +1136,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                     const float2 al = make_float2((float)S.alpha.x, (float)S.alpha.y);
                     const float2 om = make_float2((float)S.omega.x, (float)S.omega.y);
                     const float2 mom = make_float2(-om.x, -om.y);
+                    float fr = 0.f, fi = 0.f, fn = 0.f;
                     FOR_WORDS
                     {
                         WORD_ADDR;
@@ -1133,9 +1144,12 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
                         W4(A.e)[a] = caxpy2(om, ss, caxpy2(al, W4(A.p)[a], W4(A.e)[a]));
                         const float4 rr = caxpy2(mom, W4(A.t)[a], ss);
                         W4(A.r)[a] = rr;
-                        cdot2(W4(A.rh)[a], rr, qr, qi);
-                        qn += nrm2w(rr);
+                        cdot2(W4(A.rh)[a], rr, fr, fi);
+                        fn += nrm2w(rr);
                     }
+                    qr = fr;
+                    qi = fi;
+                    qn = fn;
                 } else if (act2) {
                     const cx<T> al = mk((T)S.alpha.x, (T)S.alpha.y);
                     const cx<T> om = mk((T)S.omega.x, (T)S.omega.y);
