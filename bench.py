@@ -296,8 +296,9 @@ def run_ours(args):
     lat.set_gauge(U0)
     lqcd.lqcd_autotune(lat.h, 3, WL["kappa"])
     tune = lqcd.lqcd_tune_read(lat.h)
-    if args.global_solver == "sap":
-        lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP, args.sap_terms)
+    if args.global_solver != "bicgstab":
+        lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP if args.global_solver == "sap"
+                                    else lqcd.SOLVER_SAP_BLOCKS, args.sap_terms)
 
     def params(prec):
         return lqcd.hmc_params(WL["beta"], WL["kappa"], WL["tau"], WL["nlevels"], WL["scheme"], WL["nsteps"],
@@ -487,7 +488,9 @@ def run_ours(args):
                    "chronological_guesses": 0 if args.no_chrono else args.chrono,
                    "global_solver": ("Schwarz-preconditioned BiCGstab, %d series terms per slab solve"
                                      % args.sap_terms) if args.global_solver == "sap"
-                                    else "even-odd BiCGstab",
+                                    else ("Schwarz-preconditioned BiCGstab over 4^4 blocks in shared memory, "
+                                          "%d series terms per block solve" % args.sap_terms)
+                                    if args.global_solver == "sap-blocks" else "even-odd BiCGstab",
                    "dynamical_thermalisation": args.therm_fermion},
         "roofline": {"bound": "hbm", "kernel": "persistent batched solver (k_solve)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -744,16 +747,16 @@ def run_case(args):
         # the global solve with the Schwarz preconditioner (Sec. 3, S4
         # solver) for several series lengths of its slab solves; each timed
         # after one untimed solve
-        if hasattr(lqcd, "SOLVER_SAP"):
+        for tag, meth in (("sap", lqcd.SOLVER_SAP), ("sapb", lqcd.SOLVER_SAP_BLOCKS)):
             for nsap in args.sap_sweep:
-                lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP, nsap)
+                lqcd.lqcd_set_global_solver(lat.h, meth, nsap)
                 lat.solve(b, WL["kappa"], 0, prec, tol=WL["tol"])
                 lqcd.lqcd_profile_reset(lat.h)
                 x, it, rs = lat.solve(b, WL["kappa"], 0, prec, tol=WL["tol"])
                 n, ms, by = lqcd.lqcd_profile_read(lat.h, lqcd.KERNEL_SOLVER)
-                out["global_sap%d" % nsap] = {"iters": it, "resid": rs, "ms": ms, "alg_bytes": by,
-                                              "gbs": by / ms / 1e6}
-            lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_BICGSTAB, 0)
+                out["global_%s%d" % (tag, nsap)] = {"iters": it, "resid": rs, "ms": ms, "alg_bytes": by,
+                                                    "gbs": by / ms / 1e6}
+        lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_BICGSTAB, 0)
         print(json.dumps({"case": "solver", "lattice": "x".join(map(str, L)), "precision": args.precision,
                           **out}), flush=True)
         lat.close()
@@ -805,9 +808,10 @@ def main():
     ap.add_argument("--force-profile", action="store_true",
                     help="add the per-time-slice force profile of each term to the line")
     ap.add_argument("--detail", default=None, help="write per-trajectory records to this JSON file")
-    ap.add_argument("--global-solver", default="bicgstab", choices=["bicgstab", "sap"],
+    ap.add_argument("--global-solver", default="bicgstab", choices=["bicgstab", "sap", "sap-blocks"],
                     help="inner iteration of the whole-lattice solves: even-odd BiCGstab, or BiCGstab "
-                         "with the Schwarz preconditioner over the x0-slabs (Sec. 3, S4 solver)")
+                         "with the Schwarz preconditioner (Sec. 3, S4 solver) over the x0-slabs or over "
+                         "4-D blocks")
     ap.add_argument("--sap-terms", type=int, default=4,
                     help="geometric-series terms of every slab solve of the Schwarz preconditioner")
     ap.add_argument("--sap-sweep", type=int, nargs="*", default=[1, 2, 4, 8],

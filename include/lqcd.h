@@ -86,7 +86,7 @@ enum { LQCD_SCHUR_R = 0, LQCD_SCHUR_RDAG = 1, LQCD_SCHUR_RINV = 2, LQCD_SCHUR_RI
 enum { LQCD_TERM_W1 = 0, LQCD_TERM_SCHUR = 1, LQCD_TERM_W2 = 2, LQCD_TERM_SCHUR2 = 3,
        LQCD_TERM_S2 = 4, LQCD_TERM_S1 = 5 };
 enum { LQCD_EO_APPLY = 0, LQCD_EO_SOLVE = 1 };
-enum { LQCD_SOLVER_BICGSTAB = 0, LQCD_SOLVER_SERIES = 1, LQCD_SOLVER_SAP = 2 };
+enum { LQCD_SOLVER_BICGSTAB = 0, LQCD_SOLVER_SERIES = 1, LQCD_SOLVER_SAP = 2, LQCD_SOLVER_SAP_BLOCKS = 3 };
 enum { LQCD_MAX_LEVELS = 5 };
 enum { LQCD_LF = 0, LQCD_SW = 1 };
 
@@ -410,7 +410,8 @@ int lqcd_profile_times(lqcd_t h, int kernel_id, float* ms_out, int64_t cap, int6
  * gauge field (the paper has no counterpart; its code ran on CPUs):
  * what & 1: threads per block of the hopping sweep (64 / 128 / 256), per
  * storage precision; what & 2: sites per thread of the persistent solver
- * (1 / 2 / 4, i.e. CTAs per system), per precision, separately for the
+ * (1 / 2, i.e. CTAs per system, or 0: every co-resident CTA with an equal
+ * contiguous share of the sites), per precision, separately for the
  * batched slab solve and the global solve, each candidate timed on a
  * solve at `kappa` to 1e-10.  The choices stay with the handle; results
  * are the same up to rounding for every choice.  Synchronous.
@@ -419,6 +420,11 @@ int lqcd_profile_times(lqcd_t h, int kernel_id, float* ms_out, int64_t cap, int6
  * solve sites per thread [F64, F32, F16, BF16]. */
 int lqcd_autotune(lqcd_t h, int what, double kappa);
 int lqcd_tune_read(lqcd_t h, int* out);
+/* Sets the persistent solver's schedule of every precision and both solve
+ * kinds to `spt` (1 or 2 sites per thread, 0 every co-resident CTA with an
+ * equal share of the sites), as lqcd_autotune would pick it.  Results are
+ * the same up to rounding.  Errors: LQCD_ERR_ARG (spt outside 0..2). */
+int lqcd_set_solver_schedule(lqcd_t h, int spt);
 
 /* Inner iteration of every whole-lattice solve of the handle (the S4
  * solver of Sec. 3: lqcd_solve_wilson, R^-1 / R^-dag and the boundary-term
@@ -435,11 +441,20 @@ int lqcd_tune_read(lqcd_t h, int* out);
  *     reduced correction y_e.  The series needs the slab operator's
  *     spectral radius below one to precondition well (it always gives a
  *     valid, if weaker, preconditioner).
- * Selecting LQCD_SOLVER_SAP allocates its workspace (11 full-lattice
- * vectors, 2.1 KB per lattice site) on the current device; it is kept
- * until lqcd_destroy.
+ *   LQCD_SOLVER_SAP_BLOCKS: the same Schwarz-preconditioned BiCGstab with
+ *     the cycle taken over small 4-D blocks instead of the x0-slabs: block
+ *     extent 4 in every direction whose L is a multiple of 4, else 2;
+ *     blocks coloured by the parity of their block coordinates; each
+ *     block's even-odd reduced operator inverted by sap_terms terms of its
+ *     geometric series (the paper does not fix the blocks of its S4
+ *     preconditioner).  Every block is solved by one CTA with the block's
+ *     links and vectors in shared memory.
+ * Selecting LQCD_SOLVER_SAP or LQCD_SOLVER_SAP_BLOCKS allocates their
+ * workspace (11 full-lattice vectors, 2.1 KB per lattice site) on the
+ * current device; it is kept until lqcd_destroy.
  * Errors: LQCD_ERR_ARG (other methods, sap_terms out of range),
- * LQCD_ERR_CUDA (allocation). */
+ * LQCD_ERR_CUDA (allocation); a later solve returns LQCD_ERR_GEOM for an
+ * odd extent with LQCD_SOLVER_SAP_BLOCKS. */
 int lqcd_set_global_solver(lqcd_t h, int method, int sap_terms);
 
 /* Limit of one barrier wait inside the persistent solver, in GPU clock

@@ -741,7 +741,7 @@ int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const do
     h->iter_count += it;
     h->site_iters += sit + ssit + asit;
     h->hop_sites += solver_hops_per_iter(SOLVER_BICGSTAB, 0) * sit + solver_hops_per_iter(SOLVER_SERIES, 0) * ssit +
-                    (int64_t)solver_hops_per_iter(SOLVER_SAP, h->sap_terms) * asit;
+                    (int64_t)solver_hops_per_iter(h->global_method, h->sap_terms) * asit;
     // kernel times of this replay (the stream is synchronised); the solver's
     // algorithmic bytes follow from the replay's iteration sums
     if (!h->prof.graph_recs.empty()) {
@@ -757,7 +757,8 @@ int md_graph(lqcd_ctx* h, const lqcd_hmc_params& p, const PfFields& pf, const do
         double ba;
         solver_site_bytes(p.precision, SOLVER_BICGSTAB, &bi, &bo);
         solver_site_bytes(p.precision, SOLVER_SERIES, &bs, &bo);
-        solver_site_bytes(p.precision, SOLVER_SAP, &ba, &bo, h->sap_terms);
+        solver_site_bytes(p.precision, h->global_method == SOLVER_SAPB ? SOLVER_SAPB : SOLVER_SAP, &ba, &bo,
+                          h->sap_terms);
         h->prof.bytes[1] += (double)sit * bi + (double)ssit * bs + (double)asit * ba + (double)osit * bo;
     }
     return st;
@@ -1618,9 +1619,10 @@ int lqcd_autotune(lqcd_t h, int what, double kappa)
         }
     }
     if ((what & 2) && st == LQCD_OK) {
-        // k_solve: sites per thread (CTAs per system), per precision, for the
+        // k_solve: sites per thread (CTAs per system; 0: every co-resident
+        // CTA with an equal share of the sites), per precision, for the
         // batched slab solve and the global solve, timed on this lattice
-        const int cand[3] = {1, 2, 4};
+        const int cand[3] = {1, 2, 0};
         for (int prec = 0; prec < NPREC && st == LQCD_OK; ++prec)
             for (int kind = 0; kind < 2 && st == LQCD_OK; ++kind) {
                 // candidates interleaved over two rounds, the minimum per
@@ -1668,6 +1670,17 @@ int lqcd_autotune(lqcd_t h, int what, double kappa)
     return st;
 }
 
+int lqcd_set_solver_schedule(lqcd_t h, int spt)
+{
+    CHECK_H(h);
+    if (spt < 0 || spt > 2) {
+        h->err = "solver schedule: 0, 1 or 2 sites per thread";
+        return LQCD_ERR_ARG;
+    }
+    for (int p = 0; p < NPREC; ++p) h->tune.solve_spt[p][0] = h->tune.solve_spt[p][1] = spt;
+    return LQCD_OK;
+}
+
 int lqcd_tune_read(lqcd_t h, int* out)
 {
     CHECK_H(h);
@@ -1711,17 +1724,19 @@ int lqcd_force_profile(lqcd_t h, const double* F, double* out)
 int lqcd_set_global_solver(lqcd_t h, int method, int sap_terms)
 {
     CHECK_H(h);
-    if (method != LQCD_SOLVER_BICGSTAB && method != LQCD_SOLVER_SAP) {
-        h->err = "global solver: LQCD_SOLVER_BICGSTAB or LQCD_SOLVER_SAP";
+    if (method != LQCD_SOLVER_BICGSTAB && method != LQCD_SOLVER_SAP && method != LQCD_SOLVER_SAP_BLOCKS) {
+        h->err = "global solver: LQCD_SOLVER_BICGSTAB, LQCD_SOLVER_SAP or LQCD_SOLVER_SAP_BLOCKS";
         return LQCD_ERR_ARG;
     }
-    if (method == LQCD_SOLVER_SAP && (sap_terms < 0 || sap_terms > 64)) {
+    const bool sap = method == LQCD_SOLVER_SAP || method == LQCD_SOLVER_SAP_BLOCKS;
+    if (sap && (sap_terms < 0 || sap_terms > 64)) {
         h->err = "global solver: 0 <= sap_terms <= 64";
         return LQCD_ERR_ARG;
     }
-    if (method == LQCD_SOLVER_SAP) LQ_TRY(solver_sap_alloc(h));
-    h->global_method = method == LQCD_SOLVER_SAP ? SOLVER_SAP : SOLVER_BICGSTAB;
-    if (method == LQCD_SOLVER_SAP) h->sap_terms = sap_terms;
+    if (sap) LQ_TRY(solver_sap_alloc(h));
+    h->global_method = method == LQCD_SOLVER_SAP ? SOLVER_SAP : method == LQCD_SOLVER_SAP_BLOCKS ? SOLVER_SAPB
+                                                                                                : SOLVER_BICGSTAB;
+    if (sap) h->sap_terms = sap_terms;
     return LQCD_OK;
 }
 

@@ -973,15 +973,17 @@ void solver_site_bytes(int prec, int method, double* inner, double* outer, int n
 // `method`: inner iteration, BiCGstab or the geometric series (which needs
 // the spectral radius of kappa^2 H_eo H_oe / diag below one)
 // SOLVER_SAP (whole-lattice solves only): BiCGstab on M preconditioned by
-// one multiplicative Schwarz cycle over the red / black x0-slabs
-enum { SOLVER_BICGSTAB = 0, SOLVER_SERIES = 1, SOLVER_SAP = 2 };
+// one multiplicative Schwarz cycle over the red / black x0-slabs;
+// SOLVER_SAPB: the same over red / black 4-D blocks of at most 4^4 sites,
+// each block solved by one CTA in shared memory
+enum { SOLVER_BICGSTAB = 0, SOLVER_SERIES = 1, SOLVER_SAP = 2, SOLVER_SAPB = 3 };
 // half-lattice hopping site updates per inner iteration and even site of
 // the system: BiCGstab 4, series 2, Schwarz-preconditioned BiCGstab two
 // applications of (red and black slab solves of nsap series terms, 2 + 2
 // nsap half sweeps, and M, 2 half sweeps)
 inline int solver_hops_per_iter(int method, int nsap)
 {
-    return method == SOLVER_SERIES ? 2 : method == SOLVER_SAP ? 4 * (2 + nsap) : 4;
+    return method == SOLVER_SERIES ? 2 : (method == SOLVER_SAP || method == SOLVER_SAPB) ? 4 * (2 + nsap) : 4;
 }
 // `guess`: 1 if x_e holds an initial guess (its residual is computed in
 // double before the first inner cycle), 0 to start from x = 0

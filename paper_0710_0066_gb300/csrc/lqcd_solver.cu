@@ -54,6 +54,7 @@ struct SolveArgs {
     int method;   // SOLVER_BICGSTAB or SOLVER_SERIES (inner iteration)
     int guess;    // 1: x holds an initial guess on entry, 0: start from x = 0
     int nsys, cps;
+    int chunk;  // sites of one system handled by one CTA (the last CTA may get fewer)
     int slab0, slabstep;
     int nsite;
     GaugeF U64, UP;
@@ -80,7 +81,11 @@ struct SolveArgs {
     // parity block; fy (the inner solution) in the precision of e, whose
     // even block it is
     double kappa;
-    int nsap;  // geometric-series terms of every slab solve of the preconditioner
+    int nsap;  // geometric-series terms of every block solve of the preconditioner
+    // SOLVER_SAPB: 4-D Schwarz blocks of extents bk[mu] (2 or 4, lbk = log2),
+    // nbk[mu] = L[mu] / bk[mu] blocks per direction, nblk in all, bvh sites
+    // of one parity in a block
+    int bk[4], lbk[4], nbk[4], nblk, bvh;
     SpinorF fr[2], frh[2], fp[2], fv[2], fs[2], ft[2], fzp[2], fzs[2], fw1[2], fw2[2], fy[2];
 };
 
@@ -213,7 +218,10 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 }
 __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
-#define FOR_SITES for (int j_ = cin * SBS + (int)threadIdx.x; j_ < A.nsite; j_ += A.cps * SBS)
+// sites of a system are split into contiguous chunks, one per CTA
+#define FOR_SITES                                                                                   \
+    for (int j_ = cin * A.chunk + (int)threadIdx.x, je_ = min(A.nsite, (cin + 1) * A.chunk); j_ < je_; \
+         j_ += SBS)
 // element-wise phases of the single-precision inner solver run over 16-byte
 // words (one float4 = two complex components) instead of whole sites: six
 // times the parallelism and few live registers per thread
@@ -374,6 +382,316 @@ __device__ bool sap_apply(const SolveArgs& A, int sys, int cin, unsigned& epoch,
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Schwarz preconditioner over small 4-D blocks (SOLVER_SAPB)
+//
+// The same multiplicative cycle as sap_apply (all blocks of colour 0, then
+// all blocks of colour 1 with the source corrected by the hops from the
+// colour-0 blocks, each block solve the truncated geometric series of the
+// even-odd reduced block operator), on blocks of bk[0] x .. x bk[3] sites
+// (bk[mu] = 4 or 2, so a block starts on an even site and its local
+// checkerboard is the global one).  A block's colour is the parity of the
+// sum of its block coordinates.  One CTA solves one block at a time with
+// the block's links and the vectors of its series in shared memory, so the
+// series needs __syncthreads only; the system's barrier is met once per
+// colour (2 per application instead of 4 nsap + 5).
+// ---------------------------------------------------------------------------
+constexpr int SAPB_BVH = SBS / 2;  // largest block: 2 SBS / 2 sites, 4^4
+
+// shared-memory bytes of one CTA: links (rows 0-1 of U_mu(y), both
+// parities) and three block vectors (odd source, even iterate, odd
+// intermediate)
+template <class T>
+constexpr int sapb_smem_bytes()
+{
+    return (4 * 2 * 6 + 3 * 12) * SAPB_BVH * (int)sizeof(cx<T>);
+}
+
+// local coordinates of the block site with parity p and local eo index n
+// (local lexicographic order with y3 fastest, as the lattice's)
+__device__ __forceinline__ void blk_coords(const SolveArgs& A, int p, int n, int y[4])
+{
+    const int l = 2 * n;
+    y[3] = l & (A.bk[3] - 1);
+    int t = l >> A.lbk[3];
+    y[2] = t & (A.bk[2] - 1);
+    t >>= A.lbk[2];
+    y[1] = t & (A.bk[1] - 1);
+    y[0] = t >> A.lbk[1];
+    y[3] += (y[0] + y[1] + y[2] + y[3] + p) & 1;
+}
+
+// block coordinates of the j-th block of colour c; false if the j-th block
+// has the other colour (when nbk[3] is odd, all blocks are enumerated)
+__device__ __forceinline__ bool blk_of(const SolveArgs& A, int c, int j, int B[4])
+{
+    int t = j;
+    if ((A.nbk[3] & 1) == 0) {
+        const int h3 = A.nbk[3] >> 1;
+        const int b3 = t % h3;
+        t /= h3;
+        B[2] = t % A.nbk[2];
+        t /= A.nbk[2];
+        B[1] = t % A.nbk[1];
+        B[0] = t / A.nbk[1];
+        B[3] = 2 * b3 + ((B[0] + B[1] + B[2] + c) & 1);
+        return true;
+    }
+    B[3] = t % A.nbk[3];
+    t /= A.nbk[3];
+    B[2] = t % A.nbk[2];
+    t /= A.nbk[2];
+    B[1] = t % A.nbk[1];
+    B[0] = t / A.nbk[1];
+    return ((B[0] + B[1] + B[2] + B[3]) & 1) == c;
+}
+
+// The hopping term inside one block (hops leaving the block dropped) at
+// output site (pout, n), from the block vector `in` of parity 1 - pout in
+// shared memory, computed by a pair of threads: thread s (0 or 1) projects
+// spin row s of every neighbour, applies the link and accumulates output
+// spins s (up) and 2 + s (lo).  The lower half of (1 + sg gamma_mu) psi
+// mixes the two rows for mu = 1, 2; those parts belong to the partner's
+// lower spin and are exchanged by one shuffle at the end.  Both threads of
+// a pair take every branch together (the spin row is data, not control).
+template <class T>
+__device__ __forceinline__ void blk_hop_pair(const SolveArgs& A, const cx<T>* Ls, const cx<T>* in, int pout, int n,
+                                             int s, bool on, cx<T> up[3], cx<T> lo[3])
+{
+    cx<T> ot[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) up[i] = lo[i] = ot[i] = mk(T(0), T(0));
+    if (on) {
+        const int bvh = A.bvh;
+        int y[4];
+        blk_coords(A, pout, n, y);
+        const int l = ((y[0] * A.bk[1] + y[1]) * A.bk[2] + y[2]) * A.bk[3] + y[3];
+        const T sig = s ? T(-1) : T(1);
+        int stride = 1;
+#pragma unroll
+        for (int mu = 3; mu >= 0; --mu) {
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {  // forward, backward
+                const bool inside = dir == 0 ? (y[mu] + 1 < A.bk[mu]) : (y[mu] > 0);
+                if (inside) {
+                    const int nn = (dir == 0 ? l + stride : l - stride) >> 1;
+                    // forward: U_mu(y) at (pout, n); backward: U_mu(y - mu) at (1 - pout, nn)
+                    const cx<T>* lp = Ls + (size_t)((mu * 2 + (dir == 0 ? pout : 1 - pout)) * 6) * bvh +
+                                      (dir == 0 ? n : nn);
+                    Su3<T> u;
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) u.m[e / 3][e % 3] = lp[e * bvh];
+                    complete_row2(u);
+                    const int sg = dir == 0 ? -1 : +1;
+                    // row s of the projection: h = p_s - sg a_s with a_s = p_(2+s)
+                    // (mu 0), i p_(3-s) (mu 1), sig p_(3-s) (mu 2), sig i p_(2+s) (mu 3)
+                    const int q = (mu == 0 || mu == 3) ? 2 + s : 3 - s;
+                    cx<T> h[3];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const cx<T> ps = in[(s * 3 + i) * bvh + nn];
+                        const cx<T> pq = in[(q * 3 + i) * bvh + nn];
+                        cx<T> a;
+                        if (mu == 0) a = pq;
+                        else if (mu == 1) a = mul_i(pq);
+                        else if (mu == 2) a = sig * pq;
+                        else a = sig * mul_i(pq);
+                        h[i] = sg < 0 ? ps + a : ps - a;
+                    }
+                    cx<T> w[3];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        w[i] = dir == 0 ? u.m[i][0] * h[0] + u.m[i][1] * h[1] + u.m[i][2] * h[2]
+                                        : cjmul(u.m[0][i], h[0]) + cjmul(u.m[1][i], h[1]) + cjmul(u.m[2][i], h[2]);
+                    // upper spin s += w; lower spin 2 + t += sg l_t with l_t =
+                    // -w_t (mu 0), i w_(1-t) (mu 1), sig_t w_(1-t) (mu 2), i sig_t w_t (mu 3)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        up[i] = up[i] + w[i];
+                        if (mu == 0) lo[i] = sg < 0 ? lo[i] + w[i] : lo[i] - w[i];
+                        else if (mu == 3) lo[i] = lo[i] + (T)sg * sig * mul_i(w[i]);
+                        else if (mu == 1) ot[i] = ot[i] + (T)sg * mul_i(w[i]);
+                        else ot[i] = ot[i] - (T)sg * sig * w[i];
+                    }
+                }
+            }
+            stride *= A.bk[mu];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        lo[i].re += __shfl_xor_sync(0xffffffffu, ot[i].re, 1);
+        lo[i].im += __shfl_xor_sync(0xffffffffu, ot[i].im, 1);
+    }
+}
+
+// z = K^-1 q with the 4-D block cycle above.  Full-lattice vectors in P;
+// two system barriers.
+template <int P>
+__device__ bool sapb_apply(const SolveArgs& A, int sys, int cin, unsigned& epoch, const SpinorF* q, const SpinorF* z)
+{
+    typedef typename Real<P>::T T;
+    extern __shared__ __align__(16) unsigned char sapb_dyn[];
+    const int bvh = A.bvh;
+    cx<T>* Ls = (cx<T>*)sapb_dyn;             // [4][2][6][bvh]
+    cx<T>* so = Ls + 4 * 2 * 6 * SAPB_BVH;    // [12][bvh] odd source
+    cx<T>* ev = so + 12 * SAPB_BVH;           // [12][bvh] even source, then iterate
+    cx<T>* od = ev + 12 * SAPB_BVH;           // [12][bvh] odd intermediate
+    const T kap = (T)A.kappa, k2 = (T)A.k2;
+    const int tid = threadIdx.x;
+    // pair mapping of the series phases: site n = tid / 2, spin row s = tid & 1
+    const int pn = tid >> 1, ps = tid & 1;
+    const bool pon = pn < bvh;
+    const int nloop = (A.nbk[3] & 1) == 0 ? A.nblk / 2 : A.nblk;
+    for (int c = 0; c < 2; ++c) {
+        for (int j = cin; j < nloop; j += A.cps) {
+            int B[4];
+            if (!blk_of(A, c, j, B)) continue;  // uniform over the CTA
+            // ---- links of the block and the source, one thread per site:
+            // src = q, plus kappa times the hops from colour-0 blocks (c = 1)
+            for (int t = tid; t < 2 * bvh; t += SBS) {
+                const int p = t >= bvh ? 1 : 0, n = t - p * bvh;
+                int y[4], x[4];
+                blk_coords(A, p, n, y);
+#pragma unroll
+                for (int mu = 0; mu < 4; ++mu) x[mu] = B[mu] * A.bk[mu] + y[mu];
+                const int lex = lex_of(A.g, x);
+                const int gi = lex >> 1;
+                Spinor<T> src, ext;
+                load_spinor<P, false>(q[p], gi, src);
+                sp_zero(ext);
+                int stride = 1;
+#pragma unroll
+                for (int mu = 3; mu >= 0; --mu) {
+                    Su3<T> u;
+                    load_link<P>(A.UP, mu, p, gi, u);
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) Ls[((mu * 2 + p) * 6 + e) * bvh + n] = u.m[e / 3][e % 3];
+                    if (c == 1) {
+                        // forward hop leaving the block
+                        if (y[mu] == A.bk[mu] - 1) {
+                            const int Bn = B[mu] + 1 == A.nbk[mu] ? 0 : B[mu] + 1;
+                            if (((c - B[mu] + Bn) & 1) == 0) {
+                                const bool wrap = x[mu] == A.g.L[mu] - 1;
+                                const int nl = wrap ? lex + stride - A.g.L[mu] * stride : lex + stride;
+                                Spinor<T> pz;
+                                load_spinor<P, false>(z[1 - p], nl >> 1, pz);
+                                HalfSp<T> hh, w;
+                                project(mu, -1, pz, hh);
+                                su3_mul_half(u, hh, w);
+                                if (mu == 0 && wrap && A.g.bc_t < 0) {
+#pragma unroll
+                                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                                        for (int b = 0; b < 3; ++b) w.c[a][b] = -w.c[a][b];
+                                }
+                                accum_recon(mu, -1, w, ext);
+                            }
+                        }
+                        // backward hop leaving the block
+                        if (y[mu] == 0) {
+                            const int Bn = B[mu] == 0 ? A.nbk[mu] - 1 : B[mu] - 1;
+                            if (((c - B[mu] + Bn) & 1) == 0) {
+                                const bool wrap = x[mu] == 0;
+                                const int nl = wrap ? lex - stride + A.g.L[mu] * stride : lex - stride;
+                                Spinor<T> pz;
+                                load_spinor<P, false>(z[1 - p], nl >> 1, pz);
+                                Su3<T> ub;
+                                load_link<P>(A.UP, mu, 1 - p, nl >> 1, ub);
+                                HalfSp<T> hh, w;
+                                project(mu, +1, pz, hh);
+                                su3_dagmul_half(ub, hh, w);
+                                if (mu == 0 && wrap && A.g.bc_t < 0) {
+#pragma unroll
+                                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                                        for (int b = 0; b < 3; ++b) w.c[a][b] = -w.c[a][b];
+                                }
+                                accum_recon(mu, +1, w, ext);
+                            }
+                        }
+                    }
+                    stride *= A.g.L[mu];
+                }
+                if (c == 1) sp_axpy(ext, kap, src);  // ext <- src + kappa ext
+                else ext = src;
+                cx<T>* dst = p ? so : ev;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) dst[k * bvh + n] = ext.c[k / 3][k % 3];
+            }
+            __syncthreads();
+            // ---- be = src_e + kappa H_eo src_o (the pair's two spins kept
+            // in registers); the series starts from u_0 = be
+            cx<T> be[2][3];
+            {
+                cx<T> up[3], lo[3];
+                blk_hop_pair<T>(A, Ls, so, 0, pn, ps, pon, up, lo);
+                if (pon) {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        be[0][i] = ev[(ps * 3 + i) * bvh + pn] + kap * up[i];
+                        be[1][i] = ev[((2 + ps) * 3 + i) * bvh + pn] + kap * lo[i];
+                        ev[(ps * 3 + i) * bvh + pn] = be[0][i];
+                        ev[((2 + ps) * 3 + i) * bvh + pn] = be[1][i];
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- u <- be + kappa^2 H_eo H_oe u, nsap times
+            for (int it = 0; it < A.nsap; ++it) {
+                cx<T> up[3], lo[3];
+                blk_hop_pair<T>(A, Ls, ev, 1, pn, ps, pon, up, lo);
+                if (pon) {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        od[(ps * 3 + i) * bvh + pn] = up[i];
+                        od[((2 + ps) * 3 + i) * bvh + pn] = lo[i];
+                    }
+                }
+                __syncthreads();
+                blk_hop_pair<T>(A, Ls, od, 0, pn, ps, pon, up, lo);
+                if (pon) {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        ev[(ps * 3 + i) * bvh + pn] = be[0][i] + k2 * up[i];
+                        ev[((2 + ps) * 3 + i) * bvh + pn] = be[1][i] + k2 * lo[i];
+                    }
+                }
+                __syncthreads();
+            }
+            // ---- y_o = src_o + kappa H_oe u (into the odd intermediate)
+            {
+                cx<T> up[3], lo[3];
+                blk_hop_pair<T>(A, Ls, ev, 1, pn, ps, pon, up, lo);
+                if (pon) {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        od[(ps * 3 + i) * bvh + pn] = so[(ps * 3 + i) * bvh + pn] + kap * up[i];
+                        od[((2 + ps) * 3 + i) * bvh + pn] = so[((2 + ps) * 3 + i) * bvh + pn] + kap * lo[i];
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- z on the block (y_e = u, y_o), one thread per site
+            for (int t = tid; t < 2 * bvh; t += SBS) {
+                const int p = t >= bvh ? 1 : 0, n = t - p * bvh;
+                int y[4], x[4];
+                blk_coords(A, p, n, y);
+#pragma unroll
+                for (int mu = 0; mu < 4; ++mu) x[mu] = B[mu] * A.bk[mu] + y[mu];
+                const cx<T>* srcv = p ? od : ev;
+                Spinor<T> out;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) out.c[k / 3][k % 3] = srcv[k * bvh + n];
+                store_spinor<P>(z[p], lex_of(A.g, x) >> 1, out);
+            }
+            __syncthreads();
+        }
+        SAP_SYNC;
+    }
+    return true;
+}
+
 #define FOR_FULL_SITES \
     for (int t_ = cin * SBS + (int)threadIdx.x; t_ < 2 * A.g.Vh; t_ += A.cps * SBS)
 
@@ -435,7 +753,9 @@ __device__ bool sap_bicgstab(const SolveArgs& A, int sys, int cin, unsigned& epo
     for (;;) {
         if (S.idone) break;
         // zp = K^-1 p ; v = M zp ; <rh, v>
-        if (!sap_apply<P>(A, sys, cin, epoch, A.fp, A.fzp)) return false;
+        if (!(A.method == SOLVER_SAPB ? sapb_apply<P>(A, sys, cin, epoch, A.fp, A.fzp)
+                                      : sap_apply<P>(A, sys, cin, epoch, A.fp, A.fzp)))
+            return false;
         {
             double qr = 0.0, qi = 0.0;
             FOR_FULL_SITES
@@ -484,7 +804,9 @@ __device__ bool sap_bicgstab(const SolveArgs& A, int sys, int cin, unsigned& epo
             SAP_SYNC;
         }
         // zs = K^-1 s ; t = M zs ; <t, s>, <t, t>
-        if (!sap_apply<P>(A, sys, cin, epoch, A.fs, A.fzs)) return false;
+        if (!(A.method == SOLVER_SAPB ? sapb_apply<P>(A, sys, cin, epoch, A.fs, A.fzs)
+                                      : sap_apply<P>(A, sys, cin, epoch, A.fs, A.fzs)))
+            return false;
         {
             double qr = 0.0, qi = 0.0, qt = 0.0;
             FOR_FULL_SITES
@@ -1314,7 +1636,7 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
         if (final_flag == F_NAN) atomicCAS(A.sticky, 0, LQCD_ERR_NAN);
         if (final_flag == F_MAXIT) atomicCAS(A.sticky, 0, LQCD_ERR_NOCONVERGE);
         atomicAdd(A.acc, (unsigned long long)S.it);
-        atomicAdd(A.acc + (A.method == SOLVER_SERIES ? 3 : A.method == SOLVER_SAP ? 4 : 1),
+        atomicAdd(A.acc + (A.method == SOLVER_SERIES ? 3 : (A.method == SOLVER_SAP || A.method == SOLVER_SAPB) ? 4 : 1),
                   (unsigned long long)S.it * (unsigned long long)A.nsite);
         atomicAdd(A.acc + 2, (unsigned long long)outer * (unsigned long long)A.nsite);
     }
@@ -1394,10 +1716,17 @@ int solver_init(lqcd_ctx* h)
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_solve<PREC32, false>, SBS, 0));
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_solve<PREC16, false>, SBS, 0));
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_solve<PRECBF, false>, SBS, 0));
-    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[0], k_solve<PREC64, true>, SBS, 0));
-    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[1], k_solve<PREC32, true>, SBS, 0));
-    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[2], k_solve<PREC16, true>, SBS, 0));
-    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[3], k_solve<PRECBF, true>, SBS, 0));
+    // the Schwarz variants run with the 4-D block preconditioner's dynamic
+    // shared memory (opted in here, counted in their occupancy)
+    const int smd = sapb_smem_bytes<double>(), smf = sapb_smem_bytes<float>();
+    LQ_CUDA(h, cudaFuncSetAttribute(k_solve<PREC64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smd));
+    LQ_CUDA(h, cudaFuncSetAttribute(k_solve<PREC32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf));
+    LQ_CUDA(h, cudaFuncSetAttribute(k_solve<PREC16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf));
+    LQ_CUDA(h, cudaFuncSetAttribute(k_solve<PRECBF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smf));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[0], k_solve<PREC64, true>, SBS, smd));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[1], k_solve<PREC32, true>, SBS, smf));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[2], k_solve<PREC16, true>, SBS, smf));
+    LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[3], k_solve<PRECBF, true>, SBS, smf));
     int gm = 0;
     for (int k = 0; k < NPREC; ++k) {
         w->gmax[k] = std::max(1, std::min(occ[k], occs[k])) * h->num_sms;
@@ -1477,8 +1806,13 @@ void solver_site_bytes(int prec, int method, double* inner, double* outer, int n
     // spinor passes and (4 + 2 nsap) half sweeps of links each (slab solves
     // of both colours, the face update, the Wilson matrix), plus 28 passes
     // of vector updates and the solution r/w of both parities
+    // 4-D block preconditioner: per application the source and the links
+    // are read and the block solution written once (the series runs in
+    // shared memory); the Wilson matrix and vector updates as above
     if (method == SOLVER_SAP)
         *inner = 2.0 * (17.0 + 5.0 * nsap) * sp + 28.0 * sp + 2.0 * (4.0 + 2.0 * nsap) * lk + 4.0 * se;
+    else if (method == SOLVER_SAPB)
+        *inner = 2.0 * (4.0 * sp + lk) + 4.0 * lk + 28.0 * sp + 4.0 * se;
     else
         *inner = method == SOLVER_SERIES ? 6.0 * sp + 2.0 * lk : 24.0 * sp + 4.0 * lk + 2.0 * se;
     *outer = (192.0 + 3.0 * sp + se) + (2.0 * 192.0 + se) + (2.0 * 192.0 + 1152.0) + (4.0 * 192.0 + 1152.0);
@@ -1498,6 +1832,32 @@ int solver_sap_alloc(lqcd_ctx* h)
     return LQCD_OK;
 }
 
+// block extents of the 4-D Schwarz preconditioner: 4 where L[mu] is a
+// multiple of 4, else 2 (every extent is even)
+static int sapb_geometry(lqcd_ctx* h, SolveArgs& A)
+{
+    const Geo& g = h->g;
+    int bvol = 1;
+    A.nblk = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (g.L[mu] % 2) {
+            h->err = "the block Schwarz preconditioner needs even extents";
+            return LQCD_ERR_GEOM;
+        }
+        A.bk[mu] = g.L[mu] % 4 == 0 ? 4 : 2;
+        A.lbk[mu] = A.bk[mu] == 4 ? 2 : 1;
+        A.nbk[mu] = g.L[mu] / A.bk[mu];
+        A.nblk *= A.nbk[mu];
+        bvol *= A.bk[mu];
+    }
+    A.bvh = bvol / 2;
+    if (A.bvh > SAPB_BVH) {
+        h->err = "Schwarz block larger than one CTA";
+        return LQCD_ERR_GEOM;
+    }
+    return LQCD_OK;
+}
+
 int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2* x_e, const double2* b_e,
              double tol, int max_iter, int* iters_sys, double* resid_sys, double diag, int method, int guess)
 {
@@ -1511,12 +1871,17 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     A.method = method;
     A.guess = guess;
     A.kappa = kappa;
-    const bool sap = method == SOLVER_SAP;
+    const bool sap = method == SOLVER_SAP || method == SOLVER_SAPB;
     if (sap && (mode != MODE_ALL || diag != 1.0)) {
         h->err = "the Schwarz-preconditioned solve is a whole-lattice solve of M";
         return LQCD_ERR_ARG;
     }
     A.nsap = h->sap_terms;
+    int smem = 0;
+    if (method == SOLVER_SAPB) {
+        LQ_TRY(sapb_geometry(h, A));
+        smem = prec == PREC64 ? sapb_smem_bytes<double>() : sapb_smem_bytes<float>();
+    }
     if (mode == MODE_INTRA) {
         A.nsys = colour < 0 ? g.nb : g.nb / 2;
         A.slab0 = colour < 0 ? 0 : colour;
@@ -1533,8 +1898,12 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
         return LQCD_ERR_GEOM;
     }
     const int want = (A.nsite + SBS - 1) / SBS;
-    const int spt = std::max(1, h->tune.solve_spt[prec][mode == MODE_INTRA ? 0 : 1]);
-    A.cps = std::max(1, std::min(w->gmax[prec] / A.nsys, (want + spt - 1) / spt));
+    // CTAs per system: spt sites per thread, or (spt = 0) every co-resident
+    // CTA, so that all SMs carry the same share (at least 32 sites per CTA)
+    const int spt = h->tune.solve_spt[prec][mode == MODE_INTRA ? 0 : 1];
+    A.cps = spt <= 0 ? std::max(1, std::min(w->gmax[prec] / A.nsys, (A.nsite + 31) / 32))
+                     : std::max(1, std::min(w->gmax[prec] / A.nsys, (want + spt - 1) / spt));
+    A.chunk = (A.nsite + A.cps - 1) / A.cps;
     const int G = A.cps * A.nsys;
     A.U64 = gauge_view(h, PREC64);
     A.UP = gauge_view(h, prec);
@@ -1592,6 +1961,7 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(SBS);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = h->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

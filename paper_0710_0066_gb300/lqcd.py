@@ -25,7 +25,7 @@ SCHUR_R, SCHUR_RDAG, SCHUR_RINV, SCHUR_RINVDAG = 0, 1, 2, 3
 SCHUR2_R, SCHUR2_RDAG, SCHUR2_RINV, SCHUR2_RINVDAG = 4, 5, 6, 7
 TERM_W1, TERM_SCHUR, TERM_W2, TERM_SCHUR2, TERM_S2, TERM_S1 = 0, 1, 2, 3, 4, 5
 EO_APPLY, EO_SOLVE = 0, 1
-SOLVER_BICGSTAB, SOLVER_SERIES, SOLVER_SAP = 0, 1, 2
+SOLVER_BICGSTAB, SOLVER_SERIES, SOLVER_SAP, SOLVER_SAP_BLOCKS = 0, 1, 2, 3
 MAX_LEVELS = 5
 LF, SW = 0, 1
 KERNEL_HOP, KERNEL_SOLVER, KERNEL_FORCE, KERNEL_GAUGE, KERNEL_BLAS = 0, 1, 2, 3, 4
@@ -39,7 +39,7 @@ EXPORTS = [
     "lqcd_gauge_action_static", "lqcd_force_profile", "lqcd_set_subslabs", "lqcd_subblock_dslash",
     "lqcd_subblock_solve_batched", "lqcd_subblock_eo", "lqcd_pf_force_eo", "lqcd_link_update",
     "lqcd_autotune", "lqcd_tune_read", "lqcd_profile_times", "lqcd_set_wait_limit",
-    "lqcd_set_global_solver",
+    "lqcd_set_global_solver", "lqcd_set_solver_schedule",
 ]
 
 
@@ -136,6 +136,7 @@ def load():
         "lqcd_gauge_action_static": [C.POINTER(C.c_int * 4), vp, d, vp, vp],
         "lqcd_force_profile": [vp, vp, vp],
         "lqcd_set_wait_limit": [vp, i64],
+        "lqcd_set_solver_schedule": [vp, i],
         "lqcd_set_global_solver": [vp, i, i],
     }
     for name, args in sig.items():
@@ -232,6 +233,10 @@ def lqcd_block_solve_batched(h, x, b, kappa, colour=-1, dagger=0, precision=PREC
 
 def lqcd_autotune(h, what=3, kappa=0.15):
     return _check(h, load().lqcd_autotune(h, int(what), float(kappa)))
+
+
+def lqcd_set_solver_schedule(h, spt):
+    return _check(h, load().lqcd_set_solver_schedule(h, int(spt)))
 
 
 def lqcd_tune_read(h):

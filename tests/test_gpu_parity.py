@@ -210,7 +210,7 @@ def test_md_matches_oracle():
 
 @pytest.mark.parametrize("pf_init", [0, 1])
 def test_hmc_trajectory_matches_oracle(pf_init):
-    """BASELINE config 1: 4^4, two slabs of thickness 2, kappa = 0.15,
+    """The small 4^4 workload: two slabs of thickness 2, kappa = 0.15,
     beta = 5.6, one leapfrog trajectory tau = 0.5 in 10 steps"""
     L, l0, kappa, beta = (4, 4, 4, 4), 2, 0.15, 5.6
     U = syn.random_links(L, 0.3, 2007)

@@ -4,7 +4,10 @@ with even-odd and Schwarz preconditioning) against the FP64 oracle.
 The handle's global solver (lqcd_set_global_solver) is switched to
 LQCD_SOLVER_SAP: BiCGstab on M with one multiplicative Schwarz cycle over
 the red / black x0-slabs as right preconditioner, every slab solve a
-truncated geometric series of its even-odd reduced operator.  Checked:
+truncated geometric series of its even-odd reduced operator; or to
+LQCD_SOLVER_SAP_BLOCKS, the same cycle over red / black 4-D blocks of at
+most 4^4 sites, each block solved by one CTA in shared memory.  Checked,
+for both:
 the solution of M x = b and of M^dag x = b by the oracle's residual
 (<= 1e-10 relative) in all three inner precisions and for several series
 lengths (0 terms: the first-order block inverse), R^-1 and R^-dag of the
@@ -29,6 +32,10 @@ from paper_0710_0066_gb300 import lqcd  # noqa: E402
 # synthetic field of the solver tests; 8 x 4 x 2 x 6 with slabs of 2 (odd-
 # sized slab faces, a ragged tail of the CTA loops)
 GEOMS = [((16, 8, 8, 8), 4, 0.6, 0.156), ((8, 4, 2, 6), 2, 0.3, 0.14)]
+# slab blocks, and 4-D blocks (4^4 on 16 x 8^3; 4 x 4 x 2 x 2 on 8 x 4 x 2 x 6,
+# three blocks along x3: an odd block count, two same-colour neighbours)
+METHODS = [lqcd.SOLVER_SAP, lqcd.SOLVER_SAP_BLOCKS]
+MIDS = ["slabs", "blocks"]
 
 
 def cuda(x):
@@ -51,13 +58,15 @@ def setup(request):
     lat.close()
 
 
+@pytest.mark.parametrize("method", METHODS, ids=MIDS)
 @pytest.mark.parametrize("prec,nsap", [(lqcd.PREC_F64, 4), (lqcd.PREC_F32, 4), (lqcd.PREC_F16, 4),
-                                       (lqcd.PREC_F32, 0), (lqcd.PREC_F32, 1), (lqcd.PREC_F32, 8)])
+                                       (lqcd.PREC_BF16, 4), (lqcd.PREC_F32, 0), (lqcd.PREC_F32, 1),
+                                       (lqcd.PREC_F32, 8)])
 @pytest.mark.parametrize("dagger", [0, 1])
-def test_sap_solve_residual(setup, prec, nsap, dagger):
+def test_sap_solve_residual(setup, method, prec, nsap, dagger):
     lat, olat, U, kappa = setup
     b = syn.gaussian_spinor(olat.V, 2201 + dagger)
-    lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP, nsap)
+    lqcd.lqcd_set_global_solver(lat.h, method, nsap)
     try:
         x, it, rs = lat.solve(cuda(b), kappa, dagger, prec, tol=1e-10)
     finally:
@@ -71,13 +80,14 @@ def test_sap_solve_residual(setup, prec, nsap, dagger):
     assert rel(x, x2.cpu().numpy()) < 1e-8
 
 
-def test_sap_needs_fewer_iterations(setup):
+@pytest.mark.parametrize("method", METHODS, ids=MIDS)
+def test_sap_needs_fewer_iterations(setup, method):
     """the preconditioned operator is better conditioned: fewer (more
     expensive) iterations than the plain even-odd BiCGstab"""
     lat, olat, U, kappa = setup
     b = cuda(syn.gaussian_spinor(olat.V, 2203))
     it_plain = lat.solve(b, kappa, 0, lqcd.PREC_F64, tol=1e-10)[1]
-    lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP, 4)
+    lqcd.lqcd_set_global_solver(lat.h, method, 4)
     try:
         it_sap = lat.solve(b, kappa, 0, lqcd.PREC_F64, tol=1e-10)[1]
     finally:
@@ -85,12 +95,13 @@ def test_sap_needs_fewer_iterations(setup):
     assert it_sap < it_plain, (it_sap, it_plain)
 
 
+@pytest.mark.parametrize("method", METHODS, ids=MIDS)
 @pytest.mark.parametrize("op", [lqcd.SCHUR_RINV, lqcd.SCHUR_RINVDAG])
-def test_sap_schur_inverse(setup, op):
+def test_sap_schur_inverse(setup, op, method):
     lat, olat, U, kappa = setup
     c = syn.gaussian_complex(olat.bnd_shape(), 2204 + op)
     ref = olat.schur(U, kappa, c, op, route=1, tol=1e-13)
-    lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP, 4)
+    lqcd.lqcd_set_global_solver(lat.h, method, 4)
     try:
         out = lat.schur(cuda(c), kappa, op, lqcd.PREC_F32, tol=1e-12)
     finally:
@@ -98,10 +109,11 @@ def test_sap_schur_inverse(setup, op):
     assert rel(out, ref) < 1e-9
 
 
-def test_sap_schur_force(setup):
+@pytest.mark.parametrize("method", METHODS, ids=MIDS)
+def test_sap_schur_force(setup, method):
     lat, olat, U, kappa = setup
     phi = syn.gaussian_complex(olat.bnd_shape(), 2206)
-    lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP, 4)
+    lqcd.lqcd_set_global_solver(lat.h, method, 4)
     try:
         S, F = lat.pf_force(cuda(phi), kappa, lqcd.TERM_SCHUR, lqcd.PREC_F32, tol=1e-12)
     finally:
@@ -111,11 +123,12 @@ def test_sap_schur_force(setup):
     assert rel(F, Fo) < 1e-5
 
 
-def test_sap_trajectory_matches_oracle():
+@pytest.mark.parametrize("method", METHODS, ids=MIDS)
+def test_sap_trajectory_matches_oracle(method):
     L, l0, kappa, beta = (4, 4, 4, 4), 2, 0.15, 5.6
     U = syn.random_links(L, 0.3, 2207)
     lat = lqcd.Lattice(L, l0, -1)
-    lqcd.lqcd_set_global_solver(lat.h, lqcd.SOLVER_SAP, 4)
+    lqcd.lqcd_set_global_solver(lat.h, method, 4)
     olat = O.Lattice(L, l0, -1)
     prm = lqcd.hmc_params(beta, kappa, 0.5, 2, (lqcd.SW, lqcd.LF), [2, 4], 0, 0, 1, roll=1,
                           precision=lqcd.PREC_F32, tol=1e-11, use_graph=1, chrono=1)
@@ -131,7 +144,8 @@ def test_sap_trajectory_matches_oracle():
 
 def test_set_global_solver_validates():
     lat = lqcd.Lattice((4, 4, 4, 4), 2, -1)
-    for method, n in ((lqcd.SOLVER_SERIES, 4), (7, 4), (lqcd.SOLVER_SAP, -1), (lqcd.SOLVER_SAP, 65)):
+    for method, n in ((lqcd.SOLVER_SERIES, 4), (7, 4), (lqcd.SOLVER_SAP, -1), (lqcd.SOLVER_SAP, 65),
+                      (lqcd.SOLVER_SAP_BLOCKS, -1), (lqcd.SOLVER_SAP_BLOCKS, 65)):
         with pytest.raises(lqcd.LqcdError) as e:
             lqcd.lqcd_set_global_solver(lat.h, method, n)
         assert e.value.status == lqcd.ERR_ARG

@@ -249,7 +249,7 @@ def test_det_factorisation_dense(L, l0, bc):
 
 
 def test_det_factorisation_4x4x4x4():
-    """BASELINE config-1 geometry (4^4, l0=2): dense det M / det W1 against
+    """The small 4^4 workload geometry (l0=2): dense det M / det W1 against
     det R, with R assembled from dense blocks; the oracle's R matches it on
     random vectors"""
     L = (4, 4, 4, 4)
