@@ -964,6 +964,7 @@ int lqcd_create(lqcd_t* out, const int L[4], int l0, int bc_t, void* stream)
     g.bc_t = bc_t;
     g.Sh = l0 * g.V3 / 2;
     g.l0s = 0;
+    geo_finish(g);
     h->g1 = g;
     h->stream = (cudaStream_t)stream;
     *out = h;
@@ -1044,6 +1045,7 @@ int lqcd_set_subslabs(lqcd_t h, int l0s)
         return LQCD_ERR_GEOM;
     }
     h->g1.l0s = l0s;
+    geo_finish(h->g1);
     h->g = h->g1;
     return LQCD_OK;
 }

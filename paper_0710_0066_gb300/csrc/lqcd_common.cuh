@@ -37,7 +37,31 @@ struct Geo {
     int l0, nb, bc_t;
     int Sh;   // sites of one parity in one slab = l0 * V3 / 2
     int l0s;  // iterated decomposition: sub-slab thickness l0 / 2, or 0
+    // index helpers set by geo_finish: log2 of L1, L2, L3 when all three are
+    // powers of two (lg[0] = 1), and bit t of face / sface set when slice t
+    // starts a slab / sub-slab (used when L0 <= 64)
+    int lg[4];
+    unsigned long long face, sface;
 };
+
+// fills the index helpers of g from L, l0 and l0s
+inline void geo_finish(Geo& g)
+{
+    int ok = 1;
+    for (int mu = 1; mu < 4; ++mu) {
+        int k = 0;
+        while ((1 << k) < g.L[mu]) ++k;
+        g.lg[mu] = k;
+        if ((1 << k) != g.L[mu]) ok = 0;
+    }
+    g.lg[0] = ok;
+    g.face = g.sface = 0ull;
+    if (g.L[0] <= 64)
+        for (int t = 0; t < g.L[0]; ++t) {
+            if (g.l0 > 0 && t % g.l0 == 0) g.face |= 1ull << t;
+            if (g.l0s > 0 && t % g.l0s == 0) g.sface |= 1ull << t;
+        }
+}
 
 // Geometry of the second level of the iterated decomposition (Sec. 1): the
 // sub-slabs of thickness l0s play the part of the slabs, so every block
@@ -49,19 +73,29 @@ inline Geo sub_geo(const Geo& g)
     s.nb = g.L[0] / g.l0s;
     s.Sh = g.l0s * g.V3 / 2;
     s.l0s = 0;
+    geo_finish(s);
     return s;
 }
 
 // coordinates of eo index i of parity p
 LQ_HD void eo_coords(const Geo& g, int p, int i, int x[4])
 {
-    int j = 2 * i;
-    x[3] = j % g.L[3];
-    int t = j / g.L[3];
-    x[2] = t % g.L[2];
-    t /= g.L[2];
-    x[1] = t % g.L[1];
-    x[0] = t / g.L[1];
+    const int j = 2 * i;
+    if (g.lg[0]) {  // L1, L2, L3 powers of two: shifts and masks
+        x[3] = j & (g.L[3] - 1);
+        int t = j >> g.lg[3];
+        x[2] = t & (g.L[2] - 1);
+        t >>= g.lg[2];
+        x[1] = t & (g.L[1] - 1);
+        x[0] = t >> g.lg[1];
+    } else {
+        x[3] = j % g.L[3];
+        int t = j / g.L[3];
+        x[2] = t % g.L[2];
+        t /= g.L[2];
+        x[1] = t % g.L[1];
+        x[0] = t / g.L[1];
+    }
     x[3] += (x[0] + x[1] + x[2] + x[3] + p) & 1;
 }
 
@@ -581,10 +615,12 @@ enum { MODE_ALL = 0, MODE_INTRA = 1, MODE_CROSS = 2, MODE_INTRA2 = 3, MODE_CROSS
 LQ_HD bool t_hop_kept(const Geo& g, int mode, int xf)
 {
     if (mode == MODE_ALL) return true;
-    const bool slab_face = (xf % g.l0) == 0;
+    const bool small = g.L[0] <= 64;
+    const int xn = xf >= g.L[0] ? xf - g.L[0] : xf;  // xf = L0 is the face at 0
+    const bool slab_face = small ? ((g.face >> xn) & 1ull) != 0 : (xf % g.l0) == 0;
     if (mode == MODE_INTRA) return !slab_face;
     if (mode == MODE_CROSS) return slab_face;
-    const bool sub_face = g.l0s > 0 && (xf % g.l0s) == 0;
+    const bool sub_face = g.l0s > 0 && (small ? ((g.sface >> xn) & 1ull) != 0 : (xf % g.l0s) == 0);
     if (mode == MODE_INTRA2) return !sub_face;
     return sub_face && !slab_face;
 }

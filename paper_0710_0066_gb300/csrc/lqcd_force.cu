@@ -794,6 +794,8 @@ extern "C" int lqcd_gauge_action_static(const int L[4], const double* U, double 
     g.nb = L[0];
     g.bc_t = 1;
     g.Sh = g.V3 / 2;
+    g.l0s = 0;
+    geo_finish(g);
     cudaStream_t s = (cudaStream_t)stream;
     k_plaq_static<<<(unsigned)nblocks, STATIC_SITES_PER_BLOCK, 0, s>>>(g, (const double2*)U, part);
     k_plaq_static_final<<<1, 1024, 0, s>>>(part, (int)nblocks, out, beta, 1.0 / (18.0 * (double)V));
