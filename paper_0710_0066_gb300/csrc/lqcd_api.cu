@@ -659,6 +659,7 @@ std::vector<unsigned char> md_key(const lqcd_ctx* h, const lqcd_hmc_params& p)
         k.push_back((double)h->tune.hop_bs[q]);
         k.push_back((double)h->tune.solve_spt[q][0]);
         k.push_back((double)h->tune.solve_spt[q][1]);
+        k.push_back((double)h->tune.cluster_series);
     }
     for (int j = 0; j < LQCD_MAX_LEVELS; ++j) {
         k.push_back((double)p.scheme[j]);
@@ -1670,6 +1671,13 @@ int lqcd_autotune(lqcd_t h, int what, double kappa)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+int lqcd_set_cluster_series(lqcd_t h, int enable)
+{
+    CHECK_H(h);
+    h->tune.cluster_series = enable ? 1 : 0;
+    return LQCD_OK;
 }
 
 int lqcd_set_solver_schedule(lqcd_t h, int spt)

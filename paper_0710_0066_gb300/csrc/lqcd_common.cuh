@@ -831,6 +831,7 @@ struct Work;  // solver workspace (lqcd_solver.cu)
 struct Tune {
     int hop_bs[NPREC] = {128, 128, 128, 128};  // k_hop threads per block, per precision
     int solve_spt[NPREC][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}};  // k_solve sites per thread [prec][block, global]
+    int cluster_series = 0;  // single-precision slab series on thread-block clusters (opt-in: slower on GB300)
 };
 
 struct lqcd_ctx {

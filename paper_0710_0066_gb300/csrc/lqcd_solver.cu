@@ -22,6 +22,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "lqcd_common.cuh"
 
 namespace {
@@ -1648,6 +1650,431 @@ __global__ void __launch_bounds__(SBS, P == PREC64 ? 1 : 2) k_solve(SolveArgs A)
 #undef W4
 #undef SYNC_OR_RETURN
 
+// ---------------------------------------------------------------------------
+// The geometric series of the slab systems on thread-block clusters
+//
+// One cluster of CL_CTAS CTAs per system (one x0-slab or sub-slab), one CTA
+// per SM.  The single-precision inner vectors of the series (the iterate p,
+// the odd intermediate H_oe p and the inner source r) live in the CTAs'
+// shared memory, each CTA holding a contiguous chunk of the system's sites;
+// the hopping term reads a neighbour's spinor from the shared memory of the
+// CTA that owns it (distributed shared memory), and the CTAs of a system
+// meet at an mbarrier handshake inside the cluster instead of the global
+// counter of k_solve.  The outer double defect correction (double-float
+// residual sweeps on the double fields) is that of k_solve.  Every wait is
+// bounded: a CTA that gives up records LQCD_ERR_TIMEOUT and skips to the
+// end, where the cluster's CTAs meet once more before they exit (no CTA
+// leaves while another may still read its shared memory).
+// ---------------------------------------------------------------------------
+constexpr int CL_CTAS = 16;     // CTAs per cluster (one system)
+constexpr int CL_BS = 512;      // threads per CTA
+constexpr int CL_CHUNK = 512;   // at most this many sites per CTA
+constexpr int CL_VEC = 6 * CL_CHUNK;  // float4 words of one vector chunk
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// bounded barrier of the cluster: every CTA arrives (release, cluster
+// scope) on every CTA's mbarrier, then waits on its own for the phase to
+// complete; false when the wait gave up
+__device__ bool cl_sync(const SolveArgs& A, unsigned long long* mbar, uint32_t& parity, int ncta)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    // thread r arrives on CTA r's barrier: the ncta releases run in parallel
+    // (each orders the CTA's writes before it through the __syncthreads)
+    const uint32_t local = smem_u32(mbar);
+    if ((int)threadIdx.x < ncta) {
+        uint32_t remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"((int)threadIdx.x));
+        asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+    }
+    if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        int ok = 0;
+        for (;;) {
+            uint32_t done;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(local), "r"(parity)
+                : "memory");
+            if (done) {
+                ok = 1;
+                break;
+            }
+            if (*(volatile int*)A.status == LQCD_ERR_TIMEOUT || clock64() - t0 > A.spin_limit) break;
+        }
+        if (!ok) {
+            atomicExch(A.status, LQCD_ERR_TIMEOUT);
+            atomicCAS(A.sticky, 0, LQCD_ERR_TIMEOUT);
+        }
+        parity ^= 1u;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// sum over the cluster of up to three doubles: the CTA's partial goes to
+// its own slot, and after the barrier every CTA adds all slots in rank
+// order (the same totals in every CTA).  Double-buffered like reduce_put.
+__device__ bool cl_reduce(const SolveArgs& A, unsigned long long* mbar, uint32_t& parity, int ncta,
+                          double (*slot)[NQ], int& rb, double a, double b, double c, int nq, double* out)
+{
+    namespace cg = cooperative_groups;
+    __shared__ double sh[NQ][CL_BS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][w] = a;
+        sh[1][w] = b;
+        sh[2][w] = c;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nq) {
+        double v = 0.0;
+        for (int k = 0; k < CL_BS / 32; ++k) v += sh[threadIdx.x][k];
+        slot[rb][threadIdx.x] = v;
+    }
+    if (!cl_sync(A, mbar, parity, ncta)) return false;
+    if ((int)threadIdx.x < nq) {
+        cg::cluster_group cl = cg::this_cluster();
+        double v = 0.0;
+        for (int r = 0; r < ncta; ++r) v += cl.map_shared_rank(&slot[rb][0], r)[threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+    rb ^= 1;
+    __syncthreads();
+    return true;
+}
+
+__global__ void __launch_bounds__(CL_BS, 1) k_series_cl(SolveArgs A)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int ncta = CL_CTAS;
+    const int sys = blockIdx.x / CL_CTAS;
+    const int tid = threadIdx.x;
+    const bool leader = (rank == 0 && tid == 0);
+    const int base = (A.slab0 + sys * A.slabstep) * A.g.Sh;
+    const int chunk = A.chunk;
+    const int j0 = rank * chunk, j1 = min(A.nsite, j0 + chunk);
+    extern __shared__ __align__(16) float4 cl_dyn[];
+    float4* ps = cl_dyn;              // iterate p, [6][CL_CHUNK]
+    float4* ts = cl_dyn + CL_VEC;      // H_oe p
+    float4* rs = cl_dyn + 2 * CL_VEC;  // inner source r
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ double slot[2][NQ];
+    __shared__ SysSt S;
+    __shared__ double red[NQ];
+    __shared__ int s_fail;
+    uint32_t parity = 0;
+    int rb = 0;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(ncta) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    // every CTA's mbarrier exists before anyone arrives on it
+    cl.sync();
+
+    // spinor of eo index j (of the system's parity block) from the shared
+    // memory of the CTA that owns it
+    // (chunk a power of two: the owner by a shift; the own chunk read
+    // directly, only the other CTAs' through the cluster window)
+    const int lgc = (chunk & (chunk - 1)) == 0 ? __ffs(chunk) - 1 : -1;
+    auto dsm = [&](const float4* buf, int j, Spinor<float>& sp) {
+        const int loc = j - base;
+        const int r = lgc >= 0 ? loc >> lgc : loc / chunk, off = loc - r * chunk;
+        const float4* q = (r == rank ? buf : cl.map_shared_rank(buf, r)) + off;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 d = q[k * CL_CHUNK];
+            sp.c[(2 * k) / 3][(2 * k) % 3] = mk(d.x, d.y);
+            sp.c[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(d.z, d.w);
+        }
+    };
+    auto st_loc = [&](float4* buf, int off, const Spinor<float>& sp) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const cx<float> a = sp.c[(2 * k) / 3][(2 * k) % 3], b = sp.c[(2 * k + 1) / 3][(2 * k + 1) % 3];
+            buf[k * CL_CHUNK + off] = make_float4(a.re, a.im, b.re, b.im);
+        }
+    };
+    auto ld_loc = [&](const float4* buf, int off, Spinor<float>& sp) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 d = buf[k * CL_CHUNK + off];
+            sp.c[(2 * k) / 3][(2 * k) % 3] = mk(d.x, d.y);
+            sp.c[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(d.z, d.w);
+        }
+    };
+#define CL_SITES for (int j_ = j0 + tid; j_ < j1; j_ += CL_BS)
+#define CL_SYNC_OR_END                                     \
+    if (!cl_sync(A, &mbar, parity, ncta)) { \
+        s_fail = 1;                                        \
+        goto the_end;                                      \
+    }
+#define CL_REDUCE_OR_END(a, b, c, nq)                                                  \
+    if (!cl_reduce(A, &mbar, parity, ncta, slot, rb, (a), (b), (c), (nq), red)) { \
+        s_fail = 1;                                                                    \
+        goto the_end;                                                                  \
+    }
+    {
+        int outer = 0, final_flag = F_DONE;
+        // ---- x = 0, r64 = b, |b|^2; with an initial guess: t64 = H_oe x
+        {
+            double q = 0.0;
+            CL_SITES
+            {
+                const int i = base + j_;
+                Spinor<double> bb, z;
+                load_spinor<PREC64, true>(A.b, i, bb);
+                if (A.guess) {
+                    Spinor<df> hz;
+                    hop_site<PRECDF, false, SOLVE_UNR>(A.g, A.mode, 0, 1, i, A.x, A.U64, hz);
+                    store_spinor<PRECDS>(A.t64, i, hz);
+                } else {
+                    store_spinor<PREC64>(A.r64, i, bb);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) z.c[s][c] = mk(0.0, 0.0);
+                    store_spinor<PREC64>(A.x, i, z);
+                }
+                q += nrm_acc(bb);
+            }
+            CL_REDUCE_OR_END(q, 0.0, 0.0, 1);
+            if (tid == 0) {
+                S.bn2 = red[0];
+                S.rn2 = red[0];
+                S.it = 0;
+            }
+            __syncthreads();
+        }
+        if (A.guess) {
+            double q = 0.0;
+            CL_SITES
+            {
+                const int i = base + j_;
+                Spinor<double> a, xx, bb;
+                {
+                    Spinor<df> ha;
+                    hop_site<PRECDS, false, SOLVE_UNR>(A.g, A.mode, 0, 0, i, A.t64, A.U64, ha);
+                    to_double(ha, a);
+                }
+                load_spinor<PREC64, false>(A.x, i, xx);
+                load_spinor<PREC64, true>(A.b, i, bb);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) a.c[s][c] = bb.c[s][c] - A.diag * xx.c[s][c] + A.k2 * a.c[s][c];
+                store_spinor<PREC64>(A.r64, i, a);
+                q += nrm_acc(a);
+            }
+            CL_REDUCE_OR_END(q, 0.0, 0.0, 1);
+            if (tid == 0) S.rn2 = red[0];
+            __syncthreads();
+            if (!(S.bn2 > 0.0)) CL_SITES
+                {
+                    Spinor<double> z;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) z.c[s][c] = mk(0.0, 0.0);
+                    store_spinor<PREC64>(A.x, base + j_, z);
+                }
+        }
+        for (;;) {
+            if (tid == 0) {
+                const bool nan = !isfinite(S.rn2);
+                const bool conv = !(S.rn2 > A.tol * A.tol * S.bn2) || !(S.bn2 > 0.0);
+                S.active = (!nan && !conv) ? 1 : 0;
+                int f = nan ? F_NAN : conv ? F_DONE : F_ACTIVE;
+                if (f == F_ACTIVE && (outer >= A.max_outer || S.it >= A.max_iter)) f = F_MAXIT;
+                S.flag = f;
+            }
+            __syncthreads();
+            if (S.flag != F_ACTIVE) {
+                final_flag = S.flag;
+                break;
+            }
+            ++outer;
+            // ---- inner start: r = p = r64 / |r64|
+            {
+                const double sc = 1.0 / sqrt(S.rn2);
+                double q = 0.0;
+                CL_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<double> r6;
+                    load_spinor<PREC64, false>(A.r64, i, r6);
+                    Spinor<float> r;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            r.c[s][c] = mk((float)(sc * r6.c[s][c].re), (float)(sc * r6.c[s][c].im));
+                    st_loc(rs, j_ - j0, r);
+                    st_loc(ps, j_ - j0, r);
+                    q += nrm_acc(r);
+                }
+                CL_REDUCE_OR_END(q, 0.0, 0.0, 1);
+                if (tid == 0) {
+                    S.idone = 0;
+                    S.itc = 0;
+                    const double need = 0.5 * A.tol * sqrt(S.bn2 / fmax(S.rn2, 1e-300));
+                    const double it = fmax(A.inner_tol, need);
+                    S.itol2 = it * it;
+                }
+                __syncthreads();
+            }
+            // ---- the series p <- (r + k2 H_eo H_oe p) / diag, its residual
+            // reduced every second iteration (as in k_solve)
+            {
+                const float k2 = (float)A.k2, dinv = (float)(1.0 / A.diag);
+                for (;;) {
+                    if (S.idone) break;
+                    const bool chk = (S.itc & 1) || S.itc + 1 >= A.max_inner || S.it + 1 >= A.max_iter;
+                    CL_SITES
+                    {
+                        Spinor<float> a;
+                        hop_site_ld<PREC32, SERIES_UNR>(A.g, A.mode, 0, 1, base + j_,
+                                                        [&](int j, Spinor<float>& sp) { dsm(ps, j, sp); }, A.UP, a);
+                        st_loc(ts, j_ - j0, a);
+                    }
+                    CL_SYNC_OR_END;
+                    double q = 0.0;
+                    CL_SITES
+                    {
+                        Spinor<float> a, pp, rr;
+                        hop_site_ld<PREC32, SERIES_UNR>(A.g, A.mode, 0, 0, base + j_,
+                                                        [&](int j, Spinor<float>& sp) { dsm(ts, j, sp); }, A.UP, a);
+                        ld_loc(ps, j_ - j0, pp);
+                        ld_loc(rs, j_ - j0, rr);
+#pragma unroll
+                        for (int s = 0; s < 4; ++s)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) a.c[s][c] = dinv * (rr.c[s][c] + k2 * a.c[s][c]);
+                        st_loc(ps, j_ - j0, a);
+                        if (chk) {
+#pragma unroll
+                            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) pp.c[s][c] = a.c[s][c] - pp.c[s][c];
+                            q += nrm_acc(pp);
+                        }
+                    }
+                    if (!chk) {
+                        CL_SYNC_OR_END;
+                        if (tid == 0) {
+                            S.it += 1;
+                            S.itc += 1;
+                        }
+                        __syncthreads();
+                        continue;
+                    }
+                    CL_REDUCE_OR_END(q, 0.0, 0.0, 1);
+                    if (tid == 0) {
+                        S.it += 1;
+                        S.itc += 1;
+                        const double res2 = A.diag * A.diag * red[0];
+                        if (!(res2 > S.itol2) || S.itc >= A.max_inner || S.it >= A.max_iter) S.idone = 1;
+                        if (!isfinite(res2) || (S.itc >= 16 && res2 > 1e6)) {
+                            S.idone = 1;
+                            S.it = A.max_iter;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            // ---- x += |r64| p (double)
+            {
+                const double sc = sqrt(S.rn2);
+                CL_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<double> xx;
+                    Spinor<float> e;
+                    load_spinor<PREC64, false>(A.x, i, xx);
+                    ld_loc(ps, j_ - j0, e);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            xx.c[s][c] = xx.c[s][c] + mk(sc * (double)e.c[s][c].re, sc * (double)e.c[s][c].im);
+                    store_spinor<PREC64>(A.x, i, xx);
+                }
+            }
+            CL_SYNC_OR_END;
+            // ---- t64 = H_oe x (double-float)
+            CL_SITES
+            {
+                const int i = base + j_;
+                Spinor<df> a;
+                hop_site<PRECDF, false, SOLVE_UNR>(A.g, A.mode, 0, 1, i, A.x, A.U64, a);
+                store_spinor<PRECDS>(A.t64, i, a);
+            }
+            CL_SYNC_OR_END;
+            // ---- r64 = b - diag x + k2 H_eo t64 ; |r64|^2
+            {
+                double q = 0.0;
+                CL_SITES
+                {
+                    const int i = base + j_;
+                    Spinor<double> a, xx, bb;
+                    {
+                        Spinor<df> ha;
+                        hop_site<PRECDS, false, SOLVE_UNR>(A.g, A.mode, 0, 0, i, A.t64, A.U64, ha);
+                        to_double(ha, a);
+                    }
+                    load_spinor<PREC64, false>(A.x, i, xx);
+                    load_spinor<PREC64, true>(A.b, i, bb);
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) a.c[s][c] = bb.c[s][c] - A.diag * xx.c[s][c] + A.k2 * a.c[s][c];
+                    store_spinor<PREC64>(A.r64, i, a);
+                    q += nrm_acc(a);
+                }
+                CL_REDUCE_OR_END(q, 0.0, 0.0, 1);
+                if (tid == 0) S.rn2 = red[0];
+                __syncthreads();
+            }
+        }
+        if (leader) {
+            A.iters[sys] = S.it;
+            A.resid[sys] = S.bn2 > 0.0 ? sqrt(S.rn2 / S.bn2) : 0.0;
+            if (sys == 0) *A.outer_out = outer;
+            if (final_flag == F_NAN) atomicCAS(A.status, 0, LQCD_ERR_NAN);
+            if (final_flag == F_MAXIT) atomicCAS(A.status, 0, LQCD_ERR_NOCONVERGE);
+            if (final_flag == F_NAN) atomicCAS(A.sticky, 0, LQCD_ERR_NAN);
+            if (final_flag == F_MAXIT) atomicCAS(A.sticky, 0, LQCD_ERR_NOCONVERGE);
+            atomicAdd(A.acc, (unsigned long long)S.it);
+            atomicAdd(A.acc + 3, (unsigned long long)S.it * (unsigned long long)A.nsite);
+            atomicAdd(A.acc + 2, (unsigned long long)outer * (unsigned long long)A.nsite);
+        }
+    }
+the_end:
+    // no CTA leaves while another of its cluster may still read its shared
+    // memory: every path (converged, failed, or a wait that gave up) ends here
+    cl.sync();
+}
+#undef CL_SITES
+#undef CL_SYNC_OR_END
+#undef CL_REDUCE_OR_END
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1667,6 +2094,7 @@ struct Work {
     int* h_status = nullptr;  // pinned mirror: status, outer, iters[NSYS_MAX]
     double* h_resid = nullptr;
     int gmax[NPREC] = {0, 0, 0, 0};  // co-resident CTAs per precision
+    int cl_ok = 0;                   // the device runs k_series_cl's clusters
     // the Schwarz-preconditioned global solve: 11 full-lattice vectors, each
     // sized for a double full field (allocated on first use)
     static constexpr int NSAP = 11;
@@ -1727,6 +2155,29 @@ int solver_init(lqcd_ctx* h)
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[1], k_solve<PREC32, true>, SBS, smf));
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[2], k_solve<PREC16, true>, SBS, smf));
     LQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs[3], k_solve<PRECBF, true>, SBS, smf));
+    // the cluster series solver: 16-CTA clusters (a non-portable size) with
+    // three vector chunks of shared memory each; unsupported -> not used
+    {
+        const int clsm = 3 * CL_VEC * (int)sizeof(float4);
+        cudaLaunchConfig_t cc = {};
+        cc.gridDim = dim3(CL_CTAS);
+        cc.blockDim = dim3(CL_BS);
+        cc.dynamicSmemBytes = clsm;
+        cudaLaunchAttribute ca[1];
+        ca[0].id = cudaLaunchAttributeClusterDimension;
+        ca[0].val.clusterDim.x = CL_CTAS;
+        ca[0].val.clusterDim.y = 1;
+        ca[0].val.clusterDim.z = 1;
+        cc.attrs = ca;
+        cc.numAttrs = 1;
+        int ncl = 0;
+        if (cudaFuncSetAttribute(k_series_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, clsm) != cudaSuccess ||
+            cudaFuncSetAttribute(k_series_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+            cudaOccupancyMaxActiveClusters(&ncl, (const void*)k_series_cl, &cc) != cudaSuccess)
+            ncl = 0;
+        cudaGetLastError();  // an unsupported configuration leaves no error behind
+        w->cl_ok = ncl >= 1 ? 1 : 0;
+    }
     int gm = 0;
     for (int k = 0; k < NPREC; ++k) {
         w->gmax[k] = std::max(1, std::min(occ[k], occs[k])) * h->num_sms;
@@ -1950,12 +2401,35 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     LQ_CUDA(h, cudaMemsetAsync(w->bar, 0, sizeof(unsigned) * BAR_STRIDE * A.nsys, h->stream));
     LQ_CUDA(h, cudaMemsetAsync(w->status, 0, sizeof(int) * 4, h->stream));
     void* args[] = {&A};
+    // the geometric series of single-precision slab systems of at most
+    // CL_CTAS * CL_CHUNK sites runs on thread-block clusters (k_series_cl)
+    const bool clu = w->cl_ok && h->tune.cluster_series && prec == PREC32 && method == SOLVER_SERIES &&
+                     mode == MODE_INTRA && A.nsite <= CL_CTAS * CL_CHUNK;
+    cudaEvent_t ev = nullptr;
+    if (clu) {
+        A.cps = CL_CTAS;
+        A.chunk = (A.nsite + CL_CTAS - 1) / CL_CTAS;
+        prof_begin(h, 1, &ev);
+        cudaLaunchConfig_t cc = {};
+        cc.gridDim = dim3(A.nsys * CL_CTAS);
+        cc.blockDim = dim3(CL_BS);
+        cc.dynamicSmemBytes = 3 * CL_VEC * sizeof(float4);
+        cc.stream = h->stream;
+        cudaLaunchAttribute ca[1];
+        ca[0].id = cudaLaunchAttributeClusterDimension;
+        ca[0].val.clusterDim.x = CL_CTAS;
+        ca[0].val.clusterDim.y = 1;
+        ca[0].val.clusterDim.z = 1;
+        cc.attrs = ca;
+        cc.numAttrs = 1;
+        LQ_CUDA(h, cudaLaunchKernelExC(&cc, (const void*)k_series_cl, args));
+        prof_end(h, 1, ev, 0.0);
+    }
     const void* fn = prec == PREC64 ? (sap ? (const void*)k_solve<PREC64, true> : (const void*)k_solve<PREC64, false>)
                      : prec == PREC32 ? (sap ? (const void*)k_solve<PREC32, true> : (const void*)k_solve<PREC32, false>)
                      : prec == PREC16 ? (sap ? (const void*)k_solve<PREC16, true> : (const void*)k_solve<PREC16, false>)
                                       : (sap ? (const void*)k_solve<PRECBF, true> : (const void*)k_solve<PRECBF, false>);
-    cudaEvent_t ev;
-    prof_begin(h, 1, &ev);
+    if (!clu) prof_begin(h, 1, &ev);
     // cooperative launch (every CTA resident), expressed as a launch
     // attribute so that it can also be recorded into a CUDA graph
     cudaLaunchConfig_t cfg = {};
@@ -1968,10 +2442,12 @@ int eo_solve(lqcd_ctx* h, int mode, int colour, int prec, double kappa, double2*
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    LQ_CUDA(h, cudaLaunchKernelExC(&cfg, fn, args));
+    if (!clu) {
+        LQ_CUDA(h, cudaLaunchKernelExC(&cfg, fn, args));
+        prof_end(h, 1, ev, 0.0);
+    }
     h->launches += 1;
     h->solve_count += 1;
-    prof_end(h, 1, ev, 0.0);
     // deferred mode (graph capture): status and iterations stay on the
     // device (sticky status, iteration sums) until solver_collect
     if (h->deferred) return LQCD_OK;

@@ -39,7 +39,7 @@ EXPORTS = [
     "lqcd_gauge_action_static", "lqcd_force_profile", "lqcd_set_subslabs", "lqcd_subblock_dslash",
     "lqcd_subblock_solve_batched", "lqcd_subblock_eo", "lqcd_pf_force_eo", "lqcd_link_update",
     "lqcd_autotune", "lqcd_tune_read", "lqcd_profile_times", "lqcd_set_wait_limit",
-    "lqcd_set_global_solver", "lqcd_set_solver_schedule",
+    "lqcd_set_global_solver", "lqcd_set_solver_schedule", "lqcd_set_cluster_series",
 ]
 
 
@@ -137,6 +137,7 @@ def load():
         "lqcd_force_profile": [vp, vp, vp],
         "lqcd_set_wait_limit": [vp, i64],
         "lqcd_set_solver_schedule": [vp, i],
+        "lqcd_set_cluster_series": [vp, i],
         "lqcd_set_global_solver": [vp, i, i],
     }
     for name, args in sig.items():
@@ -233,6 +234,10 @@ def lqcd_block_solve_batched(h, x, b, kappa, colour=-1, dagger=0, precision=PREC
 
 def lqcd_autotune(h, what=3, kappa=0.15):
     return _check(h, load().lqcd_autotune(h, int(what), float(kappa)))
+
+
+def lqcd_set_cluster_series(h, enable):
+    return _check(h, load().lqcd_set_cluster_series(h, int(bool(enable))))
 
 
 def lqcd_set_solver_schedule(h, spt):
