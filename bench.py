@@ -82,9 +82,9 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # profiles/k_solve_16x16x16x32_f32.md, valid only for the solver source
 # that was captured (bench.py reports null once the source differs)
 SOLVER_SOURCES = ("lqcd_solver.cu", "lqcd_common.cuh", "lqcd_df.cuh")  # the sources k_solve is built from
-SOLVER_TRAFFIC = dict(src_sha256="7fa603f6d2a7ac59799771f4f2296474a27bfa8db912a152917335271615022c",
-                      block_series=(301.616128e6 + 145.132800e6), block=(326.892544e6 + 324.286976e6),
-                      glob=(418.285056e6 + 516.481024e6))
+SOLVER_TRAFFIC = dict(src_sha256="aef4788cc714dda78760d271604c272fd83e3842839fc76a07edbe1288dfd3b3",
+                      block_series=(303.767e6 + 154.127e6), block=(307.420e6 + 312.868e6),
+                      glob=(392.167e6 + 425.938e6))
 
 
 def solver_traffic():
