@@ -84,5 +84,7 @@ def test_static_gauge_action_validates_on_the_host(lib):
 
 def test_null_handle_is_an_argument_error(lib):
     for name, args in [("lqcd_set_gauge", [None, None]), ("lqcd_launch_count", [None, None]),
-                       ("lqcd_set_subslabs", [None, 0])]:
+                       ("lqcd_set_subslabs", [None, 0]), ("lqcd_set_global_solver", [None, 3, 4]),
+                       ("lqcd_set_solver_schedule", [None, 0]), ("lqcd_set_cluster_series", [None, 1]),
+                       ("lqcd_set_wait_limit", [None, ctypes.c_int64(0)])]:
         assert getattr(lib, name)(*args) == -1, name
